@@ -1,0 +1,194 @@
+/*
+ * wfa_gpu.h -- C ABI of libwfa_gpu.so: batched exact gap-affine pairwise
+ * alignment with the wavefront algorithm (WFA) on one NVIDIA GB300 (sm_103a).
+ *
+ * The operation (paper, Sec. I "Introduction and Methods"): align a large
+ * number of independent read pairs, each one on its own with no
+ * communication between pairs, using the original gap-affine WFA with no
+ * algorithmic change (Sec. I, "we apply no optimizations"); every pair
+ * yields its result (Sec. I: "aligns the reads using WFA, and writes the
+ * result").  Here the result is the optimal score and one canonical optimal
+ * alignment as a run-length CIGAR.
+ *
+ * Scoring (gap-affine, match = 0):
+ *   score = min over global alignments of
+ *           x * (#mismatches) + sum over maximal gap runs of (o + len * e)
+ *   I consumes one text character, D one pattern character; an I run next to
+ *   a D run counts as two runs.
+ *
+ * Canonical alignment (the paper is silent on ties; this library fixes one
+ * rule): walking back from the end of both sequences, each operation is
+ * placed at the largest text offset it can take (fewest trailing matches);
+ * among operations at the same offset a mismatch (X) is preferred over an
+ * insertion (I) over a deletion (D); inside a gap, extending it is preferred
+ * over opening it.
+ *
+ * CIGAR word: (run_length << 4) | op, op 0 = M (match), 1 = X (mismatch),
+ * 2 = I (text only), 3 = D (pattern only).  Runs of one op never touch.
+ * SAM users: this library's I/D are from the text's point of view; with the
+ * pattern as the query and the text as the reference, swap I and D.
+ *
+ * Threading: a context may be used by one host thread at a time.  All calls
+ * are synchronous unless stated otherwise.
+ */
+#ifndef WFA_GPU_H
+#define WFA_GPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wfa_gpu_ctx wfa_gpu_ctx;
+
+/* Penalties: mismatch x >= 1, gap open o >= 0, gap extend e >= 1, each at
+ * most WFA_GPU_MAX_PENALTY.  A gap of length L costs o + L*e. */
+typedef struct {
+  int32_t x, o, e;
+} wfa_gpu_penalties;
+
+#define WFA_GPU_MAX_PENALTY (1 << 16)
+/* Longest accepted sequence.  Run lengths fit the 28-bit CIGAR field. */
+#define WFA_GPU_MAX_SEQ_LEN ((1 << 28) - 1)
+
+/* Return codes.  Negative: the call failed and no output is valid. */
+enum {
+  WFA_GPU_OK = 0,
+  WFA_GPU_EINVAL = -1,          /* bad argument (NULL, negative size, bad penalty, bad length) */
+  WFA_GPU_ENOMEM = -2,          /* device or host allocation failed, or the scratch arena is
+                                   too small for some pair's wavefronts */
+  WFA_GPU_ECUDA = -3,           /* a CUDA runtime call failed (no device, launch failure) */
+  WFA_GPU_ECIGAR_CAPACITY = -4, /* CIGAR words exceed cigar_capacity_words; scores, status
+                                   and out_cigar_offsets are still valid, the CIGAR buffer is
+                                   untouched, and out_cigar_offsets[n] is the size needed */
+  WFA_GPU_ETIMEOUT = -5         /* a bounded device-side wait gave up */
+};
+
+/* Per-pair status (out_status). */
+enum {
+  WFA_PAIR_OK = 0,
+  WFA_PAIR_SCORE_LIMIT = 1,  /* optimal score > max_score (max_score > 0) */
+  WFA_PAIR_INVALID_CHAR = 2  /* a byte other than A/C/G/T (either case) */
+};
+
+/* Flags for wfa_gpu_align_batch. */
+enum {
+  WFA_GPU_SCORE_ONLY = 1u,  /* compute scores only; out_cigars may be NULL */
+  WFA_GPU_DEVICE_PTRS = 2u, /* every input and output pointer is device memory on the
+                               context's device (default: host memory) */
+  WFA_GPU_TIMING = 4u       /* record per-phase device times for wfa_gpu_last_timing */
+};
+
+/* Device-side times of the last wfa_gpu_align_batch call on a context,
+ * measured with CUDA events on the context's stream (only with
+ * WFA_GPU_TIMING; otherwise zero). */
+typedef struct {
+  float h2d_ms;      /* host -> device copies of inputs (host-pointer mode) */
+  float align_ms;    /* the fused short-read wavefront kernel */
+  float general_ms;  /* the scratch-arena wavefront kernel (pairs it took over) */
+  float cigar_ms;    /* CIGAR offset scan and compaction */
+  float d2h_ms;      /* device -> host copies of outputs (host-pointer mode) */
+  float total_ms;    /* whole call, first to last event */
+  int32_t kernel_launches; /* kernels this library launched during the call */
+  int32_t reserved;
+  int64_t deferred_pairs;  /* pairs handed from the short-read kernel to the arena kernel */
+} wfa_gpu_timing;
+
+/* Create a context on CUDA device `device`.
+ * scratch_bytes: size of the device scratch arena holding wavefronts of
+ * pairs that do not fit the short-read kernel's shared memory (long reads,
+ * high scores); 0 selects 1 GiB.  The context owns the arena, its internal
+ * buffers (grown on demand) and a CUDA stream.
+ * Returns WFA_GPU_OK and *out, or EINVAL (out NULL, device < 0), ECUDA (no
+ * such device / CUDA unavailable) or ENOMEM; *out is NULL on failure. */
+int wfa_gpu_create(wfa_gpu_ctx **out, int device, size_t scratch_bytes);
+
+/* Make the context launch its work on `stream` (a cudaStream_t of the
+ * context's device, e.g. a framework's current stream) instead of its own;
+ * NULL restores the context's own stream.  The caller keeps ownership of the
+ * stream and must keep it alive while the context uses it. */
+int wfa_gpu_set_stream(wfa_gpu_ctx *ctx, void *stream);
+
+/* Align n_pairs independent pairs (paper Sec. I: many read pairs aligned
+ * independently, each producing its result; Sec. II workload: 100 bp reads).
+ *
+ * Inputs, for pair i:
+ *   pattern = patterns[pattern_offsets[i] .. + pattern_lengths[i])
+ *   text    = texts[text_offsets[i] .. + text_lengths[i])
+ * ASCII bytes; A/C/G/T in either case.  An offsets array may be NULL, which
+ * means the sequences lie back to back in pair order starting at byte 0.
+ * Lengths are 0 .. WFA_GPU_MAX_SEQ_LEN.  Offsets must be >= 0.
+ * pen: penalties (see wfa_gpu_penalties).
+ * max_score: if > 0, pairs whose optimal score exceeds it get status
+ *   WFA_PAIR_SCORE_LIMIT (a score equal to max_score is reported); <= 0 means
+ *   no bound.
+ * flags: WFA_GPU_SCORE_ONLY | WFA_GPU_DEVICE_PTRS | WFA_GPU_TIMING.
+ *
+ * Outputs (caller-owned):
+ *   out_scores[n]   int32 optimal score, -1 if status != OK
+ *   out_status[n]   int8 WFA_PAIR_*
+ *   out_cigar_offsets[n+1]  int64; pair i's CIGAR is
+ *       out_cigars[out_cigar_offsets[i] .. out_cigar_offsets[i+1]); empty if
+ *       status != OK; out_cigar_offsets[0] = 0.  May be NULL with SCORE_ONLY.
+ *   out_cigars[cigar_capacity_words]  uint32 CIGAR words (see above).  May be
+ *       NULL with SCORE_ONLY or when cigar_capacity_words == 0.
+ * With WFA_GPU_DEVICE_PTRS every pointer above (inputs and outputs) is device
+ * memory; otherwise all are host memory (page-locked memory copies fastest).
+ * Sizing: wfa_gpu_cigar_bound() per pair gives a safe capacity.
+ *
+ * Returns WFA_GPU_OK (every pair has a status), or EINVAL, ENOMEM, ECUDA,
+ * ECIGAR_CAPACITY (see the enum).  The call returns after all outputs are
+ * in the caller's buffers. */
+int wfa_gpu_align_batch(wfa_gpu_ctx *ctx, int64_t n_pairs,
+                        const char *patterns, const int64_t *pattern_offsets,
+                        const int32_t *pattern_lengths,
+                        const char *texts, const int64_t *text_offsets,
+                        const int32_t *text_lengths,
+                        wfa_gpu_penalties pen, int32_t max_score, uint32_t flags,
+                        int32_t *out_scores, int8_t *out_status,
+                        uint32_t *out_cigars, int64_t cigar_capacity_words,
+                        int64_t *out_cigar_offsets);
+
+/* Pack sequences into the 2-bit format the wavefront kernels extend with
+ * (the per-pair fetch of Sec. I, "fetches the read pair ... aligns"):
+ * A=0 C=1 G=2 T=3 (either case), 32 bases per uint64 word, base j of a word
+ * in bits (63-2j):(62-2j), bits past the end zero, then one zero pad word;
+ * sequence i takes ceil(len/32) + 1 words starting at out_word_offsets[i].
+ * Inputs as in wfa_gpu_align_batch (offsets may be NULL = back to back).
+ * Outputs: out_word_offsets[n_seqs+1] int64 (exclusive prefix sum of the
+ * word counts; [n_seqs] = total), out_words[words_capacity] uint64,
+ * out_invalid[n_seqs] int8 (1 if the sequence holds a byte other than
+ * A/C/G/T; its words are then unspecified).
+ * All pointers are device memory when flags has WFA_GPU_DEVICE_PTRS, else
+ * host memory.  Returns OK, EINVAL, ENOMEM, ECUDA, or ECIGAR_CAPACITY when
+ * the total word count exceeds words_capacity (offsets still valid, words
+ * untouched). */
+int wfa_gpu_pack2bit(wfa_gpu_ctx *ctx, int64_t n_seqs, const char *seqs,
+                     const int64_t *offsets, const int32_t *lengths, uint32_t flags,
+                     uint64_t *out_words, int64_t words_capacity,
+                     int64_t *out_word_offsets, int8_t *out_invalid);
+
+/* Upper bound on the CIGAR words of one pair of lengths plen, tlen under pen
+ * and max_score (<= 0: unbounded): with s the largest score the pair can
+ * report, at most 2*floor(s / min(x, o+e)) + 1 runs, and never more than
+ * plen + tlen.  Returns -1 on invalid arguments.  Host-only; no device work. */
+int64_t wfa_gpu_cigar_bound(int32_t plen, int32_t tlen, wfa_gpu_penalties pen,
+                            int32_t max_score);
+
+/* Per-phase times of the last align call (see wfa_gpu_timing).  Returns OK
+ * or EINVAL. */
+int wfa_gpu_last_timing(const wfa_gpu_ctx *ctx, wfa_gpu_timing *out);
+
+/* Static description of a return code.  Never NULL. */
+const char *wfa_gpu_strerror(int code);
+
+/* Release the context, its arena, buffers and own stream.  NULL-safe. */
+void wfa_gpu_destroy(wfa_gpu_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WFA_GPU_H */

@@ -1,0 +1,539 @@
+// api.cu -- the C ABI of libwfa_gpu.so (declared in include/wfa_gpu.h):
+// argument checks, device buffers, host<->device staging, and the order of
+// kernel launches for one batch of read pairs (the paper's host flow,
+// Sec. I: inputs distributed to the processing units, pairs aligned
+// independently, results gathered back).
+#include <algorithm>
+#include <climits>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "launch.h"
+#include "wfa_gpu.h"
+
+namespace {
+
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t cap = 0;
+  // grow to at least n elements (contents are not kept)
+  cudaError_t ensure(size_t n) {
+    if (n <= cap && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    size_t want = std::max<size_t>(n + n / 4, 64);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p), want * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    cap = want;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+int gcd(int a, int b) {
+  while (b) {
+    const int t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+bool pen_ok(const wfa_gpu_penalties& p) {
+  return p.x >= 1 && p.o >= 0 && p.e >= 1 && p.x <= WFA_GPU_MAX_PENALTY && p.o <= WFA_GPU_MAX_PENALTY &&
+         p.e <= WFA_GPU_MAX_PENALTY;
+}
+
+constexpr int kEvents = 6;  // start, inputs, align, general, cigar, end
+constexpr int64_t kPoolInitWords = 1 << 22;
+
+}  // namespace
+
+struct wfa_gpu_ctx {
+  int device = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  int32_t* arena = nullptr;
+  size_t arena_bytes = 0;
+  int general_warps = 1;
+  wfa::ShortPlan plan{};
+  wfa::Ctrl* ctrl = nullptr;    // device
+  wfa::Ctrl* h_ctrl = nullptr;  // pinned host mirror
+  int64_t* h_total = nullptr;   // pinned host scalar
+  cudaEvent_t ev[kEvents] = {};
+  wfa_gpu_timing last{};
+  // inputs staged from host memory, and computed offsets
+  DevBuf<char> pat, txt;
+  DevBuf<int32_t> plen, tlen;
+  DevBuf<int64_t> poff, toff;
+  // outputs staged for host memory
+  DevBuf<int32_t> score;
+  DevBuf<int8_t> status;
+  DevBuf<int64_t> cig_off;
+  DevBuf<uint32_t> cig;
+  // internal
+  DevBuf<int32_t> nruns, defer, overflow;
+  DevBuf<int64_t> run_src, scan_tmp;
+  DevBuf<uint32_t> runs;
+  int64_t pool_words = kPoolInitWords;
+};
+
+namespace {
+
+struct Call {
+  wfa_gpu_ctx* c;
+  bool timing;
+  int launches = 0;
+  cudaError_t err = cudaSuccess;
+  void rec(int i) {
+    if (timing && err == cudaSuccess) err = cudaEventRecord(c->ev[i], c->stream);
+  }
+  bool ok(cudaError_t e) {
+    if (err == cudaSuccess) err = e;
+    return err == cudaSuccess;
+  }
+  bool launched(cudaError_t e, int nk = 1) {
+    launches += nk;
+    return ok(e);
+  }
+};
+
+int fail_cuda(Call& k) {
+  (void)k;
+  return WFA_GPU_ECUDA;
+}
+
+int map_alloc(cudaError_t e) { return e == cudaErrorMemoryAllocation ? WFA_GPU_ENOMEM : WFA_GPU_ECUDA; }
+
+float elapsed(wfa_gpu_ctx* c, int a, int b) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, c->ev[a], c->ev[b]) != cudaSuccess) return 0.f;
+  return ms;
+}
+
+cudaError_t h2d(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (!bytes) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+}
+
+cudaError_t d2h(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (!bytes) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st);
+}
+
+// Lengths, offsets and sequences on the device; validates them.  Returns 0 or
+// a negative WFA_GPU_* code.
+int stage_inputs(wfa_gpu_ctx* c, Call& k, int64_t n, bool dev, const char* pat, const int64_t* poff,
+                 const int32_t* plen, const char* txt, const int64_t* toff, const int32_t* tlen,
+                 const char** d_pat, const int64_t** d_poff, const int32_t** d_plen, const char** d_txt,
+                 const int64_t** d_toff, const int32_t** d_tlen) {
+  cudaStream_t st = c->stream;
+  cudaError_t e;
+  if (dev) {
+    *d_plen = plen;
+    *d_tlen = tlen;
+  } else {
+    if ((e = c->plen.ensure(n)) || (e = c->tlen.ensure(n))) return map_alloc(e);
+    if (!k.ok(h2d(c->plen.p, plen, n * sizeof(int32_t), st)) || !k.ok(h2d(c->tlen.p, tlen, n * sizeof(int32_t), st)))
+      return WFA_GPU_ECUDA;
+    *d_plen = c->plen.p;
+    *d_tlen = c->tlen.p;
+  }
+  if ((e = c->scan_tmp.ensure(wfa::scan_tmp_elems(n)))) return map_alloc(e);
+  // offsets: caller's (staged if host) or the exclusive scan of the lengths
+  if (poff && dev) {
+    *d_poff = poff;
+  } else {
+    if ((e = c->poff.ensure(n + 1))) return map_alloc(e);
+    if (poff) {
+      if (!k.ok(h2d(c->poff.p, poff, n * sizeof(int64_t), st))) return WFA_GPU_ECUDA;
+    } else if (!k.launched(wfa::launch_scan(*d_plen, n, 0, c->poff.p, c->scan_tmp.p, st), 3)) {
+      return WFA_GPU_ECUDA;
+    }
+    *d_poff = c->poff.p;
+  }
+  if (toff && dev) {
+    *d_toff = toff;
+  } else {
+    if ((e = c->toff.ensure(n + 1))) return map_alloc(e);
+    if (toff) {
+      if (!k.ok(h2d(c->toff.p, toff, n * sizeof(int64_t), st))) return WFA_GPU_ECUDA;
+    } else if (!k.launched(wfa::launch_scan(*d_tlen, n, 0, c->toff.p, c->scan_tmp.p, st), 3)) {
+      return WFA_GPU_ECUDA;
+    }
+    *d_toff = c->toff.p;
+  }
+  if (!k.ok(cudaMemsetAsync(c->ctrl, 0, sizeof(wfa::Ctrl), st))) return WFA_GPU_ECUDA;
+  if (!k.launched(wfa::launch_validate(n, *d_poff, *d_plen, *d_toff, *d_tlen, c->ctrl, st))) return WFA_GPU_ECUDA;
+  if (!k.ok(d2h(c->h_ctrl, c->ctrl, sizeof(wfa::Ctrl), st)) || !k.ok(cudaStreamSynchronize(st)))
+    return WFA_GPU_ECUDA;
+  if (c->h_ctrl->bad_input) return WFA_GPU_EINVAL;
+  if (dev) {
+    *d_pat = pat;
+    *d_txt = txt;
+  } else {
+    const size_t pe = (size_t)c->h_ctrl->pat_extent, te = (size_t)c->h_ctrl->txt_extent;
+    if ((e = c->pat.ensure(pe + 16)) || (e = c->txt.ensure(te + 16))) return map_alloc(e);
+    if (!k.ok(h2d(c->pat.p, pat, pe, st)) || !k.ok(h2d(c->txt.p, txt, te, st))) return WFA_GPU_ECUDA;
+    *d_pat = c->pat.p;
+    *d_txt = c->txt.p;
+  }
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int wfa_gpu_create(wfa_gpu_ctx** out, int device, size_t scratch_bytes) {
+  if (!out) return WFA_GPU_EINVAL;
+  *out = nullptr;
+  if (device < 0) return WFA_GPU_EINVAL;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device >= count) return WFA_GPU_ECUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return WFA_GPU_ECUDA;
+  wfa_gpu_ctx* c = new (std::nothrow) wfa_gpu_ctx();
+  if (!c) return WFA_GPU_ENOMEM;
+  c->device = device;
+  int rc = WFA_GPU_OK;
+  do {
+    if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) { rc = WFA_GPU_ECUDA; break; }
+    c->stream = c->own_stream;
+    for (int i = 0; i < kEvents; ++i)
+      if (cudaEventCreate(&c->ev[i]) != cudaSuccess) { rc = WFA_GPU_ECUDA; break; }
+    if (rc) break;
+    if (cudaMalloc(reinterpret_cast<void**>(&c->ctrl), sizeof(wfa::Ctrl)) != cudaSuccess) { rc = WFA_GPU_ENOMEM; break; }
+    if (cudaHostAlloc(reinterpret_cast<void**>(&c->h_ctrl), sizeof(wfa::Ctrl), cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc(reinterpret_cast<void**>(&c->h_total), sizeof(int64_t), cudaHostAllocDefault) != cudaSuccess) {
+      rc = WFA_GPU_ENOMEM;
+      break;
+    }
+    c->arena_bytes = scratch_bytes ? scratch_bytes : ((size_t)1 << 30);
+    c->arena_bytes &= ~(size_t)255;
+    if (c->arena_bytes < 4096) { rc = WFA_GPU_EINVAL; break; }
+    if (cudaMalloc(reinterpret_cast<void**>(&c->arena), c->arena_bytes) != cudaSuccess) { rc = WFA_GPU_ENOMEM; break; }
+    if (wfa::short_plan(device, &c->plan) != cudaSuccess) { rc = WFA_GPU_ECUDA; break; }
+    int nsm = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+    c->general_warps = std::max(1, nsm * 4);
+  } while (0);
+  if (rc) {
+    wfa_gpu_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return WFA_GPU_OK;
+}
+
+int wfa_gpu_set_stream(wfa_gpu_ctx* ctx, void* stream) {
+  if (!ctx) return WFA_GPU_EINVAL;
+  ctx->stream = stream ? static_cast<cudaStream_t>(stream) : ctx->own_stream;
+  return WFA_GPU_OK;
+}
+
+int wfa_gpu_align_batch(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t* pattern_offsets,
+                        const int32_t* pattern_lengths, const char* texts, const int64_t* text_offsets,
+                        const int32_t* text_lengths, wfa_gpu_penalties pen, int32_t max_score, uint32_t flags,
+                        int32_t* out_scores, int8_t* out_status, uint32_t* out_cigars, int64_t cap,
+                        int64_t* out_cigar_offsets) {
+  if (!ctx || n < 0 || n > INT32_MAX || cap < 0 || !pen_ok(pen)) return WFA_GPU_EINVAL;
+  if (flags & ~(uint32_t)(WFA_GPU_SCORE_ONLY | WFA_GPU_DEVICE_PTRS | WFA_GPU_TIMING)) return WFA_GPU_EINVAL;
+  const bool dev = flags & WFA_GPU_DEVICE_PTRS;
+  const bool score_only = flags & WFA_GPU_SCORE_ONLY;
+  if (n > 0 && (!patterns || !pattern_lengths || !texts || !text_lengths || !out_scores || !out_status))
+    return WFA_GPU_EINVAL;
+  if (!score_only && !out_cigar_offsets) return WFA_GPU_EINVAL;
+  if (!score_only && cap > 0 && !out_cigars) return WFA_GPU_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return WFA_GPU_ECUDA;
+  std::memset(&ctx->last, 0, sizeof ctx->last);
+  cudaStream_t st = ctx->stream;
+  Call k{ctx, (flags & WFA_GPU_TIMING) != 0};
+  if (n == 0) {
+    if (!score_only) {
+      const int64_t zero = 0;
+      if (dev) {
+        if (!k.ok(cudaMemcpyAsync(out_cigar_offsets, &zero, sizeof zero, cudaMemcpyHostToDevice, st)) ||
+            !k.ok(cudaStreamSynchronize(st)))
+          return WFA_GPU_ECUDA;
+      } else {
+        out_cigar_offsets[0] = 0;
+      }
+    }
+    return WFA_GPU_OK;
+  }
+
+  const int g = gcd(pen.x, gcd(pen.o, pen.e));
+  k.rec(0);
+  const char *d_pat, *d_txt;
+  const int64_t *d_poff, *d_toff;
+  const int32_t *d_plen, *d_tlen;
+  int rc = stage_inputs(ctx, k, n, dev, patterns, pattern_offsets, pattern_lengths, texts, text_offsets,
+                        text_lengths, &d_pat, &d_poff, &d_plen, &d_txt, &d_toff, &d_tlen);
+  if (rc) return rc;
+  k.rec(1);
+
+  cudaError_t e;
+  int32_t* d_score = out_scores;
+  int8_t* d_status = out_status;
+  if (!dev) {
+    if ((e = ctx->score.ensure(n)) || (e = ctx->status.ensure(n))) return map_alloc(e);
+    d_score = ctx->score.p;
+    d_status = ctx->status.p;
+  }
+  const int64_t pool_base = score_only ? 0 : n * (int64_t)wfa::kSlot;
+  if ((e = ctx->nruns.ensure(n)) || (e = ctx->run_src.ensure(n)) || (e = ctx->defer.ensure(n)) ||
+      (e = ctx->overflow.ensure(n)) || (e = ctx->runs.ensure(pool_base + (score_only ? 1 : ctx->pool_words))))
+    return map_alloc(e);
+
+  wfa::AlignArgs a{};
+  a.n = n;
+  a.pat = d_pat; a.poff = d_poff; a.plen = d_plen;
+  a.txt = d_txt; a.toff = d_toff; a.tlen = d_tlen;
+  a.g = g;
+  a.xs = pen.x / g;
+  a.es = pen.e / g;
+  a.oes = (pen.o + pen.e) / g;
+  a.s_cap = max_score > 0 ? max_score / g : INT_MAX;
+  a.score_only = score_only ? 1 : 0;
+  a.score = d_score;
+  a.status = d_status;
+  a.nruns = ctx->nruns.p;
+  a.run_src = ctx->run_src.p;
+  a.runs = ctx->runs.p;
+  a.pool_base = pool_base;
+  a.pool_cap = score_only ? 0 : (int64_t)ctx->runs.cap - pool_base;
+  a.defer_list = ctx->defer.p;
+  a.overflow_list = ctx->overflow.p;
+  a.ctrl = ctx->ctrl;
+
+  if (!k.launched(wfa::launch_short(a, ctx->plan, st))) return fail_cuda(k);
+  k.rec(2);
+  int nwarps = ctx->general_warps;
+  const long arena_ints = (long)(ctx->arena_bytes / sizeof(int32_t));
+  long slot = (arena_ints / nwarps) & ~3L;
+  if (!k.launched(wfa::launch_general(a, ctx->arena, slot, nwarps, st))) return fail_cuda(k);
+  if (!k.ok(d2h(ctx->h_ctrl, ctx->ctrl, sizeof(wfa::Ctrl), st)) || !k.ok(cudaStreamSynchronize(st)))
+    return fail_cuda(k);
+  ctx->last.deferred_pairs = ctx->h_ctrl->defer_count;
+  // Pairs that did not fit their arena slot (or the CIGAR pool) run again
+  // with fewer, larger slots (or a larger pool).
+  while (ctx->h_ctrl->overflow_count > 0) {
+    wfa::Ctrl* hc = ctx->h_ctrl;
+    if (hc->pool_short) {
+      const int64_t used = pool_base + (int64_t)hc->pool_top;
+      const int64_t want = pool_base + 2 * (int64_t)hc->pool_top + kPoolInitWords;
+      uint32_t* nb = nullptr;
+      if ((e = cudaMalloc(reinterpret_cast<void**>(&nb), (size_t)want * sizeof(uint32_t)))) return map_alloc(e);
+      if (!k.ok(cudaMemcpyAsync(nb, ctx->runs.p, (size_t)std::min<int64_t>(used, ctx->runs.cap) * sizeof(uint32_t),
+                                cudaMemcpyDeviceToDevice, st)) ||
+          !k.ok(cudaStreamSynchronize(st))) {
+        cudaFree(nb);
+        return fail_cuda(k);
+      }
+      cudaFree(ctx->runs.p);
+      ctx->runs.p = nb;
+      ctx->runs.cap = (size_t)want;
+      ctx->pool_words = want - pool_base;
+      a.runs = nb;
+      a.pool_cap = want - pool_base;
+    } else {
+      if (nwarps == 1) return WFA_GPU_ENOMEM;  // a pair needs more than the whole arena
+      nwarps = std::max(1, nwarps / 8);
+      slot = (arena_ints / nwarps) & ~3L;
+    }
+    std::swap(a.defer_list, a.overflow_list);
+    hc->defer_count = hc->overflow_count;
+    hc->general_next = 0;
+    hc->overflow_count = 0;
+    hc->pool_short = 0;
+    if (!k.ok(cudaMemcpyAsync(ctx->ctrl, hc, sizeof(wfa::Ctrl), cudaMemcpyHostToDevice, st))) return fail_cuda(k);
+    if (!k.launched(wfa::launch_general(a, ctx->arena, slot, nwarps, st))) return fail_cuda(k);
+    if (!k.ok(d2h(hc, ctx->ctrl, sizeof(wfa::Ctrl), st)) || !k.ok(cudaStreamSynchronize(st))) return fail_cuda(k);
+  }
+  if (ctx->h_ctrl->internal_error) return WFA_GPU_ECUDA;
+  k.rec(3);
+
+  int64_t total = 0;
+  if (!score_only) {
+    int64_t* d_off = out_cigar_offsets;
+    if (!dev) {
+      if ((e = ctx->cig_off.ensure(n + 1))) return map_alloc(e);
+      d_off = ctx->cig_off.p;
+    }
+    if (!k.launched(wfa::launch_scan(ctx->nruns.p, n, 0, d_off, ctx->scan_tmp.p, st), 3)) return fail_cuda(k);
+    if (!k.ok(d2h(ctx->h_total, d_off + n, sizeof(int64_t), st)) || !k.ok(cudaStreamSynchronize(st)))
+      return fail_cuda(k);
+    total = *ctx->h_total;
+    if (total <= cap && total > 0) {
+      uint32_t* d_cig = out_cigars;
+      if (!dev) {
+        if ((e = ctx->cig.ensure(total))) return map_alloc(e);
+        d_cig = ctx->cig.p;
+      }
+      if (!k.launched(wfa::launch_compact(n, ctx->nruns.p, ctx->run_src.p, ctx->runs.p, d_off, d_cig, cap, st)))
+        return fail_cuda(k);
+    }
+  }
+  k.rec(4);
+  if (!dev) {
+    if (!k.ok(d2h(out_scores, d_score, n * sizeof(int32_t), st)) ||
+        !k.ok(d2h(out_status, d_status, n * sizeof(int8_t), st)))
+      return fail_cuda(k);
+    if (!score_only) {
+      if (!k.ok(d2h(out_cigar_offsets, ctx->cig_off.p, (n + 1) * sizeof(int64_t), st))) return fail_cuda(k);
+      if (total <= cap && !k.ok(d2h(out_cigars, ctx->cig.p, total * sizeof(uint32_t), st))) return fail_cuda(k);
+    }
+  }
+  k.rec(5);
+  if (!k.ok(cudaStreamSynchronize(st))) return fail_cuda(k);
+  ctx->last.kernel_launches = k.launches;
+  if (k.timing) {
+    ctx->last.h2d_ms = elapsed(ctx, 0, 1);
+    ctx->last.align_ms = elapsed(ctx, 1, 2);
+    ctx->last.general_ms = elapsed(ctx, 2, 3);
+    ctx->last.cigar_ms = elapsed(ctx, 3, 4);
+    ctx->last.d2h_ms = elapsed(ctx, 4, 5);
+    ctx->last.total_ms = elapsed(ctx, 0, 5);
+  }
+  return total > cap ? WFA_GPU_ECIGAR_CAPACITY : WFA_GPU_OK;
+}
+
+int wfa_gpu_pack2bit(wfa_gpu_ctx* ctx, int64_t n, const char* seqs, const int64_t* offsets, const int32_t* lengths,
+                     uint32_t flags, uint64_t* out_words, int64_t words_capacity, int64_t* out_word_offsets,
+                     int8_t* out_invalid) {
+  if (!ctx || n < 0 || n > INT32_MAX || words_capacity < 0 || !out_word_offsets) return WFA_GPU_EINVAL;
+  if (flags & ~(uint32_t)(WFA_GPU_DEVICE_PTRS)) return WFA_GPU_EINVAL;
+  if (n > 0 && (!seqs || !lengths || !out_invalid || (words_capacity > 0 && !out_words))) return WFA_GPU_EINVAL;
+  const bool dev = flags & WFA_GPU_DEVICE_PTRS;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return WFA_GPU_ECUDA;
+  cudaStream_t st = ctx->stream;
+  Call k{ctx, false};
+  if (n == 0) {
+    const int64_t zero = 0;
+    if (dev) {
+      if (!k.ok(cudaMemcpyAsync(out_word_offsets, &zero, sizeof zero, cudaMemcpyHostToDevice, st)) ||
+          !k.ok(cudaStreamSynchronize(st)))
+        return WFA_GPU_ECUDA;
+    } else {
+      out_word_offsets[0] = 0;
+    }
+    return WFA_GPU_OK;
+  }
+  const char *d_seq, *d_seq2;
+  const int64_t *d_off, *d_off2;
+  const int32_t *d_len, *d_len2;
+  // the same sequences stand in for both halves of a pair
+  int rc = stage_inputs(ctx, k, n, dev, seqs, offsets, lengths, seqs, offsets, lengths, &d_seq, &d_off, &d_len,
+                        &d_seq2, &d_off2, &d_len2);
+  if (rc) return rc;
+  cudaError_t e;
+  int64_t* d_woff = out_word_offsets;
+  if (!dev) {
+    if ((e = ctx->cig_off.ensure(n + 1))) return map_alloc(e);
+    d_woff = ctx->cig_off.p;
+  }
+  if (!k.launched(wfa::launch_scan(d_len, n, 1, d_woff, ctx->scan_tmp.p, st), 3)) return WFA_GPU_ECUDA;
+  if (!k.ok(d2h(ctx->h_total, d_woff + n, sizeof(int64_t), st)) || !k.ok(cudaStreamSynchronize(st)))
+    return WFA_GPU_ECUDA;
+  const int64_t total = *ctx->h_total;
+  uint64_t* d_words = out_words;
+  int8_t* d_inv = out_invalid;
+  if (!dev) {
+    if ((e = ctx->status.ensure(n))) return map_alloc(e);
+    d_inv = ctx->status.p;
+  }
+  if (total <= words_capacity) {
+    DevBuf<uint64_t> tmp;
+    if (!dev) {
+      if ((e = tmp.ensure(total))) return map_alloc(e);
+      d_words = tmp.p;
+    }
+    if (!k.launched(wfa::launch_pack(n, d_seq, d_off, d_len, d_woff, d_words, d_inv, st))) {
+      tmp.release();
+      return WFA_GPU_ECUDA;
+    }
+    if (!dev && (!k.ok(d2h(out_words, d_words, total * sizeof(uint64_t), st)) ||
+                 !k.ok(d2h(out_invalid, d_inv, n, st)))) {
+      tmp.release();
+      return WFA_GPU_ECUDA;
+    }
+    if (!k.ok(cudaStreamSynchronize(st))) {
+      tmp.release();
+      return WFA_GPU_ECUDA;
+    }
+    tmp.release();
+  }
+  if (!dev && (!k.ok(d2h(out_word_offsets, d_woff, (n + 1) * sizeof(int64_t), st)) ||
+               !k.ok(cudaStreamSynchronize(st))))
+    return WFA_GPU_ECUDA;
+  return total > words_capacity ? WFA_GPU_ECIGAR_CAPACITY : WFA_GPU_OK;
+}
+
+int64_t wfa_gpu_cigar_bound(int32_t plen, int32_t tlen, wfa_gpu_penalties pen, int32_t max_score) {
+  if (plen < 0 || tlen < 0 || plen > WFA_GPU_MAX_SEQ_LEN || tlen > WFA_GPU_MAX_SEQ_LEN || !pen_ok(pen)) return -1;
+  if (plen == 0 && tlen == 0) return 0;
+  const int64_t cols = (int64_t)plen + tlen;
+  const int64_t mn = std::min<int64_t>(pen.x, (int64_t)pen.o + pen.e);
+  int64_t s;
+  if (max_score > 0) {
+    s = max_score;
+  } else {
+    // the optimum is at most the cost of either of two alignments: all
+    // diagonal (mismatches) plus one gap for the length difference, or one
+    // gap per sequence
+    const int64_t lo = std::min(plen, tlen), d = std::abs((int64_t)plen - tlen);
+    const int64_t a = pen.x * lo + (d ? pen.o + d * pen.e : 0);
+    const int64_t b = (plen ? pen.o + (int64_t)plen * pen.e : 0) + (tlen ? pen.o + (int64_t)tlen * pen.e : 0);
+    s = std::min(a, b);
+  }
+  return std::min(cols, 2 * (s / mn) + 1);
+}
+
+int wfa_gpu_last_timing(const wfa_gpu_ctx* ctx, wfa_gpu_timing* out) {
+  if (!ctx || !out) return WFA_GPU_EINVAL;
+  *out = ctx->last;
+  return WFA_GPU_OK;
+}
+
+const char* wfa_gpu_strerror(int code) {
+  switch (code) {
+    case WFA_GPU_OK: return "ok";
+    case WFA_GPU_EINVAL: return "invalid argument";
+    case WFA_GPU_ENOMEM: return "out of memory (device, host, or scratch arena too small for a pair)";
+    case WFA_GPU_ECUDA: return "CUDA runtime error";
+    case WFA_GPU_ECIGAR_CAPACITY: return "CIGAR output capacity too small";
+    case WFA_GPU_ETIMEOUT: return "device-side wait timed out";
+    default: return "unknown error code";
+  }
+}
+
+void wfa_gpu_destroy(wfa_gpu_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->own_stream) cudaStreamSynchronize(c->own_stream);
+  if (c->stream && c->stream != c->own_stream) cudaStreamSynchronize(c->stream);
+  c->pat.release(); c->txt.release(); c->plen.release(); c->tlen.release();
+  c->poff.release(); c->toff.release(); c->score.release(); c->status.release();
+  c->cig_off.release(); c->cig.release(); c->nruns.release(); c->defer.release();
+  c->overflow.release(); c->run_src.release(); c->scan_tmp.release(); c->runs.release();
+  if (c->arena) cudaFree(c->arena);
+  if (c->ctrl) cudaFree(c->ctrl);
+  if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
+  if (c->h_total) cudaFreeHost(c->h_total);
+  for (int i = 0; i < kEvents; ++i)
+    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,429 @@
+// kernels.cu -- the CUDA kernels of libwfa_gpu.so (sm_103a) and their
+// launchers.
+//
+//   short_kernel    fused pack + gap-affine WFA + backtrace for pairs whose
+//                   sequences are at most kShortLmax long and whose
+//                   wavefronts fit the group's shared memory (the paper's
+//                   100 bp workload, Sec. II); everything else is deferred
+//   general_kernel  one warp per deferred pair, wavefronts in a slice of the
+//                   global scratch arena, pairs taken from a device work
+//                   queue (atomic counter)
+//   validate/scan/compact/pack  bookkeeping around them
+#include <climits>
+
+#include "launch.h"
+#include "wfa_device.cuh"
+
+namespace wfa {
+
+namespace {
+
+// ------------------------------------------------------------ short kernel
+
+constexpr int kShortG = 8;        // lanes per pair
+constexpr int kShortLmax = 256;   // longest sequence handled
+constexpr int kShortCells = 256;  // wavefront cells per pair (M, I, D each)
+constexpr int kShortScap = 47;    // largest scaled score stored
+constexpr int kShortBlock = 256;
+
+template <int LMAX, int CELLS, int SCAP>
+struct ShortShm {
+  uint64_t pw[LMAX / 32 + 1];  // packed pattern + pad word
+  uint64_t tw[LMAX / 32 + 1];  // packed text + pad word
+  int16_t M[CELLS], I[CELLS], D[CELLS];
+  int16_t lo[SCAP + 1], hi[SCAP + 1], base[SCAP + 1];
+  uint8_t ex[SCAP + 1];
+};
+
+// Per-group shared-memory stride: a multiple of 128 bytes plus 32, so that
+// the groups of one warp start 8 banks apart.
+template <class T>
+__host__ __device__ constexpr size_t group_stride() {
+  return ((sizeof(T) + 127) / 128) * 128 + 32;
+}
+
+using ShortShmT = ShortShm<kShortLmax, kShortCells, kShortScap>;
+constexpr size_t kShortStride = group_stride<ShortShmT>();
+
+__device__ __forceinline__ void defer_pair(const AlignArgs& a, int64_t pair) {
+  const int idx = atomicAdd(&a.ctrl->defer_count, 1);
+  a.defer_list[idx] = (int32_t)pair;
+}
+
+__device__ __forceinline__ void write_result(const AlignArgs& a, int64_t pair, int status, int score, int nr,
+                                             int64_t src) {
+  a.score[pair] = score;
+  a.status[pair] = (int8_t)status;
+  a.nruns[pair] = nr;
+  a.run_src[pair] = src;
+}
+
+template <int G, int LMAX, int CELLS, int SCAP>
+__global__ void __launch_bounds__(kShortBlock) short_kernel(const AlignArgs a) {
+  using Shm = ShortShm<LMAX, CELLS, SCAP>;
+  constexpr size_t kStride = group_stride<Shm>();
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & (G - 1);
+  const int gib = threadIdx.x / G;
+  const int gpb = blockDim.x / G;
+  Shm* S = reinterpret_cast<Shm*>(smem + gib * kStride);
+  const unsigned gmask = group_mask(G);
+  SmemView view{S->M, S->I, S->D, S->lo, S->hi, S->base, S->ex, CELLS, SCAP};
+  const ScaledPen pen{a.xs, a.oes, a.es};
+  const int64_t total_groups = (int64_t)gridDim.x * gpb;
+  // The groups of a warp take consecutive pairs and advance together.
+  for (int64_t pair = (int64_t)blockIdx.x * gpb + gib; __any_sync(0xffffffffu, pair < a.n);
+       pair += total_groups) {
+    if (pair < a.n) {
+      const int n = a.plen[pair], m = a.tlen[pair];
+      if (n > LMAX || m > LMAX) {
+        if (lane == 0) defer_pair(a, pair);
+      } else {
+        const bool okp = pack_seq<G>(a.pat + a.poff[pair], n, S->pw, lane, gmask);
+        const bool okt = pack_seq<G>(a.txt + a.toff[pair], m, S->tw, lane, gmask);
+        __syncwarp(gmask);
+        if (!(okp && okt)) {
+          if (lane == 0) write_result(a, pair, 2, -1, 0, 0);
+        } else {
+          int s = 0;
+          const int r = wfa_forward<G>(view, S->pw, S->tw, n, m, pen, a.s_cap, lane, gmask, &s);
+          if (r == kFwdOverflow) {
+            if (lane == 0) defer_pair(a, pair);
+          } else if (r == kFwdLimit) {
+            if (lane == 0) write_result(a, pair, 1, -1, 0, 0);
+          } else if (lane == 0) {
+            if (a.score_only) {
+              write_result(a, pair, 0, s * a.g, 0, 0);
+            } else {
+              const int64_t src = pair * kSlot;
+              const int nr = wfa_backtrace(view, n, m, pen, s, a.runs + src, kSlot);
+              if (nr == -1) {
+                defer_pair(a, pair);  // more runs than a slot holds
+              } else if (nr < 0) {
+                atomicExch(&a.ctrl->internal_error, 1);
+                write_result(a, pair, 0, s * a.g, 0, src);
+              } else {
+                write_result(a, pair, 0, s * a.g, nr, src);
+              }
+            }
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------- general kernel
+
+constexpr int kGeneralBlock = 128;
+
+__device__ __forceinline__ void overflow_pair(const AlignArgs& a, int64_t pair) {
+  const int idx = atomicAdd(&a.ctrl->overflow_count, 1);
+  a.overflow_list[idx] = (int32_t)pair;
+}
+
+__global__ void __launch_bounds__(kGeneralBlock) general_kernel(const AlignArgs a, int32_t* arena, long slot_ints,
+                                                                int nwarps) {
+  const int lane = threadIdx.x & 31;
+  const long wid = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (wid >= nwarps) return;  // the arena has exactly nwarps slots
+  int32_t* slot = arena + wid * slot_ints;
+  const ScaledPen pen{a.xs, a.oes, a.es};
+  const unsigned full = 0xffffffffu;
+  const volatile int32_t* count = &a.ctrl->defer_count;
+  for (;;) {
+    int idx = 0;
+    if (lane == 0) idx = atomicAdd(&a.ctrl->general_next, 1);
+    idx = __shfl_sync(full, idx, 0);
+    if (idx >= *count) break;
+    const int64_t pair = a.defer_list[idx];
+    const int n = a.plen[pair], m = a.tlen[pair];
+    const long nwp = (n + 31) / 32 + 1, nwt = (m + 31) / 32 + 1;
+    const long seq_ints = 2 * (nwp + nwt);
+    if (seq_ints + 64 > slot_ints) {
+      if (lane == 0) overflow_pair(a, pair);
+      __syncwarp();
+      continue;
+    }
+    uint64_t* pw = reinterpret_cast<uint64_t*>(slot);
+    uint64_t* tw = pw + nwp;
+    const bool okp = pack_seq<32>(a.pat + a.poff[pair], n, pw, lane, full);
+    const bool okt = pack_seq<32>(a.txt + a.toff[pair], m, tw, lane, full);
+    __syncwarp();
+    if (!(okp && okt)) {
+      if (lane == 0) write_result(a, pair, 2, -1, 0, 0);
+      __syncwarp();
+      continue;
+    }
+    ArenaView view{slot + seq_ints, slot + slot_ints, slot_ints - seq_ints};
+    int s = 0;
+    const int r = wfa_forward<32>(view, pw, tw, n, m, pen, a.s_cap, lane, full, &s);
+    if (lane == 0) {
+      if (r == kFwdOverflow) {
+        overflow_pair(a, pair);
+      } else if (r == kFwdLimit) {
+        write_result(a, pair, 1, -1, 0, 0);
+      } else if (a.score_only) {
+        write_result(a, pair, 0, s * a.g, 0, 0);
+      } else {
+        long bound = runs_bound_scaled(s, pen.x, pen.oe);
+        if (bound > (long)n + m + 1) bound = (long)n + m + 1;
+        const unsigned long long pos = atomicAdd(&a.ctrl->pool_top, (unsigned long long)bound);
+        if ((long long)(pos + bound) > a.pool_cap) {
+          atomicExch(&a.ctrl->pool_short, 1);
+          overflow_pair(a, pair);
+        } else {
+          const int64_t src = a.pool_base + (int64_t)pos;
+          const int nr = wfa_backtrace(view, n, m, pen, s, a.runs + src, (int)bound);
+          if (nr < 0) {
+            atomicExch(&a.ctrl->internal_error, 1);
+            write_result(a, pair, 0, s * a.g, 0, src);
+          } else {
+            write_result(a, pair, 0, s * a.g, nr, src);
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ----------------------------------------------------------------- helpers
+
+constexpr int kAuxBlock = 256;
+
+__device__ __forceinline__ long long warp_max64(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u > v ? u : v;
+  }
+  return v;
+}
+
+__global__ void validate_kernel(int64_t n, const int64_t* poff, const int32_t* plen, const int64_t* toff,
+                                const int32_t* tlen, Ctrl* ctrl) {
+  long long pe = 0, te = 0;
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int pl = plen[i], tl = tlen[i];
+    const long long po = poff[i], to = toff[i];
+    if (pl < 0 || tl < 0 || pl > ((1 << 28) - 1) || tl > ((1 << 28) - 1) || po < 0 || to < 0) {
+      bad = true;
+      continue;
+    }
+    pe = max(pe, po + pl);
+    te = max(te, to + tl);
+  }
+  pe = warp_max64(pe);
+  te = warp_max64(te);
+  if ((threadIdx.x & 31) == 0) {
+    if (pe) atomicMax(&ctrl->pat_extent, pe);
+    if (te) atomicMax(&ctrl->txt_extent, te);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(&ctrl->bad_input, 1);
+}
+
+// -------------------------------------------------------------------- scan
+
+constexpr int kScanBlock = 256;
+constexpr int kScanRows = 8;
+constexpr int kScanTile = kScanBlock * kScanRows;
+
+__device__ __forceinline__ int64_t scan_value(const int32_t* in, int64_t i, int64_t n, int kind) {
+  if (i >= n) return 0;
+  const int64_t v = in[i];
+  return kind == 0 ? v : (v + 31) / 32 + 1;
+}
+
+// exclusive scan across the block of v; *total = block sum
+__device__ __forceinline__ int64_t block_exclusive(int64_t v, int64_t* total) {
+  __shared__ int64_t wsum[kScanBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t w = lane < kScanBlock / 32 ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < kScanBlock / 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kScanBlock / 32) wsum[lane] = w;
+  }
+  __syncthreads();
+  const int64_t before = warp ? wsum[warp - 1] : 0;
+  *total = wsum[kScanBlock / 32 - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanBlock) scan_reduce(const int32_t* in, int64_t n, int kind, int64_t* tile_sums) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int64_t acc = 0;
+#pragma unroll
+  for (int r = 0; r < kScanRows; ++r) acc += scan_value(in, base + r * kScanBlock + threadIdx.x, n, kind);
+  int64_t total;
+  block_exclusive(acc, &total);
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanBlock) scan_tiles(int64_t* tile_sums, int64_t ntiles) {
+  int64_t carry = 0;
+  for (int64_t b = 0; b < ntiles; b += kScanBlock) {
+    const int64_t i = b + threadIdx.x;
+    const int64_t v = i < ntiles ? tile_sums[i] : 0;
+    int64_t total;
+    const int64_t ex = block_exclusive(v, &total);
+    if (i < ntiles) tile_sums[i] = carry + ex;
+    carry += total;
+  }
+}
+
+__global__ void __launch_bounds__(kScanBlock) scan_apply(const int32_t* in, int64_t n, int kind,
+                                                         const int64_t* tile_off, int64_t* out) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int64_t carry = tile_off[blockIdx.x];
+  for (int r = 0; r < kScanRows; ++r) {
+    const int64_t i = base + r * kScanBlock + threadIdx.x;
+    const int64_t v = scan_value(in, i, n, kind);
+    int64_t total;
+    const int64_t ex = block_exclusive(v, &total);
+    if (i <= n) out[i] = carry + ex;  // out[n] = grand total
+    carry += total;
+  }
+}
+
+// ---------------------------------------------------------------- compact
+
+__global__ void compact_kernel(int64_t n, const int32_t* nruns, const int64_t* run_src, const uint32_t* runs,
+                               const int64_t* off, uint32_t* out, int64_t cap) {
+  if (off[n] > cap) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int c = nruns[i];
+    if (c <= 0) continue;
+    const int64_t o = off[i], src = run_src[i];
+    for (int j = 0; j < c; ++j) out[o + j] = runs[src + c - 1 - j];
+  }
+}
+
+// ------------------------------------------------------------------- pack
+
+constexpr int kPackG = 8;
+
+__global__ void __launch_bounds__(kAuxBlock) pack_kernel(int64_t n, const char* seqs, const int64_t* off,
+                                                         const int32_t* len, const int64_t* woff, uint64_t* words,
+                                                         int8_t* invalid) {
+  const int lane = threadIdx.x & (kPackG - 1);
+  const unsigned gmask = group_mask(kPackG);
+  const int64_t gpb = blockDim.x / kPackG;
+  const int64_t total = (int64_t)gridDim.x * gpb;
+  for (int64_t i = (int64_t)blockIdx.x * gpb + threadIdx.x / kPackG; __any_sync(0xffffffffu, i < n); i += total) {
+    if (i < n) {
+      const bool ok = pack_seq<kPackG>(seqs + off[i], len[i], words + woff[i], lane, gmask);
+      if (lane == 0) invalid[i] = ok ? 0 : 1;
+    }
+    __syncwarp();
+  }
+}
+
+int sm_count(int device) {
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+  return v > 0 ? v : 1;
+}
+
+int aux_grid(int64_t n, int device) {
+  const int64_t want = (n + kAuxBlock - 1) / kAuxBlock;
+  const int64_t cap = (int64_t)sm_count(device) * 8;
+  return (int)(want < 1 ? 1 : want > cap ? cap : want);
+}
+
+int current_device() {
+  int d = 0;
+  cudaGetDevice(&d);
+  return d;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+
+cudaError_t short_plan(int device, ShortPlan* plan) {
+  auto k = short_kernel<kShortG, kShortLmax, kShortCells, kShortScap>;
+  const size_t smem = (size_t)(kShortBlock / kShortG) * kShortStride;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kShortBlock, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  plan->grid = sm_count(device) * per_sm;
+  plan->block = kShortBlock;
+  plan->smem = smem;
+  plan->max_len = kShortLmax;
+  return cudaSuccess;
+}
+
+cudaError_t launch_short(const AlignArgs& a, const ShortPlan& plan, cudaStream_t st) {
+  if (a.n <= 0) return cudaSuccess;
+  int grid = plan.grid;
+  const int64_t need = (a.n + (plan.block / kShortG) - 1) / (plan.block / kShortG);  // one group per pair
+  if (need < grid) grid = (int)need;
+  short_kernel<kShortG, kShortLmax, kShortCells, kShortScap><<<grid, plan.block, plan.smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_general(const AlignArgs& a, int32_t* arena, long slot_ints, int nwarps, cudaStream_t st) {
+  const int wpb = kGeneralBlock / 32;
+  const int grid = (nwarps + wpb - 1) / wpb;
+  general_kernel<<<grid, kGeneralBlock, 0, st>>>(a, arena, slot_ints, nwarps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate(int64_t n, const int64_t* poff, const int32_t* plen, const int64_t* toff,
+                            const int32_t* tlen, Ctrl* ctrl, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  validate_kernel<<<aux_grid(n, current_device()), kAuxBlock, 0, st>>>(n, poff, plen, toff, tlen, ctrl);
+  return cudaGetLastError();
+}
+
+int64_t scan_tmp_elems(int64_t n) { return (n + 1 + kScanTile - 1) / kScanTile + 1; }
+
+cudaError_t launch_scan(const int32_t* in, int64_t n, int kind, int64_t* out, int64_t* tmp, cudaStream_t st) {
+  // tiles cover indices 0..n (out[n] is the total)
+  const int64_t ntiles = (n + 1 + kScanTile - 1) / kScanTile;
+  scan_reduce<<<(unsigned)ntiles, kScanBlock, 0, st>>>(in, n, kind, tmp);
+  scan_tiles<<<1, kScanBlock, 0, st>>>(tmp, ntiles);
+  scan_apply<<<(unsigned)ntiles, kScanBlock, 0, st>>>(in, n, kind, tmp, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact(int64_t n, const int32_t* nruns, const int64_t* run_src, const uint32_t* runs,
+                           const int64_t* off, uint32_t* out, int64_t cap, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  compact_kernel<<<aux_grid(n, current_device()), kAuxBlock, 0, st>>>(n, nruns, run_src, runs, off, out, cap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(int64_t n, const char* seqs, const int64_t* off, const int32_t* len, const int64_t* woff,
+                        uint64_t* words, int8_t* invalid, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t groups_per_block = kAuxBlock / kPackG;
+  int64_t grid = (n + groups_per_block - 1) / groups_per_block;
+  const int64_t cap = (int64_t)sm_count(current_device()) * 16;
+  if (grid > cap) grid = cap;
+  pack_kernel<<<(unsigned)grid, kAuxBlock, 0, st>>>(n, seqs, off, len, woff, words, invalid);
+  return cudaGetLastError();
+}
+
+}  // namespace wfa

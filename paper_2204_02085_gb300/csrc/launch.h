@@ -1,0 +1,81 @@
+// launch.h -- host-side launchers of the library's kernels (C++ linkage,
+// internal to libwfa_gpu.so; the public interface is include/wfa_gpu.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace wfa {
+
+// Per-call device control block, zeroed before each batch.
+struct Ctrl {
+  int32_t bad_input;        // a length or offset out of range
+  int32_t internal_error;   // stored wavefronts inconsistent in a backtrace
+  int32_t defer_count;      // pairs handed to the arena kernel
+  int32_t general_next;     // work-queue head of the arena kernel
+  int32_t overflow_count;   // pairs the arena kernel could not fit
+  int32_t pool_short;       // the CIGAR pool ran out
+  unsigned long long pool_top;  // words used in the CIGAR pool
+  long long pat_extent;     // max(offset + length) over patterns
+  long long txt_extent;     // max(offset + length) over texts
+};
+
+struct AlignArgs {
+  int64_t n;
+  const char* pat;
+  const int64_t* poff;
+  const int32_t* plen;
+  const char* txt;
+  const int64_t* toff;
+  const int32_t* tlen;
+  int xs, oes, es;  // penalties divided by g
+  int g;            // gcd(x, o, e)
+  int s_cap;        // largest scaled score reported (INT_MAX: none)
+  int score_only;
+  int32_t* score;
+  int8_t* status;
+  int32_t* nruns;
+  int64_t* run_src;   // index of a pair's runs (last run first) in `runs`
+  uint32_t* runs;     // [n * kSlot] per-pair slots, then the pool
+  int64_t pool_base;  // index of the pool in `runs`
+  int64_t pool_cap;   // words in the pool
+  int32_t* defer_list;     // [n]
+  int32_t* overflow_list;  // [n]
+  Ctrl* ctrl;
+};
+
+constexpr int kSlot = 16;  // CIGAR runs a short-kernel pair may keep
+
+// Fused short-read kernel (pack + wavefronts in shared memory + backtrace).
+struct ShortPlan {
+  int grid, block;
+  size_t smem;
+  int max_len;
+};
+cudaError_t short_plan(int device, ShortPlan* plan);
+cudaError_t launch_short(const AlignArgs& a, const ShortPlan& plan, cudaStream_t st);
+
+// Arena kernel for pairs deferred by the short kernel: one warp per pair,
+// `nwarps` warps, each with slot_ints int32 of scratch.
+cudaError_t launch_general(const AlignArgs& a, int32_t* arena, long slot_ints, int nwarps, cudaStream_t st);
+
+// Validate lengths / offsets, record max(offset + length) extents.
+cudaError_t launch_validate(int64_t n, const int64_t* poff, const int32_t* plen, const int64_t* toff,
+                            const int32_t* tlen, Ctrl* ctrl, cudaStream_t st);
+
+// Exclusive prefix sums into out[0..n] (out[n] = total).  `kind`:
+//   0: values in[i];  1: ceil(in[i]/32) + 1 (packed words per sequence).
+// tmp must hold scan_tmp_elems(n) int64.
+int64_t scan_tmp_elems(int64_t n);
+cudaError_t launch_scan(const int32_t* in, int64_t n, int kind, int64_t* out, int64_t* tmp, cudaStream_t st);
+
+// CIGAR compaction: pair i's runs (stored last first at runs[run_src[i]])
+// to out[off[i] .. off[i+1]) in order; writes nothing if off[n] > cap.
+cudaError_t launch_compact(int64_t n, const int32_t* nruns, const int64_t* run_src, const uint32_t* runs,
+                           const int64_t* off, uint32_t* out, int64_t cap, cudaStream_t st);
+
+// Standalone packer: sequence i -> words[woff[i] ..], invalid[i].
+cudaError_t launch_pack(int64_t n, const char* seqs, const int64_t* off, const int32_t* len, const int64_t* woff,
+                        uint64_t* words, int8_t* invalid, cudaStream_t st);
+
+}  // namespace wfa

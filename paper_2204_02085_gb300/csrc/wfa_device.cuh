@@ -1,0 +1,437 @@
+// wfa_device.cuh -- device building blocks of the batched gap-affine WFA.
+//
+// The method is the wavefront algorithm (WFA) the paper runs unmodified on
+// every read pair (Sec. I).  With offsets h (text position) on diagonals
+// k = h - v (v = pattern position), and penalties scaled by
+// g = gcd(x, o, e) so that only integer scores s = 0, 1, 2, ... occur:
+//
+//   I_s[k] = max(M_{s-o-e}[k-1], I_{s-e}[k-1]) + 1        (consumes text)
+//   D_s[k] = max(M_{s-o-e}[k+1], D_{s-e}[k+1])            (consumes pattern)
+//   M_s[k] = extend(max(M_{s-x}[k] + 1, I_s[k], D_s[k]))
+//   M_0[0] = extend(0);   score = g * (first s with M_s[m-n] == m)
+//
+// A candidate past either sequence end is dropped before the maximum.
+// extend() advances h while pattern[h-k] == text[h]; here it compares 32
+// bases at a time: XOR of two 2-bit packed 64-bit windows, count leading
+// zeros, halve.
+//
+// A "group" of G lanes (G divides 32) owns one pair; lanes stride over the
+// diagonals of a wavefront.  The wavefronts live behind a View: shared
+// memory (int16 offsets) for short reads, a slice of a global scratch arena
+// (int32 offsets) otherwise.  The backtrace walks the stored wavefronts
+// back from the end with the library's tie-break and emits run-length
+// CIGAR words, last run first.
+#pragma once
+
+#include <cstdint>
+#include <climits>
+
+namespace wfa {
+
+// ------------------------------------------------------------------ common
+
+constexpr int kOpM = 0, kOpX = 1, kOpI = 2, kOpD = 3;
+
+// forward-pass outcomes
+constexpr int kFwdOk = 0, kFwdLimit = 1, kFwdOverflow = 3;
+
+// missing offset: negative, and stays negative after +1 (offsets are
+// bounded by the sequence length, far from these values)
+constexpr int kNull16 = -16384;
+constexpr int kNull32 = -(1 << 30);
+
+template <typename Off> struct NullOf;
+template <> struct NullOf<int16_t> { static constexpr int value = kNull16; };
+template <> struct NullOf<int32_t> { static constexpr int value = kNull32; };
+
+struct ScaledPen {
+  int x, oe, e;  // penalties divided by g; oe = o + e
+};
+
+__device__ __forceinline__ unsigned group_mask(int G) {
+  const unsigned lane = threadIdx.x & 31u;
+  return G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(unsigned)(G - 1)));
+}
+
+// ------------------------------------------------------------------ packing
+
+// 16 ASCII bytes -> 16 two-bit codes (A0 C1 G2 T3, either case), first byte
+// in the top bits.  Bytes with chunk-local index in [lo_b, hi_b) are
+// validated; *bad is set if one of them is not A/C/G/T.
+__device__ __forceinline__ uint32_t code16(uint4 v, int lo_b, int hi_b, bool* bad) {
+  const uint32_t q[4] = {v.x, v.y, v.z, v.w};
+  uint32_t code = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t w = q[i];
+    // ((b >> 1) ^ (b >> 2)) & 3 maps A,C,G,T and a,c,g,t to 0,1,2,3
+    const uint32_t c = ((w >> 1) ^ (w >> 2)) & 0x03030303u;
+    const uint32_t u = w & 0xDFDFDFDFu;  // fold case
+    const uint32_t ok = __vcmpeq4(u, 0x41414141u) | __vcmpeq4(u, 0x43434343u) |
+                        __vcmpeq4(u, 0x47474747u) | __vcmpeq4(u, 0x54545454u);
+    // bytes of this quad inside [lo_b, hi_b)
+    const int b0 = 4 * i;
+    const int lo = max(lo_b - b0, 0), hi = min(hi_b - b0, 4);
+    uint32_t in = 0;
+    if (hi > lo) in = (hi >= 4 ? 0xffffffffu : ((1u << (8 * hi)) - 1u)) & ~((1u << (8 * lo)) - 1u);
+    if (~ok & in) *bad = true;
+    const uint32_t p8 = ((c & 3u) << 6) | ((c >> 4) & 0x30u) | ((c >> 14) & 0x0Cu) | ((c >> 24) & 3u);
+    code = (code << 8) | p8;
+  }
+  return code;
+}
+
+// Packed word w of the sequence at `seq` (len bases): bases 32w .. 32w+31
+// (fewer at the end, zero-filled).  Loads only the 16-byte aligned chunks
+// that hold at least one of those bases, so it never touches a chunk
+// without a byte of the sequence (a 16-byte aligned chunk never straddles a
+// page).
+__device__ __forceinline__ uint64_t pack_word(const char* __restrict__ seq, int len, int w, bool* bad) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(seq) + 32u * (uintptr_t)w;
+  const int nb = min(32, len - 32 * w);  // bases in this word, >= 1
+  const uintptr_t a0 = a & ~(uintptr_t)15;
+  const int head = (int)(a - a0);
+  const int nch = (head + nb + 15) >> 4;  // 2 or 3 chunks (1 if nb small)
+  uint32_t c[3] = {0u, 0u, 0u};
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    if (j < nch) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(a0 + 16u * j));
+      const int lo_b = head - 16 * j, hi_b = head + nb - 16 * j;
+      c[j] = code16(v, lo_b, hi_b, bad);
+    }
+  }
+  const int r = 2 * head;  // bits to drop from the front
+  const uint32_t hi = __funnelshift_l(c[1], c[0], r);
+  const uint32_t lo = __funnelshift_l(c[2], c[1], r);
+  uint64_t word = ((uint64_t)hi << 32) | lo;
+  if (nb < 32) word &= ~0ull << (64 - 2 * nb);
+  return word;
+}
+
+// The group packs one sequence into out[0 .. ceil(len/32)] (last word = pad
+// 0).  Returns, uniformly across the group, whether every byte is valid.
+template <int G>
+__device__ __forceinline__ bool pack_seq(const char* __restrict__ seq, int len, uint64_t* out, int lane,
+                                         unsigned gmask) {
+  const int nwords = (len + 31) >> 5;
+  bool bad = false;
+  for (int w = lane; w <= nwords; w += G) out[w] = (w < nwords) ? pack_word(seq, len, w, &bad) : 0ull;
+  return __any_sync(gmask, bad) == 0;
+}
+
+// ----------------------------------------------------------------- extend
+
+// 32 bases starting at base position pos of a packed sequence (reads words
+// pos/32 and pos/32 + 1; the pad word makes the second one exist).
+__device__ __forceinline__ uint64_t window64(const uint64_t* W, int pos) {
+  const int w = pos >> 5;
+  const int sh = (pos & 31) << 1;
+  const uint64_t a = W[w], b = W[w + 1];
+  return (a << sh) | ((b >> 1) >> (63 - sh));
+}
+
+// Advance offset h on diagonal k while pattern[h-k] == text[h]; h is a
+// valid offset (0 <= h <= m, 0 <= h-k <= n).
+__device__ __forceinline__ int extend_diag(const uint64_t* pw, const uint64_t* tw, int n, int m, int k, int h) {
+  for (;;) {
+    const int v = h - k;
+    const int rem = min(n - v, m - h);
+    if (rem <= 0) break;
+    const uint64_t d = window64(pw, v) ^ window64(tw, h);
+    const int eq = d ? (__clzll(d) >> 1) : 32;
+    if (eq >= rem) {
+      h += rem;
+      break;
+    }
+    h += eq;
+    if (eq < 32) break;
+  }
+  return h;
+}
+
+// ------------------------------------------------------------------ views
+
+// Geometry of one stored wavefront: diagonals [lo, lo + w), cells at `base`
+// (w == 0: component absent).
+struct Geo {
+  int lo, w, base;
+};
+
+// Shared-memory wavefronts: int16 offsets, per-score metadata arrays.
+struct SmemView {
+  using Off = int16_t;
+  int16_t *M, *I, *D;            // cells [cell_cap]
+  int16_t *lo, *hi, *base;       // per score [score_cap + 1]
+  uint8_t* ex;                   // per score: bit0 M, bit1 I, bit2 D exist
+  int cell_cap, score_cap;
+
+  __device__ __forceinline__ int lo_of(int s) const { return lo[s]; }
+  __device__ __forceinline__ int hi_of(int s) const { return hi[s]; }
+  __device__ __forceinline__ int base_of(int s) const { return base[s]; }
+  __device__ __forceinline__ int ex_of(int s) const { return ex[s]; }
+  __device__ __forceinline__ void set_meta(int s, int l, int h, int b, int e) {
+    lo[s] = (int16_t)l; hi[s] = (int16_t)h; base[s] = (int16_t)b; ex[s] = (uint8_t)e;
+  }
+  __device__ __forceinline__ void set_absent(int s) { ex[s] = 0; }
+  // room for the metadata of score s
+  __device__ __forceinline__ bool score_ok(int s, int top) const { (void)top; return s <= score_cap; }
+  // reserve `w` cells for score s; `top` counts cells in use
+  __device__ __forceinline__ bool alloc(int s, int w, int& top, int& b) const {
+    if (s > score_cap || top + w > cell_cap) return false;
+    b = top;
+    top += w;
+    return true;
+  }
+  __device__ __forceinline__ void release(int b, int& top) const { top = b; }
+  __device__ __forceinline__ int getM(const Geo& g, int i) const { return M[g.base + i]; }
+  __device__ __forceinline__ int getI(const Geo& g, int i) const { return I[g.base + i]; }
+  __device__ __forceinline__ int getD(const Geo& g, int i) const { return D[g.base + i]; }
+  __device__ __forceinline__ void put(int b, int w, int i, int mv, int iv, int dv) {
+    (void)w;
+    M[b + i] = (int16_t)mv; I[b + i] = (int16_t)iv; D[b + i] = (int16_t)dv;
+  }
+};
+
+// Arena wavefronts: int32 offsets.  Per-score metadata (4 ints: lo, hi,
+// base, exist bits) grows up from `meta`; each wavefront's block
+// [M w][I w][D w] grows down from `end`; `base` counts ints from `end` to
+// the block start.  The two meet at `cap_ints`.
+struct ArenaView {
+  using Off = int32_t;
+  int32_t* meta;
+  int32_t* end;
+  long cap_ints;
+
+  __device__ __forceinline__ int lo_of(int s) const { return meta[4 * s]; }
+  __device__ __forceinline__ int hi_of(int s) const { return meta[4 * s + 1]; }
+  __device__ __forceinline__ int base_of(int s) const { return meta[4 * s + 2]; }
+  __device__ __forceinline__ int ex_of(int s) const { return meta[4 * s + 3]; }
+  __device__ __forceinline__ void set_meta(int s, int l, int h, int b, int e) {
+    meta[4 * s] = l; meta[4 * s + 1] = h; meta[4 * s + 2] = b; meta[4 * s + 3] = e;
+  }
+  __device__ __forceinline__ void set_absent(int s) { meta[4 * s + 3] = 0; }
+  __device__ __forceinline__ bool score_ok(int s, int top) const { return 4L * (s + 1) + (long)top <= cap_ints; }
+  __device__ __forceinline__ bool alloc(int s, int w, int& top, int& b) const {
+    const long need = 4L * (s + 1) + (long)top + 3L * w;
+    if (need > cap_ints || (long)top + 3L * w > INT_MAX) return false;
+    top += 3 * w;
+    b = top;
+    return true;
+  }
+  __device__ __forceinline__ void release(int b, int& top) const { (void)b; (void)top; }
+  __device__ __forceinline__ const int32_t* blk(const Geo& g) const { return end - g.base; }
+  __device__ __forceinline__ int getM(const Geo& g, int i) const { return blk(g)[i]; }
+  __device__ __forceinline__ int getI(const Geo& g, int i) const { return blk(g)[g.w + i]; }
+  __device__ __forceinline__ int getD(const Geo& g, int i) const { return blk(g)[2 * g.w + i]; }
+  __device__ __forceinline__ void put(int b, int w, int i, int mv, int iv, int dv) {
+    int32_t* p = end - b;
+    p[i] = mv; p[w + i] = iv; p[2 * w + i] = dv;
+  }
+};
+
+// geometry of component `bit` of stored score s (w = 0 if absent)
+template <class V>
+__device__ __forceinline__ Geo geo_of(const V& view, int s, int bit) {
+  Geo g{0, 0, 0};
+  if (s >= 0) {
+    const int e = view.ex_of(s);
+    if (e & bit) {
+      g.lo = view.lo_of(s);
+      g.w = view.hi_of(s) - g.lo + 1;
+      g.base = view.base_of(s);
+    }
+  }
+  return g;
+}
+
+template <class V, int WHICH>
+__device__ __forceinline__ int get_off(const V& view, const Geo& g, int k, int null_v) {
+  const unsigned i = (unsigned)(k - g.lo);
+  if (i >= (unsigned)g.w) return null_v;
+  return WHICH == 0 ? view.getM(g, (int)i) : WHICH == 1 ? view.getI(g, (int)i) : view.getD(g, (int)i);
+}
+
+// ------------------------------------------------------------ forward pass
+
+// Runs the score loop for one pair on a group of G lanes.  Returns kFwdOk
+// with *s_out = scaled score, kFwdLimit when the scaled score would exceed
+// s_cap (the caller's max_score bound), or kFwdOverflow when the view runs
+// out of room.  Every lane returns the same value.
+template <int G, class V>
+__device__ int wfa_forward(V& view, const uint64_t* pw, const uint64_t* tw, int n, int m, ScaledPen p, int s_cap,
+                           int lane, unsigned gmask, int* s_out) {
+  using Off = typename V::Off;
+  constexpr int NUL = NullOf<Off>::value;
+  const int kf = m - n;
+  int top = 0, b0 = 0;
+  if (!view.alloc(0, 1, top, b0)) return kFwdOverflow;
+  if (lane == 0) {
+    const int h = extend_diag(pw, tw, n, m, 0, 0);
+    view.put(b0, 1, 0, h, NUL, NUL);
+    view.set_meta(0, 0, 0, b0, 1);
+  }
+  __syncwarp(gmask);
+  if (kf == 0 && view.getM(Geo{0, 1, b0}, 0) == m) {
+    *s_out = 0;
+    return kFwdOk;
+  }
+  for (int s = 1;; ++s) {
+    if (s > s_cap) return kFwdLimit;
+    if (!view.score_ok(s, top)) return kFwdOverflow;
+    const Geo gx = geo_of(view, s - p.x, 1);
+    const Geo go = geo_of(view, s - p.oe, 1);
+    const Geo gi = geo_of(view, s - p.e, 2);
+    const Geo gd = geo_of(view, s - p.e, 4);
+    int lo = INT_MAX, hi = INT_MIN;
+    if (gx.w) { lo = min(lo, gx.lo); hi = max(hi, gx.lo + gx.w - 1); }
+    if (go.w) { lo = min(lo, go.lo - 1); hi = max(hi, go.lo + go.w); }
+    if (gi.w) { lo = min(lo, gi.lo - 1); hi = max(hi, gi.lo + gi.w); }
+    if (gd.w) { lo = min(lo, gd.lo - 1); hi = max(hi, gd.lo + gd.w); }
+    lo = max(lo, -n);  // diagonals outside [-n, m] hold no valid offset
+    hi = min(hi, m);
+    if (lo > hi) {
+      if (lane == 0) view.set_absent(s);
+      __syncwarp(gmask);
+      continue;
+    }
+    const int w = hi - lo + 1;
+    int b = 0;
+    if (!view.alloc(s, w, top, b)) return kFwdOverflow;
+    bool anyM = false, anyI = false, anyD = false;
+    for (int k = lo + lane; k <= hi; k += G) {
+      const int mx = get_off<V, 0>(view, gx, k, NUL);
+      const int ml = get_off<V, 0>(view, go, k - 1, NUL);
+      const int mr = get_off<V, 0>(view, go, k + 1, NUL);
+      const int il = get_off<V, 1>(view, gi, k - 1, NUL);
+      const int dr = get_off<V, 2>(view, gd, k + 1, NUL);
+      int iv = max(ml, il) + 1;
+      if (iv < 0 || iv > m) iv = NUL;
+      int dv = max(mr, dr);
+      if (dv < 0 || dv - k > n) dv = NUL;
+      int xv = mx + 1;
+      if (mx < 0 || xv > m || xv - k > n) xv = NUL;
+      int mv = max(xv, max(iv, dv));
+      if (mv >= 0) {
+        mv = extend_diag(pw, tw, n, m, k, mv);
+        anyM = true;
+      } else {
+        mv = NUL;
+      }
+      anyI |= iv >= 0;
+      anyD |= dv >= 0;
+      view.put(b, w, k - lo, mv, iv, dv);
+    }
+    const int exbits = (__any_sync(gmask, anyM) ? 1 : 0) | (__any_sync(gmask, anyI) ? 2 : 0) |
+                       (__any_sync(gmask, anyD) ? 4 : 0);
+    if (exbits == 0) view.release(b, top);
+    if (lane == 0) view.set_meta(s, lo, hi, b, exbits);
+    __syncwarp(gmask);
+    if ((exbits & 1) && kf >= lo && kf <= hi && view.getM(Geo{lo, w, b}, kf - lo) == m) {
+      *s_out = s;
+      return kFwdOk;
+    }
+  }
+}
+
+// -------------------------------------------------------------- backtrace
+
+// Walk back from (M, s_final, m-n, m) and write run-length CIGAR words into
+// runs[0 ..), LAST run first.  Returns the number of runs, -1 if more than
+// cap runs are needed, -2 if the stored wavefronts are inconsistent (which
+// the forward pass never produces).  Single lane.
+template <class V>
+__device__ int wfa_backtrace(const V& view, int n, int m, ScaledPen p, int s_final, uint32_t* runs, int cap) {
+  using Off = typename V::Off;
+  constexpr int NUL = NullOf<Off>::value;
+  int s = s_final, k = m - n, h = m, state = kOpM;
+  uint32_t cur_op = 0xF, cur_len = 0;
+  int nr = 0;
+  long guard = 2L * ((long)n + (long)m) + 4;
+  bool over = false;
+  auto emit = [&](uint32_t op, uint32_t len) {
+    if (len == 0) return;
+    if (op == cur_op) {
+      cur_len += len;
+      return;
+    }
+    if (cur_len) {
+      if (nr < cap) runs[nr] = (cur_len << 4) | cur_op; else over = true;
+      ++nr;
+    }
+    cur_op = op;
+    cur_len = len;
+  };
+  while (guard-- > 0) {
+    if (s < 0) return -2;
+    if (state == kOpM) {
+      if (s == 0) {
+        if (k != 0) return -2;
+        emit(kOpM, (uint32_t)h);
+        break;
+      }
+      int xv = get_off<V, 0>(view, geo_of(view, s - p.x, 1), k, NUL);
+      if (xv >= 0) {
+        xv += 1;
+        if (xv > m || xv - k > n) xv = NUL;
+      } else {
+        xv = NUL;
+      }
+      const int iv = get_off<V, 1>(view, geo_of(view, s, 2), k, NUL);
+      const int dv = get_off<V, 2>(view, geo_of(view, s, 4), k, NUL);
+      int pick, c;
+      if (xv >= 0 && xv >= iv && xv >= dv) {
+        pick = kOpX; c = xv;
+      } else if (iv >= 0 && iv >= dv) {
+        pick = kOpI; c = iv;
+      } else if (dv >= 0) {
+        pick = kOpD; c = dv;
+      } else {
+        return -2;
+      }
+      if (c > h) return -2;
+      emit(kOpM, (uint32_t)(h - c));
+      if (pick == kOpX) {
+        emit(kOpX, 1);
+        s -= p.x;
+        h = c - 1;
+      } else {
+        state = pick;
+        h = c;
+      }
+    } else if (state == kOpI) {
+      emit(kOpI, 1);
+      if (get_off<V, 1>(view, geo_of(view, s - p.e, 2), k - 1, NUL) == h - 1) {
+        s -= p.e;
+      } else {
+        s -= p.oe;
+        state = kOpM;
+      }
+      k -= 1;
+      h -= 1;
+    } else {
+      emit(kOpD, 1);
+      if (get_off<V, 2>(view, geo_of(view, s - p.e, 4), k + 1, NUL) == h) {
+        s -= p.e;
+      } else {
+        s -= p.oe;
+        state = kOpM;
+      }
+      k += 1;
+    }
+  }
+  if (guard < 0) return -2;
+  if (cur_len) {
+    if (nr < cap) runs[nr] = (cur_len << 4) | cur_op; else over = true;
+    ++nr;
+  }
+  return over ? -1 : nr;
+}
+
+// largest number of CIGAR runs of an alignment of scaled score s
+__host__ __device__ __forceinline__ long runs_bound_scaled(long s, int x, int oe) {
+  const int mn = x < oe ? x : oe;
+  return 2L * (s / mn) + 1;
+}
+
+}  // namespace wfa

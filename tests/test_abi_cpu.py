@@ -1,0 +1,121 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function
+include/wfa_gpu.h declares; host-only entry points behave as documented.
+No compute call is made here (no GPU is needed)."""
+
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "wfa_gpu.h")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_2204_02085_gb300 import build
+
+    build.build()
+    import paper_2204_02085_gb300 as p
+
+    p.load()
+    return p
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(wfa_gpu_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("wfa_gpu_create", "wfa_gpu_align_batch", "wfa_gpu_destroy", "wfa_gpu_cigar_bound",
+                     "wfa_gpu_strerror"):
+        assert required in names
+
+
+def test_exports_every_declared_symbol(pkg):
+    lib = pkg.load()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert sorted(pkg.EXPORTS) == declared_functions()
+    out = subprocess.run(["nm", "-D", "--defined-only", pkg.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (wfa_gpu_\w+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_library_targets_sm103a(pkg):
+    from paper_2204_02085_gb300 import build
+
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_strerror(pkg):
+    for code in (0, -1, -2, -3, -4, -5, 12345):
+        s = pkg.wfa_gpu_strerror(code)
+        assert isinstance(s, str) and s
+    assert pkg.wfa_gpu_strerror(-4).startswith("CIGAR")
+
+
+def test_cigar_bound(pkg):
+    pen = (4, 6, 2)
+    assert pkg.wfa_gpu_cigar_bound(0, 0, pen, 0) == 0
+    assert pkg.wfa_gpu_cigar_bound(-1, 5, pen, 0) == -1
+    assert pkg.wfa_gpu_cigar_bound(5, 5, (0, 6, 2), 0) == -1
+    assert pkg.wfa_gpu_cigar_bound(5, 5, (4, -1, 2), 0) == -1
+    assert pkg.wfa_gpu_cigar_bound(5, 5, (4, 6, 0), 0) == -1
+    # never more runs than columns
+    assert pkg.wfa_gpu_cigar_bound(100, 100, pen, 0) <= 200
+    # with a score bound: 2*floor(s/min(x, o+e)) + 1
+    assert pkg.wfa_gpu_cigar_bound(100, 100, pen, 16) == 2 * (16 // 4) + 1
+    assert pkg.wfa_gpu_cigar_bound(100, 100, (16, 6, 2), 16) == 2 * (16 // 8) + 1
+    assert 1 <= pkg.wfa_gpu_cigar_bound(10, 0, pen, 0) <= 10
+
+
+def test_cigar_bound_covers_oracle_alignments(pkg, oracle_mod):
+    """The bound holds for every canonical alignment of random pairs."""
+    from paper_2204_02085_gb300 import synth
+
+    b = synth.random_pairs(200, 0, 60, seed=13)
+    for pen in ((4, 6, 2), (1, 0, 1), (16, 6, 2), (2, 3, 1)):
+        for i in range(b.n):
+            p, t = b.pair(i)
+            st, s, ops = oracle_mod.wfa(p, t, pen)
+            runs = len(oracle_mod.ops_to_runs(ops))
+            assert runs <= pkg.wfa_gpu_cigar_bound(len(p), len(t), pen, 0)
+            assert runs <= pkg.wfa_gpu_cigar_bound(len(p), len(t), pen, s if s > 0 else 1) or s == 0
+
+
+def test_null_arguments_rejected_without_device(pkg):
+    lib = pkg.load()
+    assert lib.wfa_gpu_create(None, 0, 0) == pkg.WFA_GPU_EINVAL
+    h = ctypes.c_void_p()
+    assert lib.wfa_gpu_create(ctypes.byref(h), -1, 0) == pkg.WFA_GPU_EINVAL
+    assert pkg.wfa_gpu_align_batch(None, 1, None, None, None, None, None, None, (4, 6, 2), 0, 0, None, None,
+                                   None, 0, None) == pkg.WFA_GPU_EINVAL
+    assert pkg.wfa_gpu_set_stream(None, None) == pkg.WFA_GPU_EINVAL
+    assert lib.wfa_gpu_last_timing(None, None) == pkg.WFA_GPU_EINVAL
+    pkg.wfa_gpu_destroy(None)  # NULL-safe
+
+
+def test_create_without_gpu_fails_cleanly(pkg):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    rc, h = pkg.wfa_gpu_create(0, 0)
+    assert rc == pkg.WFA_GPU_ECUDA and h is None
+
+
+def test_product_never_imports_the_oracle():
+    """The library package and the C sources do not reference oracle/."""
+    pkg_dir = os.path.join(ROOT, "paper_2204_02085_gb300")
+    for dirpath, _, files in os.walk(pkg_dir):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "wfa_oracle" not in text, f

@@ -1,0 +1,298 @@
+"""Parity of the CUDA path with the CPU oracle, through the C ABI.
+
+Integer results must be bit-exact: scores, per-pair status, CIGAR offsets
+and CIGAR words (same canonical tie-break).  Inputs are seeded synthetic
+pairs shaped like the paper's workload (100 bp reads, E = 2 % / 4 %,
+Sec. II) plus sizes that span several kernel tiles, ragged lengths, the
+arena (long / high-score) path and the degenerate cases.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+PENALTY_SETS = [(4, 6, 2), (1, 0, 1), (2, 3, 1), (5, 1, 3), (3, 2, 2), (16, 6, 2)]
+NCPU = os.cpu_count() or 4
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_2204_02085_gb300 import build
+
+    build.build()
+    import paper_2204_02085_gb300 as p
+
+    return p
+
+
+@pytest.fixture(scope="module")
+def al(pkg):
+    a = pkg.Aligner(0)
+    yield a
+    a.close()
+
+
+def oracle_run(oracle, batch, pen, max_score=0, want_cigar=True):
+    return oracle.wfa_batch(batch, pen, max_score=max_score, want_cigar=want_cigar, nthreads=NCPU)
+
+
+def assert_same(got, want, score_only=False):
+    s, st, w, off = got
+    os_, ost, ow, ooff = want
+    bad = np.nonzero((s != os_) | (st != ost))[0]
+    assert bad.size == 0, "first mismatching pairs %s: gpu %s/%s oracle %s/%s" % (
+        bad[:5], s[bad[:5]], st[bad[:5]], os_[bad[:5]], ost[bad[:5]])
+    if not score_only:
+        assert np.array_equal(off, ooff), "CIGAR offsets differ"
+        assert np.array_equal(w, ow), "CIGAR words differ"
+
+
+def check(al, oracle, batch, pen, max_score=0, score_only=False, use_offsets=True):
+    got = al.align(batch, pen, max_score=max_score, score_only=score_only, use_offsets=use_offsets)
+    want = oracle_run(oracle, batch, pen, max_score=max_score, want_cigar=not score_only)
+    assert_same(got, want, score_only)
+    return got
+
+
+def test_config1_small_plain(al, oracle_mod):
+    """1,000 pairs, seed 0, 100 bp, exactly 2 edits, penalties 4/6/2."""
+    from paper_2204_02085_gb300 import synth
+
+    b = synth.uniform_reads(1000, 100, 2, seed=0)
+    s, st, w, off = check(al, oracle_mod, b, (4, 6, 2))
+    assert np.all(st == 0) and s.max() <= 16
+
+
+@pytest.mark.parametrize("edits", [4, 10, 25])
+def test_higher_edit_rates(al, oracle_mod, edits):
+    """More edits push wavefronts past the shared-memory budget: those pairs
+    move to the arena kernel and must still match."""
+    from paper_2204_02085_gb300 import synth
+
+    b = synth.uniform_reads(3000, 100, edits, seed=edits)
+    check(al, oracle_mod, b, (4, 6, 2))
+    if edits >= 10:
+        assert al.timing()["deferred_pairs"] >= 0
+
+
+@pytest.mark.parametrize("pen", PENALTY_SETS)
+def test_penalty_sets(al, oracle_mod, pen):
+    from paper_2204_02085_gb300 import synth
+
+    b = synth.uniform_reads(1500, 100, 4, seed=sum(pen))
+    check(al, oracle_mod, b, pen)
+
+
+def test_ragged_lengths_and_unrelated(al, oracle_mod):
+    """Lengths 0..600 (both sides of the 256-base short-kernel limit),
+    related and unrelated pairs, mixed case."""
+    from paper_2204_02085_gb300 import synth
+
+    rel = synth.random_pairs(400, 0, 600, seed=31, edit_rate=0.05)
+    unrel = synth.random_pairs(150, 0, 300, seed=32, alphabet=b"ACGTacgt")
+    pairs = [rel.pair(i) for i in range(rel.n)] + [unrel.pair(i) for i in range(unrel.n)]
+    b = synth.from_pairs(pairs)
+    for pen in ((4, 6, 2), (1, 0, 1), (16, 6, 2)):
+        check(al, oracle_mod, b, pen)
+
+
+def test_edge_cases(al, oracle_mod):
+    from paper_2204_02085_gb300 import synth
+
+    A = b"ACGT" * 80
+    pairs = [(b"", b""), (b"", b"A"), (b"G", b""), (b"", A[:256]), (A[:256], b""), (b"A", b"A"), (b"A", b"C"),
+             (b"AAAA", b"AAA"), (b"GATTACA", b"GATACA"), (b"acgt", b"ACGT"), (b"ACGN", b"ACGT"),
+             (b"ACGT", b"AC-T"), (b"ACGT\x00", b"ACGT"), (A[:31], A[:31]), (A[:32], A[:32]), (A[:33], A[:33]),
+             (A[:63], A[:64]), (A[:64], A[:65]), (A[:255], A[:256]), (A[:256], A[:256]), (A[:257], A[:256]),
+             (A[:256], A[:257]), (A[:300], A[:290]), (b"T" * 200, b"A" * 200), (b"A" * 256, b"C" * 256)]
+    b = synth.from_pairs(pairs)
+    for pen in PENALTY_SETS:
+        check(al, oracle_mod, b, pen)
+    s, st, _, _ = al.align(b, (4, 6, 2))
+    assert st[10] == 2 and st[11] == 2 and st[12] == 2 and s[10] == -1
+
+
+def test_max_score_boundary(al, oracle_mod):
+    from paper_2204_02085_gb300 import synth
+
+    b = synth.uniform_reads(2000, 100, 4, seed=7)
+    for ms in (1, 4, 8, 12, 16, 17, 30):
+        got = check(al, oracle_mod, b, (4, 6, 2), max_score=ms)
+        s, st = got[0], got[1]
+        assert np.all(s[st == 0] <= ms) and np.all(s[st == 1] == -1)
+
+
+def test_score_only_and_null_offsets(al, oracle_mod):
+    from paper_2204_02085_gb300 import synth
+
+    b = synth.random_pairs(300, 50, 400, seed=41, edit_rate=0.04)
+    check(al, oracle_mod, b, (4, 6, 2), score_only=True)
+    check(al, oracle_mod, b, (4, 6, 2), use_offsets=False)
+
+
+def test_shuffled_offsets(al, oracle_mod):
+    """Sequences need not be back to back or in pair order."""
+    from paper_2204_02085_gb300 import synth
+
+    b = synth.uniform_reads(500, 100, 3, seed=43)
+    perm = np.random.default_rng(0).permutation(b.n)
+    pat = b"".join(b.pair(int(i))[0] + b"N" for i in perm)  # gaps of one junk byte
+    txt = b"".join(b"xx" + b.pair(int(i))[1] for i in perm)
+    poff = np.zeros(b.n, np.int64)
+    toff = np.zeros(b.n, np.int64)
+    po = to = 0
+    for i in perm:
+        p, t = b.pair(int(i))
+        poff[i] = po
+        toff[i] = to + 2
+        po += len(p) + 1
+        to += len(t) + 2
+    shuffled = synth.Batch(np.frombuffer(pat, np.uint8).copy(), poff, b.pattern_lengths.copy(),
+                           np.frombuffer(txt, np.uint8).copy(), toff, b.text_lengths.copy())
+    got = al.align(shuffled, (4, 6, 2))
+    want = oracle_run(oracle_mod, b, (4, 6, 2))
+    assert_same(got, want)
+
+
+def test_cigar_capacity(pkg, al, oracle_mod):
+    from paper_2204_02085_gb300 import synth
+
+    b = synth.uniform_reads(200, 100, 2, seed=44)
+    want = oracle_run(oracle_mod, b, (4, 6, 2))
+    total = int(want[3][-1])
+    with pytest.raises(pkg.WfaGpuError) as ei:
+        al.align(b, (4, 6, 2), cigar_capacity=total - 1)
+    assert ei.value.code == pkg.WFA_GPU_ECIGAR_CAPACITY
+    got = al.align(b, (4, 6, 2), cigar_capacity=total)
+    assert_same(got, want)
+
+
+def test_small_arena_retries(pkg, oracle_mod):
+    """A tiny scratch arena forces arena-kernel retries with fewer, larger
+    slots; results are unchanged.  A pair that cannot fit even the whole
+    arena gives ENOMEM."""
+    from paper_2204_02085_gb300 import synth
+
+    b = synth.random_pairs(60, 200, 700, seed=45)
+    with pkg.Aligner(0, scratch_bytes=4 << 20) as small:
+        got = small.align(b, (4, 6, 2))
+        assert_same(got, oracle_run(oracle_mod, b, (4, 6, 2)))
+    big = synth.random_pairs(2, 3000, 3000, seed=46)
+    with pkg.Aligner(0, scratch_bytes=64 << 10) as tiny:
+        with pytest.raises(pkg.WfaGpuError) as ei:
+            tiny.align(big, (4, 6, 2))
+        assert ei.value.code == pkg.WFA_GPU_ENOMEM
+
+
+def test_device_pointers_match_host_path(pkg, al, oracle_mod):
+    import torch
+
+    from paper_2204_02085_gb300 import synth
+
+    b = synth.random_pairs(700, 0, 300, seed=47, edit_rate=0.03)
+    host = al.align(b, (4, 6, 2))
+    dev = torch.device("cuda:0")
+    al.set_stream(torch.cuda.current_stream(dev))
+    try:
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        n = b.n
+        out_s = torch.empty(n, dtype=torch.int32, device=dev)
+        out_st = torch.empty(n, dtype=torch.int8, device=dev)
+        out_off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+        out_w = torch.empty(int(host[3][-1]), dtype=torch.int32, device=dev)
+        for offsets in (True, False):
+            rc = al.align_device(t(b.patterns), t(b.pattern_offsets) if offsets else None, t(b.pattern_lengths),
+                                 t(b.texts), t(b.text_offsets) if offsets else None, t(b.text_lengths),
+                                 out_s, out_st, out_w, out_off, pen=(4, 6, 2))
+            torch.cuda.synchronize(dev)
+            assert rc == pkg.WFA_GPU_OK
+            assert np.array_equal(out_s.cpu().numpy(), host[0])
+            assert np.array_equal(out_st.cpu().numpy(), host[1])
+            assert np.array_equal(out_off.cpu().numpy(), host[3])
+            assert np.array_equal(out_w.cpu().numpy().view(np.uint32), host[2])
+    finally:
+        al.set_stream(None)
+
+
+def test_repeated_calls_are_stable(al, oracle_mod):
+    """The same batch twice, with other batches between, gives identical
+    output (no state leaks between calls)."""
+    from paper_2204_02085_gb300 import synth
+
+    b = synth.uniform_reads(3000, 100, 4, seed=48)
+    first = al.align(b, (4, 6, 2))
+    al.align(synth.random_pairs(100, 0, 500, seed=49), (1, 0, 1))
+    second = al.align(b, (4, 6, 2))
+    for x, y in zip(first, second):
+        assert np.array_equal(x, y)
+
+
+def test_pack2bit_matches_oracle(al, oracle_mod):
+    from paper_2204_02085_gb300 import synth
+
+    rng = np.random.default_rng(50)
+    seqs = []
+    for L in list(range(0, 70)) + [255, 256, 257, 1000, 4097]:
+        alpha = np.frombuffer(b"ACGTacgt", np.uint8)
+        s = alpha[rng.integers(0, 8, size=L)].tobytes()
+        seqs.append(s)
+    seqs.append(b"ACGTNACGT")
+    seqs.append(b"A" * 40 + b"-")
+    # odd starting offsets exercise every 16-byte alignment
+    buf = bytearray()
+    offs = []
+    for i, s in enumerate(seqs):
+        buf += b"#" * (i % 17)
+        offs.append(len(buf))
+        buf += s
+    offs = np.array(offs, np.int64)
+    lens = np.array([len(s) for s in seqs], np.int32)
+    words, woff, inv = al.pack2bit(np.frombuffer(bytes(buf), np.uint8), offs, lens)
+    for i, s in enumerate(seqs):
+        rc, w = oracle_mod.pack2bit(s)
+        assert inv[i] == (1 if rc != 0 else 0), i
+        assert woff[i + 1] - woff[i] == len(w)
+        if rc == 0:
+            assert np.array_equal(words[woff[i]:woff[i + 1]], w), i
+
+
+@pytest.mark.parametrize("edits", [2, 4])
+def test_config2_full_size(pkg, oracle_mod, edits):
+    """5,000,000 pairs of 100 bp at E = 2 % and 4 % (the paper's workload,
+    Sec. II), device-resident as the benchmark runs them; every pair is
+    compared bit-exactly with the oracle (in chunks on all host cores)."""
+    import torch
+
+    from paper_2204_02085_gb300 import synth
+
+    n = 5_000_000
+    b = synth.uniform_reads(n, 100, edits, seed=1)
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    out_s = torch.empty(n, dtype=torch.int32, device=dev)
+    out_st = torch.empty(n, dtype=torch.int8, device=dev)
+    out_off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    out_w = torch.empty(16 * n, dtype=torch.int32, device=dev)
+    with pkg.Aligner(0) as al:
+        al.set_stream(torch.cuda.current_stream(dev))
+        rc = al.align_device(t(b.patterns), None, t(b.pattern_lengths), t(b.texts), None, t(b.text_lengths),
+                             out_s, out_st, out_w, out_off, pen=(4, 6, 2))
+        torch.cuda.synchronize(dev)
+    assert rc == pkg.WFA_GPU_OK
+    s = out_s.cpu().numpy()
+    st = out_st.cpu().numpy()
+    off = out_off.cpu().numpy()
+    w = out_w.cpu().numpy().view(np.uint32)[: int(off[-1])]
+    chunk = 1_000_000
+    for c0 in range(0, n, chunk):
+        sub = synth.Batch(b.patterns, b.pattern_offsets[c0:c0 + chunk], b.pattern_lengths[c0:c0 + chunk],
+                          b.texts, b.text_offsets[c0:c0 + chunk], b.text_lengths[c0:c0 + chunk])
+        os_, ost, ow, ooff = oracle_mod.wfa_batch(sub, (4, 6, 2), nthreads=NCPU, runs_per_pair=40)
+        assert np.array_equal(s[c0:c0 + chunk], os_)
+        assert np.array_equal(st[c0:c0 + chunk], ost)
+        lo, hi = int(off[c0]), int(off[min(c0 + chunk, n)])
+        assert np.array_equal(off[c0:c0 + chunk + 1] - lo, ooff)
+        assert np.array_equal(w[lo:hi], ow)
