@@ -1,0 +1,418 @@
+"""Benchmark: batched exact gap-affine WFA of the paper's workload on GB300.
+
+Workload (paper Sec. II: 5 million pairs of 100 bp reads at edit-distance
+thresholds E = 2 % and 4 %): per GPU, two synthetic batches of 5,000,000
+pairs of 100 bp (2 and 4 edits), penalties x=4, o=6, e=2, score + CIGAR.
+A step aligns both batches (10 M pairs per GPU).
+
+value : pairs/s with inputs already resident in HBM (device-pointer call),
+        timed with CUDA events on the launching stream.
+e2e   : the same through the host-pointer call (pinned host buffers; the
+        library's host->device and device->host copies inside the timed
+        region).
+roofline : the short-read wavefront kernel (the dominant kernel), its
+        algorithmic work per launch over its event-timed duration.
+cpu_baseline : the plain CPU oracle on the host cores, bounded sample.
+
+Run: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU: launched by torchrun; each rank aligns its own shard (weak
+scaling, replicas, no data collective).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pairs/s 100bp E=2%/4% (score+CIGAR) batched vs plain, % roofline; p99 latency"
+PEN = (4, 6, 2)
+N_PAIRS = 5_000_000
+LENGTH = 100
+EDITS = (2, 4)
+SEED = 1
+CIGAR_WORDS_PER_PAIR = 16
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
+# integer lanes per SM per clock (32-bit add/logic/min/max) and SM count of a
+# GB300; the ALU roofline peak is their product with the maximum SM clock
+INT_LANES_PER_SM = 128
+N_SM = 152
+# algorithmic integer operations (work model of one wavefront cell, one
+# extra 32-base extension window, one backtrace step)
+OPS_PER_CELL = 32
+OPS_PER_EXTRA_WINDOW = 18
+OPS_PER_BT_STEP = 12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--pairs", type=int, default=N_PAIRS, help="pairs per batch (default: the paper's 5M)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=400_000, help="pairs per edit rate for the CPU baseline")
+    return ap.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return p, "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_batches(n_pairs: int, rank: int):
+    from paper_2204_02085_gb300 import sharding, synth
+
+    return [synth.uniform_reads(n_pairs, LENGTH, e, seed=sharding.shard_seed(SEED, rank)) for e in EDITS]
+
+
+def cpu_oracle_run(batches, sample: int):
+    """The oracle (plain CPU WFA, score + CIGAR) on the first `sample` pairs
+    of each batch, all host cores.  Returns (pairs, seconds, threads, counts)."""
+    import oracle
+    from paper_2204_02085_gb300 import synth
+
+    oracle.build()
+    threads = host_cores()
+    pairs = 0
+    cnt = oracle.Counts()
+    t0 = time.perf_counter()
+    for b in batches:
+        k = min(sample, b.n)
+        sub = synth.Batch(b.patterns, b.pattern_offsets[:k], b.pattern_lengths[:k], b.texts, b.text_offsets[:k],
+                          b.text_lengths[:k])
+        oracle.wfa_batch(sub, PEN, nthreads=threads, runs_per_pair=64, counts=cnt)
+        pairs += k
+    dt = time.perf_counter() - t0
+    return pairs, dt, threads, cnt
+
+
+def run_reference(args):
+    """--impl reference: the oracle, as it stands, timed on the host cores
+    (rank 0 only); each step is a bounded sample of the same workload."""
+    from paper_2204_02085_gb300 import sharding
+
+    rank, world, _ = sharding.dist_env()
+    if rank != 0:
+        return 0
+    sample = 100_000
+    batches = make_batches(sample, 0)
+    for _ in range(args.warmup):
+        cpu_oracle_run(batches, sample)
+    t_total, pairs_total, threads = 0.0, 0, host_cores()
+    for _ in range(args.steps):
+        p, dt, threads, _ = cpu_oracle_run(batches, sample)
+        t_total += dt
+        pairs_total += p
+    value = pairs_total / t_total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": "100bp pairs, E=2%% and E=4%% (2 and 4 edits), penalties 4/6/2, score+CIGAR; "
+                               "each step a %d-pair sample per edit rate" % sample},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+                         "sample": "%d pairs per edit rate per step" % sample},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2204_02085_gb300 as pkg
+    from paper_2204_02085_gb300 import build as gpu_build
+    from paper_2204_02085_gb300 import sharding
+
+    rank, world, local = sharding.dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    if rank == 0 or not os.path.exists(pkg.LIB_PATH):
+        gpu_build.build()
+    sharding.barrier()
+
+    batches = make_batches(args.pairs, rank)
+    stream = torch.cuda.current_stream(dev)
+    al = pkg.Aligner(dev.index)
+    al.set_stream(stream)
+
+    # device-resident inputs and outputs
+    def to_dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    dbat = []
+    for b in batches:
+        n = b.n
+        dbat.append(dict(
+            pat=to_dev(b.patterns), plen=to_dev(b.pattern_lengths), txt=to_dev(b.texts), tlen=to_dev(b.text_lengths),
+            s=torch.empty(n, dtype=torch.int32, device=dev), st=torch.empty(n, dtype=torch.int8, device=dev),
+            off=torch.empty(n + 1, dtype=torch.int64, device=dev),
+            w=torch.empty(CIGAR_WORDS_PER_PAIR * n, dtype=torch.int32, device=dev)))
+
+    def device_step(collect=None):
+        for d in dbat:
+            rc = al.align_device(d["pat"], None, d["plen"], d["txt"], None, d["tlen"], d["s"], d["st"], d["w"],
+                                 d["off"], pen=PEN, timing=True)
+            if rc != pkg.WFA_GPU_OK:
+                raise RuntimeError("CIGAR capacity too small: %d words needed" % int(d["off"][-1]))
+            if collect is not None:
+                collect.append(al.timing())
+
+    for _ in range(args.warmup):
+        device_step()
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(dev.index) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    timings = []
+    sharding.barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        device_step(timings)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    sharding.barrier()
+    clocks = sampler.stop() if sampler else None
+    ms_local = ev0.elapsed_time(ev1)
+    ms = sharding.max_over_ranks(ms_local)
+    pairs_per_step = sum(b.n for b in batches)
+    value = pairs_per_step * world * args.steps / (ms / 1000.0)
+
+    # per-edit-rate figures and the dominant kernel
+    per_batch = {}
+    for i, b in enumerate(batches):
+        ts = timings[i::len(batches)]
+        align_ms = float(np.mean([t["align_ms"] for t in ts]))
+        total_ms = float(np.mean([t["total_ms"] for t in ts]))
+        per_batch[EDITS[i]] = dict(align_ms=align_ms, total_ms=total_ms,
+                                   deferred=int(np.mean([t["deferred_pairs"] for t in ts])),
+                                   launches=int(ts[0]["kernel_launches"]))
+    launches = int(sum(t["kernel_launches"] for t in timings))
+
+    # outputs of the last step, for the work model and a sanity check
+    outs = []
+    for d in dbat:
+        s = d["s"].cpu().numpy()
+        st = d["st"].cpu().numpy()
+        off = d["off"].cpu().numpy()
+        outs.append((s, st, off))
+        assert np.all(st == 0), "unexpected pair status in the benchmark workload"
+
+    # ---- e2e: host-pointer calls (pinned host memory) ------------------
+    pinned = []
+    for b, (s, st, off) in zip(batches, outs):
+        def pin(a):
+            t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)) if a.dtype != np.uint8 else torch.uint8,
+                            pin_memory=True)
+            t.numpy()[...] = a
+            return t.numpy()
+        n = b.n
+        pinned.append(dict(pat=pin(b.patterns), plen=pin(b.pattern_lengths), txt=pin(b.texts),
+                           tlen=pin(b.text_lengths),
+                           s=torch.empty(n, dtype=torch.int32, pin_memory=True).numpy(),
+                           st=torch.empty(n, dtype=torch.int8, pin_memory=True).numpy(),
+                           off=torch.empty(n + 1, dtype=torch.int64, pin_memory=True).numpy(),
+                           w=torch.empty(CIGAR_WORDS_PER_PAIR * n, dtype=torch.int32, pin_memory=True).numpy()))
+
+    def host_step():
+        h2d = d2h = 0
+        for p in pinned:
+            n = len(p["plen"])
+            rc = pkg.wfa_gpu_align_batch(al.ctx, n, p["pat"].ctypes.data, None, p["plen"].ctypes.data,
+                                         p["txt"].ctypes.data, None, p["tlen"].ctypes.data, PEN, 0, 0,
+                                         p["s"].ctypes.data, p["st"].ctypes.data, p["w"].ctypes.data,
+                                         p["w"].size, p["off"].ctypes.data)
+            if rc != pkg.WFA_GPU_OK:
+                raise pkg.WfaGpuError(rc, "e2e align")
+            h2d += p["pat"].nbytes + p["txt"].nbytes + p["plen"].nbytes + p["tlen"].nbytes
+            d2h += p["s"].nbytes + p["st"].nbytes + p["off"].nbytes + 4 * int(p["off"][-1])
+        return h2d, d2h
+
+    for _ in range(max(1, args.warmup)):
+        host_step()
+    e2e_steps = max(3, args.steps // 4)
+    sharding.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        h2d, d2h = host_step()
+    e2e_s = sharding.max_over_ranks(time.perf_counter() - t0)
+    e2e_value = pairs_per_step * world * e2e_steps / e2e_s
+    for p, (s, st, off) in zip(pinned, outs):
+        assert np.array_equal(p["s"], s) and np.array_equal(p["off"], off), "host and device calls disagree"
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- CPU baseline (oracle) and the work model from its counters -----
+    peaks, peak_src = load_peaks()
+    cpu = None
+    cnt = None
+    if not args.no_cpu_baseline:
+        cp, cdt, cthreads, cnt = cpu_oracle_run(batches, min(args.cpu_sample, args.pairs))
+        cpu = {"value": cp / cdt, "unit": "pairs/s", "cores": cthreads, "kind": "oracle",
+               "sample": "first %d pairs of each of the two 5M-pair batches (E=2%%, E=4%%), score+CIGAR, "
+                         "%d threads, %.1f s wall" % (min(args.cpu_sample, args.pairs), cthreads, cdt)}
+
+    # algorithmic bytes per pair: 2L ASCII in, lengths in, score + status +
+    # CIGAR offset + 4 bytes per CIGAR run out
+    roof = {}
+    align_ms = float(np.mean([per_batch[e]["align_ms"] for e in EDITS]))
+    n_per_launch = float(np.mean([b.n for b in batches]))
+    bytes_per_pair = []
+    for b, (s, st, off) in zip(batches, outs):
+        runs = float(off[-1]) / b.n
+        bytes_per_pair.append(float(b.pattern_lengths.mean() + b.text_lengths.mean()) + 8 + 4 + 1 + 8 + 4 * runs)
+    bpp = float(np.mean(bytes_per_pair))
+    hbm_gbs = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    achieved_gbs = bpp * n_per_launch / (align_ms / 1000.0) / 1e9
+    hbm_time_ms = bpp * n_per_launch / (hbm_gbs * 1e9) * 1000.0
+    alu = None
+    if cnt is not None and cnt.cells > 0:
+        pairs_counted = 2 * min(args.cpu_sample, args.pairs)
+        extra_windows = cnt.char_compares // 32
+        ops_per_pair = (OPS_PER_CELL * cnt.cells + OPS_PER_EXTRA_WINDOW * extra_windows
+                        + OPS_PER_BT_STEP * cnt.bt_steps) / pairs_counted
+        sm_max = float(peaks.get("sm_max_mhz", PEAKS_FALLBACK["sm_max_mhz"]))
+        alu_peak = N_SM * INT_LANES_PER_SM * sm_max * 1e6 / 1e12  # Tops/s
+        alu_achieved = ops_per_pair * n_per_launch / (align_ms / 1000.0) / 1e12
+        alu_time_ms = ops_per_pair * n_per_launch / (alu_peak * 1e12) * 1000.0
+        alu = {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Tops/s",
+               "frac": alu_achieved / alu_peak, "ops_per_pair": ops_per_pair,
+               "peak_source": "152 SMs x 128 int32 lanes x %.0f MHz" % sm_max}
+    if alu is not None and alu_time_ms > hbm_time_ms:
+        roof = dict(alu)
+        roof["hbm"] = {"achieved": achieved_gbs, "peak": hbm_gbs, "unit": "GB/s", "frac": achieved_gbs / hbm_gbs}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_gbs, "unit": "GB/s",
+                "frac": achieved_gbs / hbm_gbs, "peak_source": peak_src}
+        if alu is not None:
+            roof["alu"] = {k: alu[k] for k in ("achieved", "peak", "unit", "frac", "ops_per_pair")}
+    roof["kernel"] = "short_kernel (fused pack + wavefront + backtrace)"
+    roof["bytes_per_pair"] = bpp
+    roof["avg_launch_ms"] = align_ms
+    roof["traffic"] = None
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "%d pairs x %d bp per batch, E=2%% and E=4%% (2 and 4 edits), penalties 4/6/2, "
+                               "score+CIGAR; one step = both batches" % (args.pairs, LENGTH),
+                   "pairs_per_step_per_gpu": pairs_per_step, "parallelism": "replicas x%d" % world,
+                   "l2": "inputs larger than L2 (about 1 GB of ASCII per batch)"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "steps": e2e_steps},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "by_edit_rate": {"E=%d%%" % e: {"pairs_per_s_kernel_path": batches[i].n / (per_batch[e]["total_ms"] / 1000.0),
+                                         "align_kernel_ms": per_batch[e]["align_ms"],
+                                         "call_ms": per_batch[e]["total_ms"],
+                                         "deferred_pairs": per_batch[e]["deferred"],
+                                         "kernels_per_call": per_batch[e]["launches"],
+                                         "mean_score": float(outs[i][0].mean())}
+                         for i, e in enumerate(EDITS)},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

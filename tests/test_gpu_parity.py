@@ -176,8 +176,11 @@ def test_small_arena_retries(pkg, oracle_mod):
     arena gives ENOMEM."""
     from paper_2204_02085_gb300 import synth
 
+    # unrelated 200-700 bp pairs need up to ~5 MB of wavefronts each: a
+    # 64 MB arena split over the default warp count is too small for them,
+    # so they are retried with fewer, larger slots
     b = synth.random_pairs(60, 200, 700, seed=45)
-    with pkg.Aligner(0, scratch_bytes=4 << 20) as small:
+    with pkg.Aligner(0, scratch_bytes=64 << 20) as small:
         got = small.align(b, (4, 6, 2))
         assert_same(got, oracle_run(oracle_mod, b, (4, 6, 2)))
     big = synth.random_pairs(2, 3000, 3000, seed=46)
