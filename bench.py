@@ -62,7 +62,13 @@ def parse():
     ap.add_argument("--pairs", type=int, default=N_PAIRS, help="pairs per batch (default: the paper's 5M)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=400_000, help="pairs per edit rate for the CPU baseline")
-    return ap.parse_args()
+    ap.add_argument("--edits", default="2,4", help="edit counts of the batches (default: the paper's 2%% and 4%%)")
+    ap.add_argument("--short-variant", type=int, default=None,
+                    help="force one short-read kernel variant (tuning; default: the library's autotuner)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-pointer (end-to-end) measurement")
+    args = ap.parse_args()
+    args.edits = tuple(int(e) for e in args.edits.split(","))
+    return args
 
 
 def load_peaks():
@@ -138,10 +144,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_batches(n_pairs: int, rank: int):
+def make_batches(n_pairs: int, rank: int, edits=EDITS):
     from paper_2204_02085_gb300 import sharding, synth
 
-    return [synth.uniform_reads(n_pairs, LENGTH, e, seed=sharding.shard_seed(SEED, rank)) for e in EDITS]
+    return [synth.uniform_reads(n_pairs, LENGTH, e, seed=sharding.shard_seed(SEED, rank)) for e in edits]
 
 
 def cpu_oracle_run(batches, sample: int):
@@ -220,7 +226,9 @@ def main():
         gpu_build.build()
     sharding.barrier()
 
-    batches = make_batches(args.pairs, rank)
+    batches = make_batches(args.pairs, rank, args.edits)
+    if args.short_variant is not None:
+        os.environ["WFA_GPU_SHORT_VARIANT"] = str(args.short_variant)
     stream = torch.cuda.current_stream(dev)
     al = pkg.Aligner(dev.index)
     al.set_stream(stream)
@@ -276,9 +284,10 @@ def main():
         ts = timings[i::len(batches)]
         align_ms = float(np.mean([t["align_ms"] for t in ts]))
         total_ms = float(np.mean([t["total_ms"] for t in ts]))
-        per_batch[EDITS[i]] = dict(align_ms=align_ms, total_ms=total_ms,
+        per_batch[args.edits[i]] = dict(align_ms=align_ms, total_ms=total_ms,
                                    deferred=int(np.mean([t["deferred_pairs"] for t in ts])),
-                                   launches=int(ts[0]["kernel_launches"]))
+                                   launches=int(ts[0]["kernel_launches"]),
+                                   variant=int(ts[-1]["short_variant"]))
     launches = int(sum(t["kernel_launches"] for t in timings))
 
     # outputs of the last step, for the work model and a sanity check
@@ -292,7 +301,7 @@ def main():
 
     # ---- e2e: host-pointer calls (pinned host memory) ------------------
     pinned = []
-    for b, (s, st, off) in zip(batches, outs):
+    for b, (s, st, off) in zip(batches if not args.no_e2e else [], outs):
         def pin(a):
             t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)) if a.dtype != np.uint8 else torch.uint8,
                             pin_memory=True)
@@ -320,17 +329,19 @@ def main():
             d2h += p["s"].nbytes + p["st"].nbytes + p["off"].nbytes + 4 * int(p["off"][-1])
         return h2d, d2h
 
-    for _ in range(max(1, args.warmup)):
+    e2e_steps = 0 if args.no_e2e else max(3, args.steps // 4)
+    for _ in range(max(1, args.warmup) if e2e_steps else 0):
         host_step()
-    e2e_steps = max(3, args.steps // 4)
+    h2d = d2h = 0
     sharding.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         h2d, d2h = host_step()
     e2e_s = sharding.max_over_ranks(time.perf_counter() - t0)
-    e2e_value = pairs_per_step * world * e2e_steps / e2e_s
-    for p, (s, st, off) in zip(pinned, outs):
-        assert np.array_equal(p["s"], s) and np.array_equal(p["off"], off), "host and device calls disagree"
+    e2e_value = pairs_per_step * world * e2e_steps / e2e_s if e2e_steps else None
+    if e2e_steps:
+        for p, (s, st, off) in zip(pinned, outs):
+            assert np.array_equal(p["s"], s) and np.array_equal(p["off"], off), "host and device calls disagree"
 
     if rank != 0:
         if world > 1:
@@ -350,7 +361,7 @@ def main():
     # algorithmic bytes per pair: 2L ASCII in, lengths in, score + status +
     # CIGAR offset + 4 bytes per CIGAR run out
     roof = {}
-    align_ms = float(np.mean([per_batch[e]["align_ms"] for e in EDITS]))
+    align_ms = float(np.mean([per_batch[e]["align_ms"] for e in args.edits]))
     n_per_launch = float(np.mean([b.n for b in batches]))
     bytes_per_pair = []
     for b, (s, st, off) in zip(batches, outs):
@@ -405,8 +416,9 @@ def main():
                                          "call_ms": per_batch[e]["total_ms"],
                                          "deferred_pairs": per_batch[e]["deferred"],
                                          "kernels_per_call": per_batch[e]["launches"],
+                                         "short_variant": per_batch[e]["variant"],
                                          "mean_score": float(outs[i][0].mean())}
-                         for i, e in enumerate(EDITS)},
+                         for i, e in enumerate(args.edits)},
     }
     print(json.dumps(line), flush=True)
     if world > 1:

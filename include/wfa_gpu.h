@@ -92,7 +92,7 @@ typedef struct {
   float d2h_ms;      /* device -> host copies of outputs (host-pointer mode) */
   float total_ms;    /* whole call, first to last event */
   int32_t kernel_launches; /* kernels this library launched during the call */
-  int32_t reserved;
+  int32_t short_variant;   /* index of the short-read kernel variant that ran (-1: none) */
   int64_t deferred_pairs;  /* pairs handed from the short-read kernel to the arena kernel */
 } wfa_gpu_timing;
 

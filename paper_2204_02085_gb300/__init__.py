@@ -55,12 +55,12 @@ class Timing(ctypes.Structure):
         ("d2h_ms", ctypes.c_float),
         ("total_ms", ctypes.c_float),
         ("kernel_launches", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("short_variant", ctypes.c_int32),
         ("deferred_pairs", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
-        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class WfaGpuError(RuntimeError):

@@ -67,6 +67,14 @@ struct wfa_gpu_ctx {
   size_t arena_bytes = 0;
   int general_warps = 1;
   wfa::ShortPlan plan{};
+  // short-kernel variants (indices into plan.v): for sequences <= 127 bases
+  // a small-store variant and a large-store one, chosen per batch from a
+  // sampled score distribution; for <= 255 bases an int16 variant
+  int variant_small = 4;
+  int variant_big = 1;
+  int variant_mid = 6;
+  int variant_forced = -1;  // tuning override (WFA_GPU_SHORT_VARIANT)
+  int last_variant = -1;
   wfa::Ctrl* ctrl = nullptr;    // device
   wfa::Ctrl* h_ctrl = nullptr;  // pinned host mirror
   int64_t* h_total = nullptr;   // pinned host scalar
@@ -86,6 +94,11 @@ struct wfa_gpu_ctx {
   DevBuf<int64_t> run_src, scan_tmp;
   DevBuf<uint32_t> runs;
   int64_t pool_words = kPoolInitWords;
+  // autotuner sample outputs
+  DevBuf<int32_t> tune_score, tune_aux;
+  DevBuf<int8_t> tune_status;
+  DevBuf<int64_t> tune_src;
+  int32_t* h_tune = nullptr;  // pinned [kTuneSample]
 };
 
 namespace {
@@ -191,6 +204,48 @@ int stage_inputs(wfa_gpu_ctx* c, Call& k, int64_t n, bool dev, const char* pat, 
   return 0;
 }
 
+constexpr int64_t kTuneSample = 8192;
+
+// Pick the short-kernel variant for a batch of sequences <= 127 bases: the
+// large-store variant scores the first kTuneSample pairs (score only); if
+// nearly all of them end at a score the small-store variant can hold, the
+// small one (more pairs resident per SM) runs the batch.  Returns the
+// variant index, or -1 on a CUDA error.
+int autotune_short(wfa_gpu_ctx* c, Call& k, const wfa::AlignArgs& a_in, int64_t n) {
+  if (c->variant_forced >= 0) return c->variant_forced;
+  const wfa::ShortVariant& small = c->plan.v[c->variant_small];
+  wfa::UGeo tab[64];
+  const wfa::ScaledPen pen{a_in.xs, a_in.oes, a_in.es};
+  const int s_small = wfa::build_ugeo(tab, small.scap, small.cells, pen);
+  const int64_t m = std::min(n, kTuneSample);
+  cudaStream_t st = c->stream;
+  if (c->tune_score.ensure(m) || c->tune_status.ensure(m) || c->tune_aux.ensure(m) || c->tune_src.ensure(m))
+    return c->variant_big;
+  wfa::AlignArgs a = a_in;
+  a.n = m;
+  a.s_cap = std::min(a_in.s_cap, 1 << 20);
+  a.score_only = 1;
+  a.score = c->tune_score.p;
+  a.status = c->tune_status.p;
+  a.nruns = c->tune_aux.p;
+  a.run_src = c->tune_src.p;
+  a.defer_list = c->overflow.p;  // scratch: the sample's deferrals are discarded
+  a.ctrl = c->ctrl + 1;
+  if (!k.ok(cudaMemsetAsync(a.ctrl, 0, sizeof(wfa::Ctrl), st))) return -1;
+  // pairs the sample run defers keep score -1
+  if (!k.ok(cudaMemsetAsync(a.score, 0xff, m * sizeof(int32_t), st))) return -1;
+  if (!k.launched(wfa::launch_short(a, c->plan.v[c->variant_big], st))) return -1;
+  if (!k.ok(d2h(c->h_tune, c->tune_score.p, m * sizeof(int32_t), st)) || !k.ok(cudaStreamSynchronize(st))) return -1;
+  int64_t fit = 0, tot = 0;
+  for (int64_t i = 0; i < m; ++i) {
+    const int sc = c->h_tune[i];
+    if (sc < 0) continue;  // deferred, invalid or over the bound: not informative
+    ++tot;
+    if (sc / a.g <= s_small) ++fit;
+  }
+  return (tot == 0 || fit * 100 >= tot * 99) ? c->variant_small : c->variant_big;
+}
+
 }  // namespace
 
 extern "C" {
@@ -212,7 +267,11 @@ int wfa_gpu_create(wfa_gpu_ctx** out, int device, size_t scratch_bytes) {
     for (int i = 0; i < kEvents; ++i)
       if (cudaEventCreate(&c->ev[i]) != cudaSuccess) { rc = WFA_GPU_ECUDA; break; }
     if (rc) break;
-    if (cudaMalloc(reinterpret_cast<void**>(&c->ctrl), sizeof(wfa::Ctrl)) != cudaSuccess) { rc = WFA_GPU_ENOMEM; break; }
+    if (cudaMalloc(reinterpret_cast<void**>(&c->ctrl), 2 * sizeof(wfa::Ctrl)) != cudaSuccess) { rc = WFA_GPU_ENOMEM; break; }
+    if (cudaHostAlloc(reinterpret_cast<void**>(&c->h_tune), 8192 * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess) {
+      rc = WFA_GPU_ENOMEM;
+      break;
+    }
     if (cudaHostAlloc(reinterpret_cast<void**>(&c->h_ctrl), sizeof(wfa::Ctrl), cudaHostAllocDefault) != cudaSuccess ||
         cudaHostAlloc(reinterpret_cast<void**>(&c->h_total), sizeof(int64_t), cudaHostAllocDefault) != cudaSuccess) {
       rc = WFA_GPU_ENOMEM;
@@ -223,6 +282,11 @@ int wfa_gpu_create(wfa_gpu_ctx** out, int device, size_t scratch_bytes) {
     if (c->arena_bytes < 4096) { rc = WFA_GPU_EINVAL; break; }
     if (cudaMalloc(reinterpret_cast<void**>(&c->arena), c->arena_bytes) != cudaSuccess) { rc = WFA_GPU_ENOMEM; break; }
     if (wfa::short_plan(device, &c->plan) != cudaSuccess) { rc = WFA_GPU_ECUDA; break; }
+    // tuning override: WFA_GPU_SHORT_VARIANT=<index> for the <= 127-base case
+    if (const char* ev = std::getenv("WFA_GPU_SHORT_VARIANT")) {
+      const int v = std::atoi(ev);
+      if (v >= 0 && v < c->plan.count && c->plan.v[v].max_len >= 127) c->variant_forced = v;
+    }
     int nsm = 1;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
     c->general_warps = std::max(1, nsm * 4);
@@ -256,6 +320,7 @@ int wfa_gpu_align_batch(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const
   if (!score_only && cap > 0 && !out_cigars) return WFA_GPU_EINVAL;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return WFA_GPU_ECUDA;
   std::memset(&ctx->last, 0, sizeof ctx->last);
+  ctx->last_variant = -1;
   cudaStream_t st = ctx->stream;
   Call k{ctx, (flags & WFA_GPU_TIMING) != 0};
   if (n == 0) {
@@ -316,7 +381,13 @@ int wfa_gpu_align_batch(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const
   a.overflow_list = ctx->overflow.p;
   a.ctrl = ctx->ctrl;
 
-  if (!k.launched(wfa::launch_short(a, ctx->plan, st))) return fail_cuda(k);
+  int vi = ctx->variant_mid;
+  if (ctx->h_ctrl->max_len <= 127) {
+    vi = autotune_short(ctx, k, a, n);
+    if (vi < 0) return fail_cuda(k);
+  }
+  ctx->last_variant = vi;
+  if (!k.launched(wfa::launch_short(a, ctx->plan.v[vi], st))) return fail_cuda(k);
   k.rec(2);
   int nwarps = ctx->general_warps;
   const long arena_ints = (long)(ctx->arena_bytes / sizeof(int32_t));
@@ -397,6 +468,7 @@ int wfa_gpu_align_batch(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const
   k.rec(5);
   if (!k.ok(cudaStreamSynchronize(st))) return fail_cuda(k);
   ctx->last.kernel_launches = k.launches;
+  ctx->last.short_variant = ctx->last_variant;
   if (k.timing) {
     ctx->last.h2d_ms = elapsed(ctx, 0, 1);
     ctx->last.align_ms = elapsed(ctx, 1, 2);
@@ -530,6 +602,8 @@ void wfa_gpu_destroy(wfa_gpu_ctx* c) {
   if (c->ctrl) cudaFree(c->ctrl);
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
   if (c->h_total) cudaFreeHost(c->h_total);
+  if (c->h_tune) cudaFreeHost(c->h_tune);
+  c->tune_score.release(); c->tune_aux.release(); c->tune_status.release(); c->tune_src.release();
   for (int i = 0; i < kEvents; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);

@@ -12,6 +12,7 @@
 #include <climits>
 
 #include "launch.h"
+#include "short_path.cuh"
 #include "wfa_device.cuh"
 
 namespace wfa {
@@ -20,98 +21,11 @@ namespace {
 
 // ------------------------------------------------------------ short kernel
 
-constexpr int kShortG = 8;        // lanes per pair
-constexpr int kShortLmax = 256;   // longest sequence handled
-constexpr int kShortCells = 256;  // wavefront cells per pair (M, I, D each)
-constexpr int kShortScap = 47;    // largest scaled score stored
-constexpr int kShortBlock = 256;
-
-template <int LMAX, int CELLS, int SCAP>
-struct ShortShm {
-  uint64_t pw[LMAX / 32 + 1];  // packed pattern + pad word
-  uint64_t tw[LMAX / 32 + 1];  // packed text + pad word
-  int16_t M[CELLS], I[CELLS], D[CELLS];
-  int16_t lo[SCAP + 1], hi[SCAP + 1], base[SCAP + 1];
-  uint8_t ex[SCAP + 1];
-};
-
-// Per-group shared-memory stride: a multiple of 128 bytes plus 32, so that
-// the groups of one warp start 8 banks apart.
-template <class T>
-__host__ __device__ constexpr size_t group_stride() {
-  return ((sizeof(T) + 127) / 128) * 128 + 32;
-}
-
-using ShortShmT = ShortShm<kShortLmax, kShortCells, kShortScap>;
-constexpr size_t kShortStride = group_stride<ShortShmT>();
-
-__device__ __forceinline__ void defer_pair(const AlignArgs& a, int64_t pair) {
-  const int idx = atomicAdd(&a.ctrl->defer_count, 1);
-  a.defer_list[idx] = (int32_t)pair;
-}
-
-__device__ __forceinline__ void write_result(const AlignArgs& a, int64_t pair, int status, int score, int nr,
-                                             int64_t src) {
-  a.score[pair] = score;
-  a.status[pair] = (int8_t)status;
-  a.nruns[pair] = nr;
-  a.run_src[pair] = src;
-}
-
-template <int G, int LMAX, int CELLS, int SCAP>
+template <int G, int LMAX, int CELLS, int SCAP, typename Off>
 __global__ void __launch_bounds__(kShortBlock) short_kernel(const AlignArgs a) {
-  using Shm = ShortShm<LMAX, CELLS, SCAP>;
-  constexpr size_t kStride = group_stride<Shm>();
   extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & (G - 1);
-  const int gib = threadIdx.x / G;
-  const int gpb = blockDim.x / G;
-  Shm* S = reinterpret_cast<Shm*>(smem + gib * kStride);
-  const unsigned gmask = group_mask(G);
-  SmemView view{S->M, S->I, S->D, S->lo, S->hi, S->base, S->ex, CELLS, SCAP};
-  const ScaledPen pen{a.xs, a.oes, a.es};
-  const int64_t total_groups = (int64_t)gridDim.x * gpb;
-  // The groups of a warp take consecutive pairs and advance together.
-  for (int64_t pair = (int64_t)blockIdx.x * gpb + gib; __any_sync(0xffffffffu, pair < a.n);
-       pair += total_groups) {
-    if (pair < a.n) {
-      const int n = a.plen[pair], m = a.tlen[pair];
-      if (n > LMAX || m > LMAX) {
-        if (lane == 0) defer_pair(a, pair);
-      } else {
-        const bool okp = pack_seq<G>(a.pat + a.poff[pair], n, S->pw, lane, gmask);
-        const bool okt = pack_seq<G>(a.txt + a.toff[pair], m, S->tw, lane, gmask);
-        __syncwarp(gmask);
-        if (!(okp && okt)) {
-          if (lane == 0) write_result(a, pair, 2, -1, 0, 0);
-        } else {
-          int s = 0;
-          const int r = wfa_forward<G>(view, S->pw, S->tw, n, m, pen, a.s_cap, lane, gmask, &s);
-          if (r == kFwdOverflow) {
-            if (lane == 0) defer_pair(a, pair);
-          } else if (r == kFwdLimit) {
-            if (lane == 0) write_result(a, pair, 1, -1, 0, 0);
-          } else if (lane == 0) {
-            if (a.score_only) {
-              write_result(a, pair, 0, s * a.g, 0, 0);
-            } else {
-              const int64_t src = pair * kSlot;
-              const int nr = wfa_backtrace(view, n, m, pen, s, a.runs + src, kSlot);
-              if (nr == -1) {
-                defer_pair(a, pair);  // more runs than a slot holds
-              } else if (nr < 0) {
-                atomicExch(&a.ctrl->internal_error, 1);
-                write_result(a, pair, 0, s * a.g, 0, src);
-              } else {
-                write_result(a, pair, 0, s * a.g, nr, src);
-              }
-            }
-          }
-        }
-      }
-    }
-    __syncwarp();
-  }
+  __shared__ int s_last;
+  short_body<G, LMAX, CELLS, SCAP, Off>(a, smem, &s_last);
 }
 
 // ---------------------------------------------------------- general kernel
@@ -205,6 +119,7 @@ __device__ __forceinline__ long long warp_max64(long long v) {
 __global__ void validate_kernel(int64_t n, const int64_t* poff, const int32_t* plen, const int64_t* toff,
                                 const int32_t* tlen, Ctrl* ctrl) {
   long long pe = 0, te = 0;
+  int ml = 0;
   bool bad = false;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -216,12 +131,15 @@ __global__ void validate_kernel(int64_t n, const int64_t* poff, const int32_t* p
     }
     pe = max(pe, po + pl);
     te = max(te, to + tl);
+    ml = max(ml, max(pl, tl));
   }
   pe = warp_max64(pe);
   te = warp_max64(te);
+  ml = __reduce_max_sync(0xffffffffu, ml);
   if ((threadIdx.x & 31) == 0) {
     if (pe) atomicMax(&ctrl->pat_extent, pe);
     if (te) atomicMax(&ctrl->txt_extent, te);
+    if (ml) atomicMax(&ctrl->max_len, ml);
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(&ctrl->bad_input, 1);
 }
@@ -358,29 +276,58 @@ int current_device() {
 
 // ---------------------------------------------------------------- launchers
 
-cudaError_t short_plan(int device, ShortPlan* plan) {
-  auto k = short_kernel<kShortG, kShortLmax, kShortCells, kShortScap>;
-  const size_t smem = (size_t)(kShortBlock / kShortG) * kShortStride;
+namespace {
+
+template <int G, int LMAX, int CELLS, int SCAP, typename Off>
+cudaError_t plan_one(int device, ShortVariant* v, const char* name) {
+  using C = ShortCfg<G, LMAX, CELLS, SCAP, Off>;
+  auto k = short_kernel<G, LMAX, CELLS, SCAP, Off>;
+  const int warps = kShortBlock / 32;
+  const size_t smem = C::smem_bytes(warps);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kShortBlock, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  plan->grid = sm_count(device) * per_sm;
-  plan->block = kShortBlock;
-  plan->smem = smem;
-  plan->max_len = kShortLmax;
+  v->grid = sm_count(device) * per_sm;
+  v->block = kShortBlock;
+  v->smem = smem;
+  v->max_len = LMAX;
+  v->pairs_per_block = warps * C::P;
+  v->kernel = reinterpret_cast<const void*>(k);
+  v->name = name;
+  v->cells = CELLS;
+  v->scap = SCAP;
   return cudaSuccess;
 }
 
-cudaError_t launch_short(const AlignArgs& a, const ShortPlan& plan, cudaStream_t st) {
+}  // namespace
+
+// The short-kernel variants: (lanes per pair, longest sequence, cells per
+// pair, largest score index, offset type).
+cudaError_t short_plan(int device, ShortPlan* plan) {
+  cudaError_t e;
+  int i = 0;
+  if ((e = plan_one<1, 127, 208, 31, int8_t>(device, &plan->v[i++], "g1_l127_c208_i8"))) return e;
+  if ((e = plan_one<2, 127, 208, 31, int8_t>(device, &plan->v[i++], "g2_l127_c208_i8"))) return e;
+  if ((e = plan_one<4, 127, 208, 31, int8_t>(device, &plan->v[i++], "g4_l127_c208_i8"))) return e;
+  if ((e = plan_one<8, 127, 208, 31, int8_t>(device, &plan->v[i++], "g8_l127_c208_i8"))) return e;
+  if ((e = plan_one<1, 127, 64, 15, int8_t>(device, &plan->v[i++], "g1_l127_c64_i8"))) return e;
+  if ((e = plan_one<2, 255, 208, 31, int16_t>(device, &plan->v[i++], "g2_l255_c208_i16"))) return e;
+  if ((e = plan_one<4, 255, 208, 31, int16_t>(device, &plan->v[i++], "g4_l255_c208_i16"))) return e;
+  plan->count = i;
+  return cudaSuccess;
+}
+
+cudaError_t launch_short(const AlignArgs& a, const ShortVariant& v, cudaStream_t st) {
   if (a.n <= 0) return cudaSuccess;
-  int grid = plan.grid;
-  const int64_t need = (a.n + (plan.block / kShortG) - 1) / (plan.block / kShortG);  // one group per pair
+  int grid = v.grid;
+  const int64_t need = (a.n + v.pairs_per_block - 1) / v.pairs_per_block;
   if (need < grid) grid = (int)need;
-  short_kernel<kShortG, kShortLmax, kShortCells, kShortScap><<<grid, plan.block, plan.smem, st>>>(a);
-  return cudaGetLastError();
+  AlignArgs copy = a;
+  void* args[] = {&copy};
+  return cudaLaunchKernel(v.kernel, dim3(grid), dim3(v.block), args, v.smem, st);
 }
 
 cudaError_t launch_general(const AlignArgs& a, int32_t* arena, long slot_ints, int nwarps, cudaStream_t st) {

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "wfa_device.cuh"
+
 namespace wfa {
 
 // Per-call device control block, zeroed before each batch.
@@ -18,6 +20,8 @@ struct Ctrl {
   unsigned long long pool_top;  // words used in the CIGAR pool
   long long pat_extent;     // max(offset + length) over patterns
   long long txt_extent;     // max(offset + length) over texts
+  int32_t max_len;          // longest pattern or text
+  int32_t pad;
 };
 
 struct AlignArgs {
@@ -46,14 +50,23 @@ struct AlignArgs {
 
 constexpr int kSlot = 16;  // CIGAR runs a short-kernel pair may keep
 
-// Fused short-read kernel (pack + wavefronts in shared memory + backtrace).
-struct ShortPlan {
-  int grid, block;
+// Fused short-read kernel (pack + wavefronts in shared memory + backtrace),
+// one instantiation per variant.
+struct ShortVariant {
+  const void* kernel;
+  const char* name;
+  int grid, block, pairs_per_block;
   size_t smem;
-  int max_len;
+  int max_len;  // longest sequence the variant takes
+  int cells;    // wavefront cells stored per pair
+  int scap;     // largest score index of the geometry table
+};
+struct ShortPlan {
+  ShortVariant v[8];
+  int count;
 };
 cudaError_t short_plan(int device, ShortPlan* plan);
-cudaError_t launch_short(const AlignArgs& a, const ShortPlan& plan, cudaStream_t st);
+cudaError_t launch_short(const AlignArgs& a, const ShortVariant& v, cudaStream_t st);
 
 // Arena kernel for pairs deferred by the short kernel: one warp per pair,
 // `nwarps` warps, each with slot_ints int32 of scratch.

@@ -1,0 +1,161 @@
+// short_path.cuh -- body of the fused short-read kernel (pack + gap-affine
+// WFA with uniform per-score geometry + backtrace), shared by the kernel in
+// kernels.cu.  See the comment on short_body.
+#pragma once
+
+#include "launch.h"
+#include "wfa_device.cuh"
+
+namespace wfa {
+
+constexpr int kShortBlock = 128;
+
+__device__ __forceinline__ void defer_pair(const AlignArgs& a, int64_t pair) {
+  const int idx = atomicAdd(&a.ctrl->defer_count, 1);
+  a.defer_list[idx] = (int32_t)pair;
+}
+
+__device__ __forceinline__ void write_result(const AlignArgs& a, int64_t pair, int status, int score, int nr,
+                                             int64_t src) {
+  a.score[pair] = score;
+  a.status[pair] = (int8_t)status;
+  a.nruns[pair] = nr;
+  a.run_src[pair] = src;
+}
+
+// Shared-memory layout of the short kernel: the geometry table, then one
+// region per warp holding its P = 32/G pairs' packed sequences and M/I/D
+// cells, interleaved by pair (element c of pair slot q at [c * P + q]).
+template <int G, int LMAX, int CELLS, int SCAP, typename Off>
+struct ShortCfg {
+  static constexpr int P = 32 / G;
+  static constexpr int NW = (LMAX + 31) / 32 + 1;  // data words + pad word
+  struct WarpShm {
+    uint64_t pw[NW * P];
+    uint64_t tw[NW * P];
+    Off M[CELLS * P];
+    Off I[CELLS * P];
+    Off D[CELLS * P];
+  };
+  static constexpr size_t kTabBytes = ((SCAP + 1) * sizeof(UGeo) + 15) / 16 * 16;
+  static constexpr size_t kWarpBytes = (sizeof(WarpShm) + 15) / 16 * 16;
+  static constexpr size_t smem_bytes(int warps) { return kTabBytes + (size_t)warps * kWarpBytes; }
+};
+
+// Fused short-read kernel: G lanes per pair, 32/G pairs per warp advancing
+// through the scores in lockstep; per pair: pack both sequences (2 bits per
+// base) into shared memory, run the wavefront recurrences with cells in
+// shared memory, then walk the backtrace and write the CIGAR runs (last
+// first) into the pair's slot.  Pairs longer than LMAX, or whose score
+// passes the last storable wavefront (but not the caller's max_score), are
+// deferred to the arena kernel.
+template <int G, int LMAX, int CELLS, int SCAP, typename Off>
+__device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* smem, int* s_last_shared) {
+  using C = ShortCfg<G, LMAX, CELLS, SCAP, Off>;
+  constexpr int P = C::P;
+  constexpr int NUL = NullOf<Off>::value;
+  constexpr unsigned FULL = 0xffffffffu;
+  int& s_last = *s_last_shared;
+  UGeo* tab = reinterpret_cast<UGeo*>(smem);
+  const int warp = threadIdx.x >> 5, lane32 = threadIdx.x & 31;
+  const int lane = lane32 & (G - 1), q = lane32 / G;
+  auto* W = reinterpret_cast<typename C::WarpShm*>(smem + C::kTabBytes + warp * C::kWarpBytes);
+  const ScaledPen pen{a.xs, a.oes, a.es};
+  if (threadIdx.x == 0) s_last = build_ugeo(tab, SCAP, CELLS, pen);
+  __syncthreads();
+  const int s_store = s_last;
+  const int s_hi = min(s_store, a.s_cap);
+  const unsigned gmask = group_mask(G);
+  UView<Off, P> view{tab, W->M, W->I, W->D, q};
+  uint64_t* pw = W->pw + q;
+  uint64_t* tw = W->tw + q;
+  const int64_t wpb = blockDim.x >> 5;
+  const int64_t stride = (int64_t)gridDim.x * wpb * P;
+  for (int64_t first = ((int64_t)blockIdx.x * wpb + warp) * P; first < a.n; first += stride) {
+    const int64_t pair = first + q;
+    bool active = pair < a.n;
+    int n = 0, m = 0;
+    if (active) {
+      n = a.plen[pair];
+      m = a.tlen[pair];
+      if (n > LMAX || m > LMAX) {
+        if (lane == 0) defer_pair(a, pair);
+        active = false;
+      }
+    }
+    if (active) {
+      const bool okp = pack_seq_strided<G>(a.pat + a.poff[pair], n, pw, P, lane, gmask);
+      const bool okt = pack_seq_strided<G>(a.txt + a.toff[pair], m, tw, P, lane, gmask);
+      if (!(okp && okt)) {
+        if (lane == 0) write_result(a, pair, 2, -1, 0, 0);
+        active = false;
+      }
+    }
+    __syncwarp();
+    const int kf = m - n;
+    int s_fin = -1;
+    if (active && lane == 0) view.put(0, 0, extend_diag(pw, tw, n, m, 0, 0, P), NUL, NUL);
+    __syncwarp();
+    if (active && kf == 0 && view.getM(Geo{0, 1, 0}, 0) == m) {
+      s_fin = 0;
+      active = false;
+    }
+    for (int s = 1; s <= s_hi && __any_sync(FULL, active); ++s) {
+      const UGeo g = tab[s];
+      if (!g.ex) continue;
+      if (active) {
+        const Geo gx = geo_of(view, s - pen.x, 1);
+        const Geo go = geo_of(view, s - pen.oe, 1);
+        const Geo ge = geo_of(view, s - pen.e, 2);
+        for (int i = lane; i < g.w; i += G) {
+          const int k = g.lo + i;
+          const int mx = get_off<UView<Off, P>, 0>(view, gx, k, NUL);
+          const int ml = get_off<UView<Off, P>, 0>(view, go, k - 1, NUL);
+          const int mr = get_off<UView<Off, P>, 0>(view, go, k + 1, NUL);
+          const int il = get_off<UView<Off, P>, 1>(view, ge, k - 1, NUL);
+          const int dr = get_off<UView<Off, P>, 2>(view, ge, k + 1, NUL);
+          int iv = max(ml, il) + 1;
+          if (iv < 0 || iv > m) iv = NUL;
+          int dv = max(mr, dr);
+          if (dv < 0 || dv - k > n) dv = NUL;
+          int xv = mx + 1;
+          if (mx < 0 || xv > m || xv - k > n) xv = NUL;
+          int mv = max(xv, max(iv, dv));
+          mv = mv >= 0 ? extend_diag(pw, tw, n, m, k, mv, P) : NUL;
+          view.put(g.base, i, mv, iv, dv);
+        }
+      }
+      __syncwarp();
+      if (active && kf >= g.lo && kf < g.lo + g.w && view.getM(Geo{g.lo, g.w, g.base}, kf - g.lo) == m) {
+        s_fin = s;
+        active = false;
+      }
+    }
+    if (lane == 0) {
+      if (active) {
+        // every stored score was tried: beyond the caller's bound, or beyond
+        // what this kernel stores (then the arena kernel takes the pair)
+        if (a.s_cap <= s_store) write_result(a, pair, 1, -1, 0, 0);
+        else defer_pair(a, pair);
+      } else if (s_fin >= 0) {
+        if (a.score_only) {
+          write_result(a, pair, 0, s_fin * a.g, 0, 0);
+        } else {
+          const int64_t src = pair * kSlot;
+          const int nr = wfa_backtrace(view, n, m, pen, s_fin, a.runs + src, kSlot);
+          if (nr == -1) {
+            defer_pair(a, pair);  // more runs than a slot holds
+          } else if (nr < 0) {
+            atomicExch(&a.ctrl->internal_error, 1);
+            write_result(a, pair, 0, s_fin * a.g, 0, src);
+          } else {
+            write_result(a, pair, 0, s_fin * a.g, nr, src);
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace wfa

@@ -40,7 +40,10 @@ constexpr int kFwdOk = 0, kFwdLimit = 1, kFwdOverflow = 3;
 constexpr int kNull16 = -16384;
 constexpr int kNull32 = -(1 << 30);
 
+constexpr int kNull8 = -128;
+
 template <typename Off> struct NullOf;
+template <> struct NullOf<int8_t> { static constexpr int value = kNull8; };
 template <> struct NullOf<int16_t> { static constexpr int value = kNull16; };
 template <> struct NullOf<int32_t> { static constexpr int value = kNull32; };
 
@@ -120,6 +123,17 @@ __device__ __forceinline__ bool pack_seq(const char* __restrict__ seq, int len, 
   return __any_sync(gmask, bad) == 0;
 }
 
+// As pack_seq, but word w goes to out[w * stride] (words of several pairs
+// interleaved in shared memory).
+template <int G>
+__device__ __forceinline__ bool pack_seq_strided(const char* __restrict__ seq, int len, uint64_t* out, int stride,
+                                                 int lane, unsigned gmask) {
+  const int nwords = (len + 31) >> 5;
+  bool bad = false;
+  for (int w = lane; w <= nwords; w += G) out[w * stride] = (w < nwords) ? pack_word(seq, len, w, &bad) : 0ull;
+  return __any_sync(gmask, bad) == 0;
+}
+
 // ----------------------------------------------------------------- extend
 
 // 32 bases starting at base position pos of a packed sequence (reads words
@@ -131,14 +145,24 @@ __device__ __forceinline__ uint64_t window64(const uint64_t* W, int pos) {
   return (a << sh) | ((b >> 1) >> (63 - sh));
 }
 
+// window64 over words stored every `stride` elements
+__device__ __forceinline__ uint64_t window64s(const uint64_t* W, int pos, int stride) {
+  const int w = pos >> 5;
+  const int sh = (pos & 31) << 1;
+  const uint64_t a = W[w * stride], b = W[(w + 1) * stride];
+  return (a << sh) | ((b >> 1) >> (63 - sh));
+}
+
 // Advance offset h on diagonal k while pattern[h-k] == text[h]; h is a
-// valid offset (0 <= h <= m, 0 <= h-k <= n).
-__device__ __forceinline__ int extend_diag(const uint64_t* pw, const uint64_t* tw, int n, int m, int k, int h) {
+// valid offset (0 <= h <= m, 0 <= h-k <= n).  Packed words are read every
+// `stride` elements.
+__device__ __forceinline__ int extend_diag(const uint64_t* pw, const uint64_t* tw, int n, int m, int k, int h,
+                                           int stride = 1) {
   for (;;) {
     const int v = h - k;
     const int rem = min(n - v, m - h);
     if (rem <= 0) break;
-    const uint64_t d = window64(pw, v) ^ window64(tw, h);
+    const uint64_t d = window64s(pw, v, stride) ^ window64s(tw, h, stride);
     const int eq = d ? (__clzll(d) >> 1) : 32;
     if (eq >= rem) {
       h += rem;
@@ -227,6 +251,75 @@ struct ArenaView {
   __device__ __forceinline__ void put(int b, int w, int i, int mv, int iv, int dv) {
     int32_t* p = end - b;
     p[i] = mv; p[w + i] = iv; p[2 * w + i] = dv;
+  }
+};
+
+// Uniform geometry: without trimming to the sequence ends, the diagonal
+// range of every wavefront depends only on the (scaled) penalties, so one
+// table serves every pair of a launch.  ex: bit0 M exists, bit1 I and D
+// exist (they always exist together); base: first cell of the wavefront in a
+// pair's store.
+struct UGeo {
+  int16_t lo, w, base;
+  uint8_t ex, pad;
+};
+
+// Fill tab[0..scap] for penalties p; wavefronts whose cells would pass
+// cellcap are marked absent and the last storable score is returned.
+__host__ __device__ inline int build_ugeo(UGeo* tab, int scap, int cellcap, ScaledPen p) {
+  int top = 0, last = scap;
+  for (int s = 0; s <= scap; ++s) {
+    UGeo g{0, 0, 0, 0, 0};
+    int lo = 1 << 14, hi = -(1 << 14);
+    bool exM = false, exG = false;
+    if (s == 0) {
+      exM = true;
+      lo = hi = 0;
+    } else {
+      const bool eX = s - p.x >= 0 && (tab[s - p.x].ex & 1);
+      const bool eO = s - p.oe >= 0 && (tab[s - p.oe].ex & 1);
+      const bool eE = s - p.e >= 0 && (tab[s - p.e].ex & 2);
+      exG = eO || eE;
+      exM = eX || exG;
+      if (eX) { lo = min(lo, (int)tab[s - p.x].lo); hi = max(hi, tab[s - p.x].lo + tab[s - p.x].w - 1); }
+      if (eO) { lo = min(lo, tab[s - p.oe].lo - 1); hi = max(hi, tab[s - p.oe].lo + tab[s - p.oe].w); }
+      if (eE) { lo = min(lo, tab[s - p.e].lo - 1); hi = max(hi, tab[s - p.e].lo + tab[s - p.e].w); }
+    }
+    if (exM) {
+      const int w = hi - lo + 1;
+      if (top + w > cellcap) {
+        last = s - 1;
+        for (int r = s; r <= scap; ++r) tab[r] = UGeo{0, 0, 0, 0, 0};
+        break;
+      }
+      g.lo = (int16_t)lo;
+      g.w = (int16_t)w;
+      g.base = (int16_t)top;
+      g.ex = (uint8_t)(1 | (exG ? 2 : 0));
+      top += w;
+    }
+    tab[s] = g;
+  }
+  return last;
+}
+
+// View over a warp's interleaved shared-memory store: cell c of the warp's
+// pair slot p at [c * P + p]; geometry from the shared table.
+template <typename OffT, int P>
+struct UView {
+  using Off = OffT;
+  const UGeo* tab;
+  OffT *M, *I, *D;
+  int p;
+  __device__ __forceinline__ int lo_of(int s) const { return tab[s].lo; }
+  __device__ __forceinline__ int hi_of(int s) const { return tab[s].lo + tab[s].w - 1; }
+  __device__ __forceinline__ int base_of(int s) const { return tab[s].base; }
+  __device__ __forceinline__ int ex_of(int s) const { return tab[s].ex & 2 ? 7 : tab[s].ex; }
+  __device__ __forceinline__ int getM(const Geo& g, int i) const { return M[(g.base + i) * P + p]; }
+  __device__ __forceinline__ int getI(const Geo& g, int i) const { return I[(g.base + i) * P + p]; }
+  __device__ __forceinline__ int getD(const Geo& g, int i) const { return D[(g.base + i) * P + p]; }
+  __device__ __forceinline__ void put(int b, int i, int mv, int iv, int dv) {
+    M[(b + i) * P + p] = (OffT)mv; I[(b + i) * P + p] = (OffT)iv; D[(b + i) * P + p] = (OffT)dv;
   }
 };
 
