@@ -170,6 +170,55 @@ int wfa_gpu_pack2bit(wfa_gpu_ctx *ctx, int64_t n_seqs, const char *seqs,
                      uint64_t *out_words, int64_t words_capacity,
                      int64_t *out_word_offsets, int8_t *out_invalid);
 
+/* Size of the device scratch array behind wfa_gpu_align_short_noalloc, and
+ * the limits it implies. */
+#define WFA_GPU_NOALLOC_SCRATCH_BYTES ((size_t)4 << 20)
+#define WFA_GPU_NOALLOC_MAX_PAIRS 32768
+#define WFA_GPU_NOALLOC_MAX_LEN 127
+
+/* Align short read pairs without allocating any memory.  (The paper has no
+ * counterpart to this entry point; it exists for callers of this library.)
+ *
+ * Who needs it: callers that cannot call cudaMalloc -- code that runs while
+ * a CUDA stream is being captured into a graph (an allocation would break
+ * the capture), applications whose device memory is owned by a pool or
+ * framework that forbids foreign allocations, and latency-critical paths
+ * that must not risk a device-wide synchronisation inside cudaMalloc or
+ * cudaFree.  wfa_gpu_create allocates a scratch arena and buffers; this
+ * entry point instead keeps its scratch (control block, offset scans,
+ * per-pair CIGAR slots, work lists) in one file-scope device array of
+ * WFA_GPU_NOALLOC_SCRATCH_BYTES that every GPU which loads the library
+ * holds until the process exits.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *
+ * Same operation, inputs and outputs as wfa_gpu_align_batch with
+ * WFA_GPU_DEVICE_PTRS (every pointer is device memory on the current device;
+ * offsets may be NULL = back to back), without flags, and limited to:
+ *   n_pairs <= WFA_GPU_NOALLOC_MAX_PAIRS, every sequence
+ *   <= WFA_GPU_NOALLOC_MAX_LEN bases -- otherwise WFA_GPU_EINVAL;
+ *   pairs whose wavefronts fit the short-read kernel's shared memory (for
+ *   penalties 4/6/2, an optimal score up to 32) -- if one does not,
+ *   WFA_GPU_ENOMEM (wfa_gpu_align_batch handles such pairs in its arena).
+ * stream: the cudaStream_t to run on (NULL: the legacy default stream).
+ *
+ * The first call on a device sets that device up (looks up the scratch
+ * array's device address, configures the kernel): make that first call
+ * before any stream capture begins.  Every call shares the one scratch
+ * array, which keeps the previous call's contents; calls whose work
+ * overlaps on the GPU (other streams, other host threads) race on it and
+ * must be serialised by the caller.  Returns after the outputs are written.
+ * Returns OK, EINVAL, ENOMEM, ECUDA or ECIGAR_CAPACITY as
+ * wfa_gpu_align_batch does. */
+int wfa_gpu_align_short_noalloc(void *stream, int64_t n_pairs,
+                                const char *patterns, const int64_t *pattern_offsets,
+                                const int32_t *pattern_lengths,
+                                const char *texts, const int64_t *text_offsets,
+                                const int32_t *text_lengths,
+                                wfa_gpu_penalties pen, int32_t max_score,
+                                int32_t *out_scores, int8_t *out_status,
+                                uint32_t *out_cigars, int64_t cigar_capacity_words,
+                                int64_t *out_cigar_offsets);
+
 /* Upper bound on the CIGAR words of one pair of lengths plen, tlen under pen
  * and max_score (<= 0: unbounded): with s the largest score the pair can
  * report, at most 2*floor(s / min(x, o+e)) + 1 runs, and never more than

@@ -39,7 +39,11 @@ EXPORTS = (
     "wfa_gpu_last_timing",
     "wfa_gpu_strerror",
     "wfa_gpu_destroy",
+    "wfa_gpu_align_short_noalloc",
 )
+WFA_GPU_NOALLOC_SCRATCH_BYTES = 4 << 20
+WFA_GPU_NOALLOC_MAX_PAIRS = 32768
+WFA_GPU_NOALLOC_MAX_LEN = 127
 
 
 class Penalties(ctypes.Structure):
@@ -98,6 +102,8 @@ def load(path: str = LIB_PATH):
     L.wfa_gpu_strerror.restype = ctypes.c_char_p
     L.wfa_gpu_destroy.argtypes = [vp]
     L.wfa_gpu_destroy.restype = None
+    L.wfa_gpu_align_short_noalloc.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, Penalties, i32, vp, vp, vp, i64, vp]
+    L.wfa_gpu_align_short_noalloc.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -153,6 +159,18 @@ def wfa_gpu_strerror(code: int) -> str:
 
 def wfa_gpu_destroy(ctx) -> None:
     load().wfa_gpu_destroy(ctx)
+
+
+def wfa_gpu_align_short_noalloc(stream, n_pairs, patterns, pattern_offsets, pattern_lengths, texts, text_offsets,
+                                text_lengths, pen, max_score, out_scores, out_status, out_cigars,
+                                cigar_capacity_words, out_cigar_offsets) -> int:
+    """Raw call of the entry point that allocates nothing: device addresses
+    (int) or None, ``stream`` a cudaStream_t handle (int) or None."""
+    if not isinstance(pen, Penalties):
+        pen = Penalties(*pen)
+    return load().wfa_gpu_align_short_noalloc(stream or None, n_pairs, patterns, pattern_offsets, pattern_lengths,
+                                              texts, text_offsets, text_lengths, pen, max_score, out_scores,
+                                              out_status, out_cigars, cigar_capacity_words, out_cigar_offsets)
 
 
 # ------------------------------------------------------------ marshalling
