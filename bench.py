@@ -320,15 +320,17 @@ def main():
         for p in pinned:
             n = len(p["plen"])
             rc = pkg.wfa_gpu_align_batch(al.ctx, n, p["pat"].ctypes.data, None, p["plen"].ctypes.data,
-                                         p["txt"].ctypes.data, None, p["tlen"].ctypes.data, PEN, 0, 0,
-                                         p["s"].ctypes.data, p["st"].ctypes.data, p["w"].ctypes.data,
-                                         p["w"].size, p["off"].ctypes.data)
+                                         p["txt"].ctypes.data, None, p["tlen"].ctypes.data, PEN, 0,
+                                         pkg.WFA_GPU_TIMING, p["s"].ctypes.data, p["st"].ctypes.data,
+                                         p["w"].ctypes.data, p["w"].size, p["off"].ctypes.data)
             if rc != pkg.WFA_GPU_OK:
                 raise pkg.WfaGpuError(rc, "e2e align")
+            e2e_phases.append(al.timing())
             h2d += p["pat"].nbytes + p["txt"].nbytes + p["plen"].nbytes + p["tlen"].nbytes
             d2h += p["s"].nbytes + p["st"].nbytes + p["off"].nbytes + 4 * int(p["off"][-1])
         return h2d, d2h
 
+    e2e_phases = []
     e2e_steps = 0 if args.no_e2e else max(3, args.steps // 4)
     for _ in range(max(1, args.warmup) if e2e_steps else 0):
         host_step()
@@ -408,7 +410,12 @@ def main():
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "steps": e2e_steps},
+                "steps": e2e_steps,
+                "inputs": "page-locked host buffers; the kernels read them over NVLink-C2C (mapped), outputs "
+                          "copied back",
+                "phase_ms_per_call": {k: round(float(np.mean([t[k] for t in e2e_phases[-2 * e2e_steps:]])), 3)
+                                      for k in ("h2d_ms", "align_ms", "general_ms", "cigar_ms", "d2h_ms",
+                                                "total_ms")} if e2e_phases else None},
         "gpu_launches": launches,
         "clocks": clocks,
         "by_edit_rate": {"E=%d%%" % e: {"pairs_per_s_kernel_path": batches[i].n / (per_batch[e]["total_ms"] / 1000.0),

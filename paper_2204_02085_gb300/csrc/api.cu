@@ -70,7 +70,9 @@ struct wfa_gpu_ctx {
   // short-kernel variants (indices into plan.v): for sequences <= 127 bases
   // a small-store variant and a large-store one, chosen per batch from a
   // sampled score distribution; for <= 255 bases an int16 variant
-  int variant_small = 4;
+  // candidates for sequences <= 127 bases, smallest store first; the last
+  // one (largest store) scores the autotuner's sample
+  int variants_small[3] = {7, 4, 1};
   int variant_big = 1;
   int variant_mid = 6;
   int variant_forced = -1;  // tuning override (WFA_GPU_SHORT_VARIANT)
@@ -144,8 +146,32 @@ cudaError_t d2h(void* dst, const void* src, size_t bytes, cudaStream_t st) {
   return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st);
 }
 
-// Lengths, offsets and sequences on the device; validates them.  Returns 0 or
-// a negative WFA_GPU_* code.
+// Device address through which kernels can read the host range
+// [p, p + bytes), or nullptr when that range is not page-locked, mapped
+// memory of one allocation (then it is copied instead).  On a Grace-Blackwell
+// node such reads travel over NVLink-C2C while the kernel runs, so page-locked
+// inputs need no staging copy.
+const void* mapped_range(const void* p, size_t bytes) {
+  if (!p || !bytes) return nullptr;
+  cudaPointerAttributes a0{}, a1{};
+  if (cudaPointerGetAttributes(&a0, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a0.type != cudaMemoryTypeHost || !a0.devicePointer) return nullptr;
+  const char* last = static_cast<const char*>(p) + bytes - 1;
+  if (cudaPointerGetAttributes(&a1, last) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a1.type != cudaMemoryTypeHost || !a1.devicePointer) return nullptr;
+  if (static_cast<const char*>(a1.devicePointer) != static_cast<const char*>(a0.devicePointer) + (bytes - 1))
+    return nullptr;
+  return a0.devicePointer;
+}
+
+// Lengths, offsets and sequences on the device (or mapped from page-locked
+// host memory); validates them.  Returns 0 or a negative WFA_GPU_* code.
 int stage_inputs(wfa_gpu_ctx* c, Call& k, int64_t n, bool dev, const char* pat, const int64_t* poff,
                  const int32_t* plen, const char* txt, const int64_t* toff, const int32_t* tlen,
                  const char** d_pat, const int64_t** d_poff, const int32_t** d_plen, const char** d_txt,
@@ -156,16 +182,31 @@ int stage_inputs(wfa_gpu_ctx* c, Call& k, int64_t n, bool dev, const char* pat, 
     *d_plen = plen;
     *d_tlen = tlen;
   } else {
-    if ((e = c->plen.ensure(n)) || (e = c->tlen.ensure(n))) return map_alloc(e);
-    if (!k.ok(h2d(c->plen.p, plen, n * sizeof(int32_t), st)) || !k.ok(h2d(c->tlen.p, tlen, n * sizeof(int32_t), st)))
-      return WFA_GPU_ECUDA;
-    *d_plen = c->plen.p;
-    *d_tlen = c->tlen.p;
+    const void* mp = mapped_range(plen, n * sizeof(int32_t));
+    const void* mt = mapped_range(tlen, n * sizeof(int32_t));
+    if (mp) {
+      *d_plen = static_cast<const int32_t*>(mp);
+    } else {
+      if ((e = c->plen.ensure(n))) return map_alloc(e);
+      if (!k.ok(h2d(c->plen.p, plen, n * sizeof(int32_t), st))) return WFA_GPU_ECUDA;
+      *d_plen = c->plen.p;
+    }
+    if (mt) {
+      *d_tlen = static_cast<const int32_t*>(mt);
+    } else {
+      if ((e = c->tlen.ensure(n))) return map_alloc(e);
+      if (!k.ok(h2d(c->tlen.p, tlen, n * sizeof(int32_t), st))) return WFA_GPU_ECUDA;
+      *d_tlen = c->tlen.p;
+    }
   }
   if ((e = c->scan_tmp.ensure(wfa::scan_tmp_elems(n)))) return map_alloc(e);
   // offsets: caller's (staged if host) or the exclusive scan of the lengths
+  const void* mpo = (poff && !dev) ? mapped_range(poff, n * sizeof(int64_t)) : nullptr;
+  const void* mto = (toff && !dev) ? mapped_range(toff, n * sizeof(int64_t)) : nullptr;
   if (poff && dev) {
     *d_poff = poff;
+  } else if (mpo) {
+    *d_poff = static_cast<const int64_t*>(mpo);
   } else {
     if ((e = c->poff.ensure(n + 1))) return map_alloc(e);
     if (poff) {
@@ -177,6 +218,8 @@ int stage_inputs(wfa_gpu_ctx* c, Call& k, int64_t n, bool dev, const char* pat, 
   }
   if (toff && dev) {
     *d_toff = toff;
+  } else if (mto) {
+    *d_toff = static_cast<const int64_t*>(mto);
   } else {
     if ((e = c->toff.ensure(n + 1))) return map_alloc(e);
     if (toff) {
@@ -196,10 +239,22 @@ int stage_inputs(wfa_gpu_ctx* c, Call& k, int64_t n, bool dev, const char* pat, 
     *d_txt = txt;
   } else {
     const size_t pe = (size_t)c->h_ctrl->pat_extent, te = (size_t)c->h_ctrl->txt_extent;
-    if ((e = c->pat.ensure(pe + 16)) || (e = c->txt.ensure(te + 16))) return map_alloc(e);
-    if (!k.ok(h2d(c->pat.p, pat, pe, st)) || !k.ok(h2d(c->txt.p, txt, te, st))) return WFA_GPU_ECUDA;
-    *d_pat = c->pat.p;
-    *d_txt = c->txt.p;
+    const void* mp = mapped_range(pat, pe);
+    const void* mt = mapped_range(txt, te);
+    if (mp || pe == 0) {
+      *d_pat = mp ? static_cast<const char*>(mp) : pat;
+    } else {
+      if ((e = c->pat.ensure(pe + 16))) return map_alloc(e);
+      if (!k.ok(h2d(c->pat.p, pat, pe, st))) return WFA_GPU_ECUDA;
+      *d_pat = c->pat.p;
+    }
+    if (mt || te == 0) {
+      *d_txt = mt ? static_cast<const char*>(mt) : txt;
+    } else {
+      if ((e = c->txt.ensure(te + 16))) return map_alloc(e);
+      if (!k.ok(h2d(c->txt.p, txt, te, st))) return WFA_GPU_ECUDA;
+      *d_txt = c->txt.p;
+    }
   }
   return 0;
 }
@@ -213,10 +268,13 @@ constexpr int64_t kTuneSample = 8192;
 // variant index, or -1 on a CUDA error.
 int autotune_short(wfa_gpu_ctx* c, Call& k, const wfa::AlignArgs& a_in, int64_t n) {
   if (c->variant_forced >= 0) return c->variant_forced;
-  const wfa::ShortVariant& small = c->plan.v[c->variant_small];
   wfa::UGeo tab[64];
   const wfa::ScaledPen pen{a_in.xs, a_in.oes, a_in.es};
-  const int s_small = wfa::build_ugeo(tab, small.scap, small.cells, pen);
+  int s_store[3];
+  for (int j = 0; j < 3; ++j) {
+    const wfa::ShortVariant& v = c->plan.v[c->variants_small[j]];
+    s_store[j] = wfa::build_ugeo(tab, v.scap, v.cells, pen);
+  }
   const int64_t m = std::min(n, kTuneSample);
   cudaStream_t st = c->stream;
   if (c->tune_score.ensure(m) || c->tune_status.ensure(m) || c->tune_aux.ensure(m) || c->tune_src.ensure(m))
@@ -236,14 +294,16 @@ int autotune_short(wfa_gpu_ctx* c, Call& k, const wfa::AlignArgs& a_in, int64_t 
   if (!k.ok(cudaMemsetAsync(a.score, 0xff, m * sizeof(int32_t), st))) return -1;
   if (!k.launched(wfa::launch_short(a, c->plan.v[c->variant_big], st))) return -1;
   if (!k.ok(d2h(c->h_tune, c->tune_score.p, m * sizeof(int32_t), st)) || !k.ok(cudaStreamSynchronize(st))) return -1;
-  int64_t fit = 0, tot = 0;
+  int64_t fit[3] = {0, 0, 0}, tot = 0;
   for (int64_t i = 0; i < m; ++i) {
     const int sc = c->h_tune[i];
     if (sc < 0) continue;  // deferred, invalid or over the bound: not informative
     ++tot;
-    if (sc / a.g <= s_small) ++fit;
+    for (int j = 0; j < 3; ++j) fit[j] += (sc / a.g <= s_store[j]);
   }
-  return (tot == 0 || fit * 100 >= tot * 99) ? c->variant_small : c->variant_big;
+  for (int j = 0; j < 3; ++j)
+    if (tot == 0 || fit[j] * 100 >= tot * 99) return c->variants_small[j];
+  return c->variant_big;
 }
 
 }  // namespace

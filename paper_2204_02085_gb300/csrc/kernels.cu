@@ -316,6 +316,7 @@ cudaError_t short_plan(int device, ShortPlan* plan) {
   if ((e = plan_one<1, 127, 64, 15, int8_t>(device, &plan->v[i++], "g1_l127_c64_i8"))) return e;
   if ((e = plan_one<2, 255, 208, 31, int16_t>(device, &plan->v[i++], "g2_l255_c208_i16"))) return e;
   if ((e = plan_one<4, 255, 208, 31, int16_t>(device, &plan->v[i++], "g4_l255_c208_i16"))) return e;
+  if ((e = plan_one<1, 127, 40, 15, int8_t>(device, &plan->v[i++], "g1_l127_c40_i8"))) return e;
   plan->count = i;
   return cudaSuccess;
 }

@@ -62,7 +62,7 @@ struct ShortVariant {
   int scap;     // largest score index of the geometry table
 };
 struct ShortPlan {
-  ShortVariant v[8];
+  ShortVariant v[12];
   int count;
 };
 cudaError_t short_plan(int device, ShortPlan* plan);

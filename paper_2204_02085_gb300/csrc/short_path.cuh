@@ -29,14 +29,23 @@ __device__ __forceinline__ void write_result(const AlignArgs& a, int64_t pair, i
 template <int G, int LMAX, int CELLS, int SCAP, typename Off>
 struct ShortCfg {
   static constexpr int P = 32 / G;
-  static constexpr int NW = (LMAX + 31) / 32 + 1;  // data words + pad word
+  // packed sequence: 32-bit words (16 bases), data + two zero pad words,
+  // stored every PS elements (PS = P + 1 keeps the lanes of one pair on
+  // different banks)
+  static constexpr int NW = 2 * ((LMAX + 31) / 32 + 1);
+  static constexpr int PS = P + 1;
   struct WarpShm {
-    uint64_t pw[NW * P];
-    uint64_t tw[NW * P];
+    uint32_t pw[NW * PS];
+    uint32_t tw[NW * PS];
     Off M[CELLS * P];
     Off I[CELLS * P];
     Off D[CELLS * P];
   };
+  // the packer's span scratch (codes + bad-byte masks of up to P
+  // back-to-back sequences) borrows the cell arrays, unused while packing
+  static constexpr int SPAN = (P * LMAX + 15) / 16 + 1;
+  static_assert((SPAN + 1) * (sizeof(uint32_t) + sizeof(uint16_t)) <= 3 * CELLS * P * sizeof(Off),
+                "packer scratch does not fit the cell arrays");
   static constexpr size_t kTabBytes = ((SCAP + 1) * sizeof(UGeo) + 15) / 16 * 16;
   static constexpr size_t kWarpBytes = (sizeof(WarpShm) + 15) / 16 * 16;
   static constexpr size_t smem_bytes(int warps) { return kTabBytes + (size_t)warps * kWarpBytes; }
@@ -67,8 +76,9 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
   const int s_hi = min(s_store, a.s_cap);
   const unsigned gmask = group_mask(G);
   UView<Off, P> view{tab, W->M, W->I, W->D, q};
-  uint64_t* pw = W->pw + q;
-  uint64_t* tw = W->tw + q;
+  constexpr int PS = C::PS;
+  uint32_t* pw = W->pw + q;
+  uint32_t* tw = W->tw + q;
   const int64_t wpb = blockDim.x >> 5;
   const int64_t stride = (int64_t)gridDim.x * wpb * P;
   for (int64_t first = ((int64_t)blockIdx.x * wpb + warp) * P; first < a.n; first += stride) {
@@ -83,10 +93,14 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
         active = false;
       }
     }
-    if (active) {
-      const bool okp = pack_seq_strided<G>(a.pat + a.poff[pair], n, pw, P, lane, gmask);
-      const bool okt = pack_seq_strided<G>(a.txt + a.toff[pair], m, tw, P, lane, gmask);
-      if (!(okp && okt)) {
+    {
+      // all lanes take part: the warp reads its pairs' sequences together
+      uint32_t* scratch = reinterpret_cast<uint32_t*>(W->M);
+      const bool okp = pack_warp32<G, C::SPAN>(active ? a.pat + a.poff[pair] : nullptr, n, active, pw, PS, scratch,
+                                               lane, gmask);
+      const bool okt = pack_warp32<G, C::SPAN>(active ? a.txt + a.toff[pair] : nullptr, m, active, tw, PS, scratch,
+                                               lane, gmask);
+      if (active && !(okp && okt)) {
         if (lane == 0) write_result(a, pair, 2, -1, 0, 0);
         active = false;
       }
@@ -94,7 +108,7 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
     __syncwarp();
     const int kf = m - n;
     int s_fin = -1;
-    if (active && lane == 0) view.put(0, 0, extend_diag(pw, tw, n, m, 0, 0, P), NUL, NUL);
+    if (active && lane == 0) view.put(0, 0, extend_diag32(pw, tw, n, m, 0, 0, PS), NUL, NUL);
     __syncwarp();
     if (active && kf == 0 && view.getM(Geo{0, 1, 0}, 0) == m) {
       s_fin = 0;
@@ -121,7 +135,7 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
           int xv = mx + 1;
           if (mx < 0 || xv > m || xv - k > n) xv = NUL;
           int mv = max(xv, max(iv, dv));
-          mv = mv >= 0 ? extend_diag(pw, tw, n, m, k, mv, P) : NUL;
+          mv = mv >= 0 ? extend_diag32(pw, tw, n, m, k, mv, PS) : NUL;
           view.put(g.base, i, mv, iv, dv);
         }
       }

@@ -134,7 +134,151 @@ __device__ __forceinline__ bool pack_seq_strided(const char* __restrict__ seq, i
   return __any_sync(gmask, bad) == 0;
 }
 
+// As pack_seq_strided, into 32-bit words (16 bases each, first base in the
+// top bits): 64-bit word w becomes 32-bit words 2w (high half) and 2w + 1.
+// Writes ceil(len/32)*2 + 2 words, the last two zero.
+template <int G>
+__device__ __forceinline__ bool pack_seq_strided32(const char* __restrict__ seq, int len, uint32_t* out, int stride,
+                                                   int lane, unsigned gmask) {
+  const int nwords = (len + 31) >> 5;
+  bool bad = false;
+  for (int w = lane; w <= nwords; w += G) {
+    const uint64_t v = (w < nwords) ? pack_word(seq, len, w, &bad) : 0ull;
+    out[(2 * w) * stride] = (uint32_t)(v >> 32);
+    out[(2 * w + 1) * stride] = (uint32_t)v;
+  }
+  return __any_sync(gmask, bad) == 0;
+}
+
+// 16 ASCII bytes -> 16 two-bit codes (first byte in the top bits) and, in
+// *bad16, bit i set when byte i is not A/C/G/T in either case.  The check
+// rebuilds the upper-case letter of each byte's code (A C G T = 0x41 0x43
+// 0x47 0x54 = 0x41 + 2 b0 + 6 b1 + 11 b0 b1 for code bits b1 b0) and
+// compares it with the byte folded to upper case.
+__device__ __forceinline__ uint32_t code16_bad(uint4 v, uint32_t* bad16) {
+  const uint32_t q[4] = {v.x, v.y, v.z, v.w};
+  uint32_t code = 0, bad = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t w = q[i];
+    const uint32_t c = ((w >> 1) ^ (w >> 2)) & 0x03030303u;
+    const uint32_t b0 = c & 0x01010101u, b1 = (c >> 1) & 0x01010101u;
+    const uint32_t f = 0x41414141u + 2u * b0 + 6u * b1 + 11u * (b0 & b1);
+    const uint32_t x = (w & 0xDFDFDFDFu) ^ f;                                   // zero byte <=> valid
+    const uint32_t hb = ((((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) >> 7) & 0x01010101u;  // 1 per bad byte
+    bad |= ((hb * 0x01020408u) >> 24 & 0xFu) << (4 * i);
+    code = (code << 8) | ((c * 0x40100401u) >> 24);  // 4 codes, first in the top bits
+  }
+  *bad16 = bad;
+  return code;
+}
+
+// Warp-cooperative packing of one sequence per pair slot of a warp (P pair
+// slots of G lanes).  When the active slots' sequences lie in one span of at
+// most 16 * SPAN_CHUNKS bytes, the warp reads the span once with coalesced
+// 16-byte loads into shared scratch (codes + bad-byte masks) and every slot
+// cuts its 32-bit words (16 bases, first base in the top bits) from it;
+// otherwise every slot reads its own chunks.  Slot q writes words
+// 0 .. ceil(len/16) (the last one zero) to out[j * stride].  scratch holds
+// SPAN_CHUNKS + 1 uint32 codes then SPAN_CHUNKS + 1 uint16 masks.  Returns, per
+// slot, whether every byte of its sequence is A/C/G/T.  All 32 lanes call it.
+template <int G, int SPAN_CHUNKS>
+__device__ __forceinline__ bool pack_warp32(const char* seq, int len, bool active, uint32_t* out, int stride,
+                                            uint32_t* scratch, int lane, unsigned gmask) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane32 = threadIdx.x & 31;
+  const unsigned long long a = reinterpret_cast<uintptr_t>(seq);
+  unsigned long long lo = active && len > 0 ? a : ~0ull;
+  unsigned long long hi = active && len > 0 ? a + (unsigned)len : 0ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long l2 = __shfl_xor_sync(FULL, lo, o), h2 = __shfl_xor_sync(FULL, hi, o);
+    lo = l2 < lo ? l2 : lo;
+    hi = h2 > hi ? h2 : hi;
+  }
+  const int nw = (len + 15) >> 4;  // data words of this slot
+  bool bad = false;
+  if (hi > lo && hi - (lo & ~15ull) <= 16ull * SPAN_CHUNKS) {
+    const unsigned long long base = lo & ~15ull;
+    const int nch = (int)((hi - base + 15) >> 4);
+    uint16_t* masks = reinterpret_cast<uint16_t*>(scratch + SPAN_CHUNKS + 1);
+    for (int c = lane32; c < nch; c += 32) {
+      uint32_t b16;
+      scratch[c] = code16_bad(__ldg(reinterpret_cast<const uint4*>(base + 16ull * c)), &b16);
+      masks[c] = (uint16_t)b16;
+    }
+    if (lane32 == 0) {
+      scratch[nch] = 0u;
+      masks[nch] = 0;
+    }
+    __syncwarp();
+    if (active) {
+      const int off = (int)(a - base);  // bytes from the span start
+      const int c0 = off >> 4, r = (off & 15) << 1;
+      for (int j = lane; j <= nw; j += G) {
+        uint32_t word = 0u;
+        if (j < nw) {
+          word = __funnelshift_l(scratch[c0 + j + 1], scratch[c0 + j], r);
+          const int rem = len - 16 * j;
+          if (rem < 16) word &= ~0u << (32 - 2 * rem);
+          // bad bytes among this word's 16 (at most 2 chunks)
+          const uint32_t m2 = (uint32_t)masks[c0 + j] | ((uint32_t)masks[c0 + j + 1] << 16);
+          const int nb = min(16, rem);
+          const uint32_t in = (nb >= 16 ? 0xFFFFu : ((1u << nb) - 1u)) << (off & 15);
+          if (m2 & in) bad = true;
+        }
+        out[j * stride] = word;
+      }
+    }
+    __syncwarp();
+  } else if (active) {
+    for (int j = lane; j <= nw; j += G) {
+      uint32_t word = 0u;
+      if (j < nw) {
+        // the 16 bytes of word j span at most two aligned chunks
+        const unsigned long long w0 = a + 16ull * j, b0 = w0 & ~15ull;
+        const int h = (int)(w0 - b0), rem = min(16, len - 16 * j);
+        uint32_t m0, m1 = 0u, c1 = 0u;
+        const uint32_t c0 = code16_bad(__ldg(reinterpret_cast<const uint4*>(b0)), &m0);
+        if (h + rem > 16) c1 = code16_bad(__ldg(reinterpret_cast<const uint4*>(b0 + 16)), &m1);
+        word = __funnelshift_l(c1, c0, 2 * h);
+        if (rem < 16) word &= ~0u << (32 - 2 * rem);
+        const uint32_t in = (rem >= 16 ? 0xFFFFu : ((1u << rem) - 1u)) << h;
+        if ((m0 | (m1 << 16)) & in) bad = true;
+      }
+      out[j * stride] = word;
+    }
+  }
+  return __any_sync(gmask, bad) == 0;
+}
+
 // ----------------------------------------------------------------- extend
+
+// 16 bases starting at base position pos of a sequence packed into 32-bit
+// words stored every `stride` elements (reads words pos/16 and pos/16 + 1).
+__device__ __forceinline__ uint32_t window32s(const uint32_t* W, int pos, int stride) {
+  const int j = pos >> 4;
+  return __funnelshift_l(W[(j + 1) * stride], W[j * stride], (pos & 15) << 1);
+}
+
+// extend_diag over 32-bit packed words: 16 bases per compare.
+__device__ __forceinline__ int extend_diag32(const uint32_t* pw, const uint32_t* tw, int n, int m, int k, int h,
+                                             int stride) {
+  for (;;) {
+    const int v = h - k;
+    const int rem = min(n - v, m - h);
+    if (rem <= 0) break;
+    const uint32_t d = window32s(pw, v, stride) ^ window32s(tw, h, stride);
+    const int eq = __clz(d) >> 1;  // 16 when the windows are equal
+    if (eq >= rem) {
+      h += rem;
+      break;
+    }
+    h += eq;
+    if (eq < 16) break;
+  }
+  return h;
+}
 
 // 32 bases starting at base position pos of a packed sequence (reads words
 // pos/32 and pos/32 + 1; the pad word makes the second one exist).

@@ -220,6 +220,30 @@ def test_device_pointers_match_host_path(pkg, al, oracle_mod):
         al.set_stream(None)
 
 
+def test_page_locked_host_inputs(pkg, al, oracle_mod):
+    """Host-pointer calls whose buffers are page-locked (read by the kernels
+    in place over the host link) give the oracle's results, as pageable
+    buffers (copied) do."""
+    import torch
+
+    from paper_2204_02085_gb300 import synth
+
+    b = synth.random_pairs(900, 0, 300, seed=52, edit_rate=0.04)
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype={np.uint8: torch.uint8, np.int32: torch.int32,
+                                         np.int64: torch.int64}[a.dtype.type], pin_memory=True)
+        t.numpy()[...] = a
+        return t.numpy()
+
+    pb = synth.Batch(pinned(b.patterns), pinned(b.pattern_offsets), pinned(b.pattern_lengths), pinned(b.texts),
+                     pinned(b.text_offsets), pinned(b.text_lengths))
+    want = oracle_run(oracle_mod, b, (4, 6, 2))
+    assert_same(al.align(pb, (4, 6, 2)), want)
+    assert_same(al.align(pb, (4, 6, 2), use_offsets=False), want)
+    assert_same(al.align(b, (4, 6, 2)), want)
+
+
 def test_repeated_calls_are_stable(al, oracle_mod):
     """The same batch twice, with other batches between, gives identical
     output (no state leaks between calls)."""
