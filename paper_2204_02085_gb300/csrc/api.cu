@@ -65,7 +65,8 @@ struct wfa_gpu_ctx {
   cudaStream_t stream = nullptr;
   int32_t* arena = nullptr;
   size_t arena_bytes = 0;
-  int general_warps = 1;
+  int teams_medium = 1;  // one-warp arena teams
+  int teams_long = 1;    // one-CTA arena teams
   wfa::ShortPlan plan{};
   // short-kernel variants (indices into plan.v): for sequences <= 127 bases
   // a small-store variant and a large-store one, chosen per batch from a
@@ -92,10 +93,10 @@ struct wfa_gpu_ctx {
   DevBuf<int64_t> cig_off;
   DevBuf<uint32_t> cig;
   // internal
-  DevBuf<int32_t> nruns, defer, overflow;
+  DevBuf<int32_t> nruns, defer, defer_long, overflow;
   DevBuf<int64_t> run_src, scan_tmp;
-  DevBuf<uint32_t> runs;
-  int64_t pool_words = kPoolInitWords;
+  DevBuf<uint32_t> runs, pool;
+  int64_t pool_words = kPoolInitWords;  // CIGAR words the arena pool holds
   // autotuner sample outputs
   DevBuf<int32_t> tune_score, tune_aux;
   DevBuf<int8_t> tune_status;
@@ -259,6 +260,67 @@ int stage_inputs(wfa_gpu_ctx* c, Call& k, int64_t n, bool dev, const char* pat, 
   return 0;
 }
 
+// The arena kernels over the pairs the short kernel deferred (medium pairs
+// on one-warp teams, long ones on one-CTA teams), then retries of the pairs
+// that did not fit: fewer, larger arena slices on one-CTA teams, or a larger
+// CIGAR pool.  A pair that does not fit the whole arena gives ENOMEM.
+int run_arena(wfa_gpu_ctx* c, Call& k, wfa::AlignArgs& a) {
+  cudaStream_t st = c->stream;
+  wfa::Ctrl* hc = c->h_ctrl;
+  wfa::Ctrl* dc = c->ctrl;
+  const long arena = (long)c->arena_bytes;
+  if (hc->defer_count > 0 &&
+      !k.launched(wfa::launch_arena(false, a, a.defer_list, &dc->defer_count, &dc->next_medium, &dc->overflow_count,
+                                    reinterpret_cast<unsigned char*>(c->arena), (arena / c->teams_medium) & ~255L, c->teams_medium, st)))
+    return WFA_GPU_ECUDA;
+  if (hc->defer_long_count > 0 &&
+      !k.launched(wfa::launch_arena(true, a, a.defer_long_list, &dc->defer_long_count, &dc->next_long,
+                                    &dc->overflow_count, reinterpret_cast<unsigned char*>(c->arena), (arena / c->teams_long) & ~255L, c->teams_long,
+                                    st)))
+    return WFA_GPU_ECUDA;
+  if (!k.ok(d2h(hc, dc, sizeof(wfa::Ctrl), st)) || !k.ok(cudaStreamSynchronize(st))) return WFA_GPU_ECUDA;
+  int teams = c->teams_long;
+  int32_t* in = a.overflow_list;  // the pairs to retry
+  int32_t* out = a.defer_list;    // free again: receives the next overflow
+  while (hc->overflow_count > 0) {
+    if (hc->pool_short) {
+      // keep the runs already written, and at least double the pool
+      const int64_t used = std::min<int64_t>((int64_t)hc->pool_top, (int64_t)c->pool.cap);
+      const int64_t want = 2 * (int64_t)hc->pool_top + (1 << 22);
+      uint32_t* nb = nullptr;
+      cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&nb), (size_t)want * sizeof(uint32_t));
+      if (e != cudaSuccess) return map_alloc(e);
+      if (!k.ok(cudaMemcpyAsync(nb, c->pool.p, (size_t)used * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st)) ||
+          !k.ok(cudaStreamSynchronize(st))) {
+        cudaFree(nb);
+        return WFA_GPU_ECUDA;
+      }
+      cudaFree(c->pool.p);
+      c->pool.p = nb;
+      c->pool.cap = (size_t)want;
+      c->pool_words = want;
+      a.pool = nb;
+      a.pool_cap = want;
+    } else {
+      if (teams == 1) return WFA_GPU_ENOMEM;  // a pair needs more than the whole arena
+      teams = std::max(1, teams / 8);
+    }
+    hc->retry_count = hc->overflow_count;
+    hc->next_retry = 0;
+    hc->overflow_count = 0;
+    hc->pool_short = 0;
+    if (!k.ok(cudaMemcpyAsync(dc, hc, sizeof(wfa::Ctrl), cudaMemcpyHostToDevice, st))) return WFA_GPU_ECUDA;
+    wfa::AlignArgs ar = a;
+    ar.overflow_list = out;
+    if (!k.launched(wfa::launch_arena(true, ar, in, &dc->retry_count, &dc->next_retry, &dc->overflow_count, reinterpret_cast<unsigned char*>(c->arena),
+                                      (arena / teams) & ~255L, teams, st)))
+      return WFA_GPU_ECUDA;
+    if (!k.ok(d2h(hc, dc, sizeof(wfa::Ctrl), st)) || !k.ok(cudaStreamSynchronize(st))) return WFA_GPU_ECUDA;
+    std::swap(in, out);
+  }
+  return 0;
+}
+
 constexpr int64_t kTuneSample = 8192;
 
 // Pick the short-kernel variant for a batch of sequences <= 127 bases: the
@@ -349,7 +411,8 @@ int wfa_gpu_create(wfa_gpu_ctx** out, int device, size_t scratch_bytes) {
     }
     int nsm = 1;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
-    c->general_warps = std::max(1, nsm * 4);
+    c->teams_medium = std::max(1, nsm * 16);
+    c->teams_long = std::max(1, nsm * 2);
   } while (0);
   if (rc) {
     wfa_gpu_destroy(c);
@@ -415,9 +478,10 @@ int wfa_gpu_align_batch(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const
     d_score = ctx->score.p;
     d_status = ctx->status.p;
   }
-  const int64_t pool_base = score_only ? 0 : n * (int64_t)wfa::kSlot;
+  const int64_t slot_words = score_only ? 1 : n * (int64_t)wfa::kSlot;
   if ((e = ctx->nruns.ensure(n)) || (e = ctx->run_src.ensure(n)) || (e = ctx->defer.ensure(n)) ||
-      (e = ctx->overflow.ensure(n)) || (e = ctx->runs.ensure(pool_base + (score_only ? 1 : ctx->pool_words))))
+      (e = ctx->defer_long.ensure(n)) || (e = ctx->overflow.ensure(n)) || (e = ctx->runs.ensure(slot_words)) ||
+      (e = ctx->pool.ensure(score_only ? 1 : ctx->pool_words)))
     return map_alloc(e);
 
   wfa::AlignArgs a{};
@@ -435,9 +499,10 @@ int wfa_gpu_align_batch(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const
   a.nruns = ctx->nruns.p;
   a.run_src = ctx->run_src.p;
   a.runs = ctx->runs.p;
-  a.pool_base = pool_base;
-  a.pool_cap = score_only ? 0 : (int64_t)ctx->runs.cap - pool_base;
+  a.pool = ctx->pool.p;
+  a.pool_cap = score_only ? 0 : (int64_t)ctx->pool.cap;
   a.defer_list = ctx->defer.p;
+  a.defer_long_list = ctx->defer_long.p;
   a.overflow_list = ctx->overflow.p;
   a.ctrl = ctx->ctrl;
 
@@ -449,49 +514,13 @@ int wfa_gpu_align_batch(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const
   ctx->last_variant = vi;
   if (!k.launched(wfa::launch_short(a, ctx->plan.v[vi], st))) return fail_cuda(k);
   k.rec(2);
-  int nwarps = ctx->general_warps;
-  const long arena_ints = (long)(ctx->arena_bytes / sizeof(int32_t));
-  long slot = (arena_ints / nwarps) & ~3L;
-  if (!k.launched(wfa::launch_general(a, ctx->arena, slot, nwarps, st))) return fail_cuda(k);
   if (!k.ok(d2h(ctx->h_ctrl, ctx->ctrl, sizeof(wfa::Ctrl), st)) || !k.ok(cudaStreamSynchronize(st)))
     return fail_cuda(k);
-  ctx->last.deferred_pairs = ctx->h_ctrl->defer_count;
-  // Pairs that did not fit their arena slot (or the CIGAR pool) run again
-  // with fewer, larger slots (or a larger pool).
-  while (ctx->h_ctrl->overflow_count > 0) {
-    wfa::Ctrl* hc = ctx->h_ctrl;
-    if (hc->pool_short) {
-      const int64_t used = pool_base + (int64_t)hc->pool_top;
-      const int64_t want = pool_base + 2 * (int64_t)hc->pool_top + kPoolInitWords;
-      uint32_t* nb = nullptr;
-      if ((e = cudaMalloc(reinterpret_cast<void**>(&nb), (size_t)want * sizeof(uint32_t)))) return map_alloc(e);
-      if (!k.ok(cudaMemcpyAsync(nb, ctx->runs.p, (size_t)std::min<int64_t>(used, ctx->runs.cap) * sizeof(uint32_t),
-                                cudaMemcpyDeviceToDevice, st)) ||
-          !k.ok(cudaStreamSynchronize(st))) {
-        cudaFree(nb);
-        return fail_cuda(k);
-      }
-      cudaFree(ctx->runs.p);
-      ctx->runs.p = nb;
-      ctx->runs.cap = (size_t)want;
-      ctx->pool_words = want - pool_base;
-      a.runs = nb;
-      a.pool_cap = want - pool_base;
-    } else {
-      if (nwarps == 1) return WFA_GPU_ENOMEM;  // a pair needs more than the whole arena
-      nwarps = std::max(1, nwarps / 8);
-      slot = (arena_ints / nwarps) & ~3L;
-    }
-    std::swap(a.defer_list, a.overflow_list);
-    hc->defer_count = hc->overflow_count;
-    hc->general_next = 0;
-    hc->overflow_count = 0;
-    hc->pool_short = 0;
-    if (!k.ok(cudaMemcpyAsync(ctx->ctrl, hc, sizeof(wfa::Ctrl), cudaMemcpyHostToDevice, st))) return fail_cuda(k);
-    if (!k.launched(wfa::launch_general(a, ctx->arena, slot, nwarps, st))) return fail_cuda(k);
-    if (!k.ok(d2h(hc, ctx->ctrl, sizeof(wfa::Ctrl), st)) || !k.ok(cudaStreamSynchronize(st))) return fail_cuda(k);
-  }
-  if (ctx->h_ctrl->internal_error) return WFA_GPU_ECUDA;
+  ctx->last.deferred_pairs = (int64_t)ctx->h_ctrl->defer_count + ctx->h_ctrl->defer_long_count;
+  if (ctx->last.deferred_pairs > 0) {
+    rc = run_arena(ctx, k, a);
+    if (rc) return rc;
+  }  if (ctx->h_ctrl->internal_error) return WFA_GPU_ECUDA;
   k.rec(3);
 
   int64_t total = 0;
@@ -511,7 +540,8 @@ int wfa_gpu_align_batch(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const
         if ((e = ctx->cig.ensure(total))) return map_alloc(e);
         d_cig = ctx->cig.p;
       }
-      if (!k.launched(wfa::launch_compact(n, ctx->nruns.p, ctx->run_src.p, ctx->runs.p, d_off, d_cig, cap, st)))
+      if (!k.launched(
+              wfa::launch_compact(n, ctx->nruns.p, ctx->run_src.p, ctx->runs.p, ctx->pool.p, d_off, d_cig, cap, st)))
         return fail_cuda(k);
     }
   }
@@ -658,6 +688,7 @@ void wfa_gpu_destroy(wfa_gpu_ctx* c) {
   c->poff.release(); c->toff.release(); c->score.release(); c->status.release();
   c->cig_off.release(); c->cig.release(); c->nruns.release(); c->defer.release();
   c->overflow.release(); c->run_src.release(); c->scan_tmp.release(); c->runs.release();
+  c->defer_long.release(); c->pool.release();
   if (c->arena) cudaFree(c->arena);
   if (c->ctrl) cudaFree(c->ctrl);
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);

@@ -1,0 +1,355 @@
+// arena_path.cuh -- the gap-affine WFA for pairs that do not fit the
+// short-read kernel: medium and long reads, or high scores.
+//
+// A team -- one warp, or a whole CTA of WPP warps for long reads -- owns one
+// pair at a time; its threads stride over the diagonals of each wavefront.
+// Both sequences are packed (2 bits per base) into the team's shared memory
+// when they fit, else into its slice of the global scratch arena.  The
+// wavefronts live in that slice: every score's M/I/D block (int16 offsets
+// when both sequences are shorter than 32,767, else int32) for score +
+// CIGAR, or only a ring of the last max(x, o+e, e) + 1 scores when just the
+// score is wanted (memory linear in the wavefront width).  Pairs come from
+// a device work queue (an atomic counter over a list of pair indices).
+#pragma once
+
+#include "launch.h"
+#include "short_path.cuh"
+#include "wfa_device.cuh"
+
+namespace wfa {
+
+// Threads that work on one pair: a warp (WPP == 1) or a CTA of WPP warps.
+template <int WPP>
+struct Team {
+  static constexpr int kSize = 32 * WPP;
+  __device__ static int rank() { return WPP == 1 ? (int)(threadIdx.x & 31) : (int)threadIdx.x; }
+  __device__ static void sync() {
+    if (WPP == 1) __syncwarp();
+    else __syncthreads();
+  }
+  // OR of `bits` over the team; a barrier for the team as well.  `flags`
+  // points at the team's three rotating shared words; `round` counts calls.
+  __device__ static int reduce_or(int bits, int* flags, int& round) {
+    if (WPP == 1) {
+      __syncwarp();  // orders the team's memory writes before its next reads
+      return __reduce_or_sync(0xffffffffu, bits);
+    }
+    const int w = __reduce_or_sync(0xffffffffu, bits);
+    volatile int* f = flags + (round % 3);
+    if ((threadIdx.x & 31) == 0 && w) atomicOr(flags + (round % 3), w);
+    if (threadIdx.x == 0) flags[(round + 1) % 3] = 0;
+    ++round;
+    __syncthreads();
+    return *f;
+  }
+  // rank 0's value of v, for every member
+  __device__ static int broadcast(int v, int* slot) {
+    if (WPP == 1) return __shfl_sync(0xffffffffu, v, 0);
+    if (threadIdx.x == 0) *slot = v;
+    __syncthreads();
+    const int r = *(volatile int*)slot;
+    __syncthreads();
+    return r;
+  }
+};
+
+// Every score's wavefront kept in an arena slice.  Per-score metadata (4
+// ints: lo, hi, base, exist bits) grows up from `meta`; each block
+// [M w][I w][D w] of Off grows down from `end`; `base` counts elements from
+// `end` to the block start.  Metadata and blocks meet at cap_bytes.
+template <typename OffT>
+struct ArenaViewT {
+  using Off = OffT;
+  int32_t* meta;
+  OffT* end;
+  long cap_bytes;
+
+  __device__ __forceinline__ int lo_of(int s) const { return meta[4 * s]; }
+  __device__ __forceinline__ int hi_of(int s) const { return meta[4 * s + 1]; }
+  __device__ __forceinline__ int base_of(int s) const { return meta[4 * s + 2]; }
+  __device__ __forceinline__ int ex_of(int s) const { return meta[4 * s + 3]; }
+  __device__ __forceinline__ void set_meta(int s, int l, int h, int b, int e) {
+    meta[4 * s] = l; meta[4 * s + 1] = h; meta[4 * s + 2] = b; meta[4 * s + 3] = e;
+  }
+  __device__ __forceinline__ void set_absent(int s) { meta[4 * s + 3] = 0; }
+  __device__ __forceinline__ bool score_ok(int s, int top) const {
+    return 16L * (s + 1) + (long)top * (long)sizeof(OffT) <= cap_bytes;
+  }
+  __device__ __forceinline__ bool alloc(int s, int w, int& top, int& b) const {
+    const long elems = (long)top + 3L * w;
+    if (16L * (s + 1) + elems * (long)sizeof(OffT) > cap_bytes || elems > INT_MAX) return false;
+    top = (int)elems;
+    b = top;
+    return true;
+  }
+  __device__ __forceinline__ void release(int b, int& top) const {
+    (void)b;
+    (void)top;
+  }
+  __device__ __forceinline__ const OffT* blk(const Geo& g) const { return end - g.base; }
+  __device__ __forceinline__ int getM(const Geo& g, int i) const { return blk(g)[i]; }
+  __device__ __forceinline__ int getI(const Geo& g, int i) const { return blk(g)[g.w + i]; }
+  __device__ __forceinline__ int getD(const Geo& g, int i) const { return blk(g)[2 * g.w + i]; }
+  __device__ __forceinline__ void put(int b, int w, int i, int mv, int iv, int dv) {
+    OffT* q = end - b;
+    q[i] = (OffT)mv; q[w + i] = (OffT)iv; q[2 * w + i] = (OffT)dv;
+  }
+};
+
+// Only the last R scores: score s lives in ring slot s % R, a block
+// [M W][I W][D W] with W the widest possible wavefront; metadata likewise in
+// a ring.  Enough for the recurrences, not for a backtrace.
+template <typename OffT>
+struct RingView {
+  using Off = OffT;
+  int32_t* meta;  // 4 ints per ring slot
+  OffT* cells;    // R blocks of 3 W
+  int R, W;
+
+  __device__ __forceinline__ int slot(int s) const { return s % R; }
+  __device__ __forceinline__ int lo_of(int s) const { return meta[4 * slot(s)]; }
+  __device__ __forceinline__ int hi_of(int s) const { return meta[4 * slot(s) + 1]; }
+  __device__ __forceinline__ int base_of(int s) const { return meta[4 * slot(s) + 2]; }
+  __device__ __forceinline__ int ex_of(int s) const { return meta[4 * slot(s) + 3]; }
+  __device__ __forceinline__ void set_meta(int s, int l, int h, int b, int e) {
+    const int r = 4 * slot(s);
+    meta[r] = l; meta[r + 1] = h; meta[r + 2] = b; meta[r + 3] = e;
+  }
+  __device__ __forceinline__ void set_absent(int s) { meta[4 * slot(s) + 3] = 0; }
+  __device__ __forceinline__ bool score_ok(int s, int top) const {
+    (void)s;
+    (void)top;
+    return true;
+  }
+  __device__ __forceinline__ bool alloc(int s, int w, int& top, int& b) const {
+    (void)top;
+    if (w > W) return false;
+    b = slot(s) * 3 * W;
+    return true;
+  }
+  __device__ __forceinline__ void release(int b, int& top) const {
+    (void)b;
+    (void)top;
+  }
+  __device__ __forceinline__ int getM(const Geo& g, int i) const { return cells[g.base + i]; }
+  __device__ __forceinline__ int getI(const Geo& g, int i) const { return cells[g.base + W + i]; }
+  __device__ __forceinline__ int getD(const Geo& g, int i) const { return cells[g.base + 2 * W + i]; }
+  __device__ __forceinline__ void put(int b, int w, int i, int mv, int iv, int dv) {
+    (void)w;
+    cells[b + i] = (OffT)mv; cells[b + W + i] = (OffT)iv; cells[b + 2 * W + i] = (OffT)dv;
+  }
+};
+
+// The score loop for one pair on a team (same recurrences, range rules and
+// outcomes as wfa_forward).  Metadata of each score is written by every
+// warp's lane 0 (identical values), so each warp reads its own writes.
+template <int WPP, class V>
+__device__ int team_forward(V& view, const uint64_t* pw, const uint64_t* tw, int n, int m, ScaledPen p, int s_cap,
+                            int* flags, int& round, int* s_out) {
+  using Off = typename V::Off;
+  using T = Team<WPP>;
+  constexpr int NUL = NullOf<Off>::value;
+  const int r = T::rank();
+  const bool leader = (threadIdx.x & 31) == 0;
+  const int kf = m - n;
+  int top = 0, b0 = 0;
+  if (!view.alloc(0, 1, top, b0)) return kFwdOverflow;
+  if (r == 0) view.put(b0, 1, 0, extend_diag(pw, tw, n, m, 0, 0), NUL, NUL);
+  if (leader) view.set_meta(0, 0, 0, b0, 1);
+  T::sync();
+  if (kf == 0 && view.getM(Geo{0, 1, b0}, 0) == m) {
+    *s_out = 0;
+    return kFwdOk;
+  }
+  for (int s = 1;; ++s) {
+    if (s > s_cap) return kFwdLimit;
+    if (!view.score_ok(s, top)) return kFwdOverflow;
+    const Geo gx = geo_of(view, s - p.x, 1);
+    const Geo go = geo_of(view, s - p.oe, 1);
+    const Geo gi = geo_of(view, s - p.e, 2);
+    const Geo gd = geo_of(view, s - p.e, 4);
+    int lo = INT_MAX, hi = INT_MIN;
+    if (gx.w) { lo = min(lo, gx.lo); hi = max(hi, gx.lo + gx.w - 1); }
+    if (go.w) { lo = min(lo, go.lo - 1); hi = max(hi, go.lo + go.w); }
+    if (gi.w) { lo = min(lo, gi.lo - 1); hi = max(hi, gi.lo + gi.w); }
+    if (gd.w) { lo = min(lo, gd.lo - 1); hi = max(hi, gd.lo + gd.w); }
+    lo = max(lo, -n);
+    hi = min(hi, m);
+    if (lo > hi) {
+      if (leader) view.set_absent(s);
+      __syncwarp();
+      continue;
+    }
+    const int w = hi - lo + 1;
+    int b = 0;
+    if (!view.alloc(s, w, top, b)) return kFwdOverflow;
+    int bits = 0;
+    for (int k = lo + r; k <= hi; k += T::kSize) {
+      const int mx = get_off<V, 0>(view, gx, k, NUL);
+      const int ml = get_off<V, 0>(view, go, k - 1, NUL);
+      const int mr = get_off<V, 0>(view, go, k + 1, NUL);
+      const int il = get_off<V, 1>(view, gi, k - 1, NUL);
+      const int dr = get_off<V, 2>(view, gd, k + 1, NUL);
+      int iv = max(ml, il) + 1;
+      if (iv < 0 || iv > m) iv = NUL;
+      int dv = max(mr, dr);
+      if (dv < 0 || dv - k > n) dv = NUL;
+      int xv = mx + 1;
+      if (mx < 0 || xv > m || xv - k > n) xv = NUL;
+      int mv = max(xv, max(iv, dv));
+      if (mv >= 0) {
+        mv = extend_diag(pw, tw, n, m, k, mv);
+        bits |= 1;
+      } else {
+        mv = NUL;
+      }
+      bits |= (iv >= 0 ? 2 : 0) | (dv >= 0 ? 4 : 0);
+      view.put(b, w, k - lo, mv, iv, dv);
+    }
+    const int exbits = T::reduce_or(bits, flags, round);  // also the barrier after the writes
+    if (exbits == 0) view.release(b, top);
+    if (leader) view.set_meta(s, lo, hi, b, exbits);
+    __syncwarp();
+    if ((exbits & 1) && kf >= lo && kf <= hi && view.getM(Geo{lo, w, b}, kf - lo) == m) {
+      *s_out = s;
+      return kFwdOk;
+    }
+  }
+}
+
+// Team packing of one sequence into out[0 .. ceil(len/32)] (64-bit words,
+// last one zero).  Returns, for every member, whether every byte is valid.
+template <int WPP>
+__device__ __forceinline__ bool team_pack(const char* __restrict__ seq, int len, uint64_t* out, int* flags,
+                                          int& round) {
+  const int nwords = (len + 31) >> 5;
+  bool bad = false;
+  for (int w = Team<WPP>::rank(); w <= nwords; w += Team<WPP>::kSize)
+    out[w] = (w < nwords) ? pack_word(seq, len, w, &bad) : 0ull;
+  return Team<WPP>::reduce_or(bad ? 1 : 0, flags, round) == 0;
+}
+
+__device__ __forceinline__ void overflow_pair_to(const AlignArgs& a, int64_t pair, int32_t* count) {
+  const int idx = atomicAdd(count, 1);
+  a.overflow_list[idx] = (int32_t)pair;
+}
+
+// After the forward pass of a pair (single thread): its outcome, and for a
+// score its CIGAR, backtraced into a reservation of the run pool.
+template <class V>
+__device__ void finish_cigar(const AlignArgs& a, const V& view, int64_t pair, int n, int m, ScaledPen pen, int res,
+                             int s, int32_t* overflow_count) {
+  if (res == kFwdOverflow) {
+    overflow_pair_to(a, pair, overflow_count);
+    return;
+  }
+  if (res == kFwdLimit) {
+    write_result(a, pair, 1, -1, 0, 0);
+    return;
+  }
+  long bound = runs_bound_scaled(s, pen.x, pen.oe);
+  if (bound > (long)n + m + 1) bound = (long)n + m + 1;
+  const unsigned long long pos = atomicAdd(&a.ctrl->pool_top, (unsigned long long)bound);
+  if ((long long)(pos + bound) > a.pool_cap) {
+    atomicExch(&a.ctrl->pool_short, 1);
+    overflow_pair_to(a, pair, overflow_count);
+    return;
+  }
+  const int64_t src = -(int64_t)pos - 1;  // negative: an index into the pool
+  const int nr = wfa_backtrace(view, n, m, pen, s, a.pool + pos, (int)bound);
+  if (nr < 0) {
+    atomicExch(&a.ctrl->internal_error, 1);
+    write_result(a, pair, 0, s * a.g, 0, src);
+  } else {
+    write_result(a, pair, 0, s * a.g, nr, src);
+  }
+}
+
+// Shared memory of one team: both packed sequences when they fit (seq_words
+// 64-bit words each), the rotating reduction words and a broadcast slot.
+struct TeamShm {
+  int flags[3];
+  int bcast;
+};
+
+template <int WPP>
+__device__ void arena_body(const AlignArgs& a, const int32_t* list, const int32_t* count, int32_t* next,
+                           int32_t* overflow_count, unsigned char* arena, long slot_bytes, int nteams,
+                           int seq_words, unsigned char* smem) {
+  using T = Team<WPP>;
+  const int team = WPP == 1 ? (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) : (int)blockIdx.x;
+  if (team >= nteams) return;  // whole team: uniform
+  const int team_in_block = WPP == 1 ? (int)(threadIdx.x >> 5) : 0;
+  const size_t team_smem = sizeof(TeamShm) + 2 * (size_t)seq_words * sizeof(uint64_t);
+  unsigned char* my = smem + team_in_block * team_smem;
+  TeamShm* ts = reinterpret_cast<TeamShm*>(my);
+  uint64_t* spw = reinterpret_cast<uint64_t*>(my + sizeof(TeamShm));
+  uint64_t* stw = spw + seq_words;
+  const int r = T::rank();
+  if (r == 0) ts->flags[0] = ts->flags[1] = ts->flags[2] = 0;
+  T::sync();
+  int round = 0;
+  unsigned char* slot = arena + (size_t)team * (size_t)slot_bytes;
+  const ScaledPen pen{a.xs, a.oes, a.es};
+  for (;;) {
+    const int idx = T::broadcast(r == 0 ? atomicAdd(next, 1) : 0, &ts->bcast);
+    if (idx >= *(volatile const int32_t*)count) break;
+    const int64_t pair = list[idx];
+    const int n = a.plen[pair], m = a.tlen[pair];
+    const long nwp = (n + 31) / 32 + 1, nwt = (m + 31) / 32 + 1;
+    // sequences in shared memory if they fit, else at the slice's start
+    const bool in_smem = nwp <= seq_words && nwt <= seq_words;
+    uint64_t* pw = in_smem ? spw : reinterpret_cast<uint64_t*>(slot);
+    uint64_t* tw = in_smem ? stw : reinterpret_cast<uint64_t*>(slot) + nwp;
+    const long seq_bytes = in_smem ? 0 : 8L * (nwp + nwt);
+    const long room = slot_bytes - seq_bytes;
+    if (room < 1024) {
+      if (r == 0) overflow_pair_to(a, pair, overflow_count);
+      T::sync();
+      continue;
+    }
+    const bool okp = team_pack<WPP>(a.pat + a.poff[pair], n, pw, ts->flags, round);
+    const bool okt = team_pack<WPP>(a.txt + a.toff[pair], m, tw, ts->flags, round);
+    if (!(okp && okt)) {
+      if (r == 0) write_result(a, pair, 2, -1, 0, 0);
+      T::sync();
+      continue;
+    }
+    unsigned char* wf = slot + seq_bytes;
+    int s = 0, res;
+    const bool small = n < 32000 && m < 32000;
+    if (a.score_only) {
+      const int R = max(pen.x, max(pen.oe, pen.e)) + 1;
+      const int W = n + m + 3;
+      const long need = 16L * R + 3L * R * W * (small ? 2 : 4);
+      if (need > room) {
+        res = kFwdOverflow;
+      } else if (small) {
+        RingView<int16_t> v{reinterpret_cast<int32_t*>(wf), reinterpret_cast<int16_t*>(wf + 16L * R), R, W};
+        res = team_forward<WPP>(v, pw, tw, n, m, pen, a.s_cap, ts->flags, round, &s);
+      } else {
+        RingView<int32_t> v{reinterpret_cast<int32_t*>(wf), reinterpret_cast<int32_t*>(wf + 16L * R), R, W};
+        res = team_forward<WPP>(v, pw, tw, n, m, pen, a.s_cap, ts->flags, round, &s);
+      }
+      if (r == 0) {
+        if (res == kFwdOverflow) overflow_pair_to(a, pair, overflow_count);
+        else if (res == kFwdLimit) write_result(a, pair, 1, -1, 0, 0);
+        else write_result(a, pair, 0, s * a.g, 0, 0);
+      }
+    } else {
+      const long cap = room & ~15L;
+      if (small) {
+        ArenaViewT<int16_t> v{reinterpret_cast<int32_t*>(wf), reinterpret_cast<int16_t*>(wf + cap), cap};
+        res = team_forward<WPP>(v, pw, tw, n, m, pen, a.s_cap, ts->flags, round, &s);
+        if (r == 0) finish_cigar(a, v, pair, n, m, pen, res, s, overflow_count);
+      } else {
+        ArenaViewT<int32_t> v{reinterpret_cast<int32_t*>(wf), reinterpret_cast<int32_t*>(wf + cap), cap};
+        res = team_forward<WPP>(v, pw, tw, n, m, pen, a.s_cap, ts->flags, round, &s);
+        if (r == 0) finish_cigar(a, v, pair, n, m, pen, res, s, overflow_count);
+      }
+    }
+    T::sync();
+  }
+}
+
+}  // namespace wfa

@@ -11,6 +11,7 @@
 //   validate/scan/compact/pack  bookkeeping around them
 #include <climits>
 
+#include "arena_path.cuh"
 #include "launch.h"
 #include "short_path.cuh"
 #include "wfa_device.cuh"
@@ -28,79 +29,14 @@ __global__ void __launch_bounds__(kShortBlock) short_kernel(const AlignArgs a) {
   short_body<G, LMAX, CELLS, SCAP, Off>(a, smem, &s_last);
 }
 
-// ---------------------------------------------------------- general kernel
+// ----------------------------------------------------------- arena kernels
 
-constexpr int kGeneralBlock = 128;
-
-__device__ __forceinline__ void overflow_pair(const AlignArgs& a, int64_t pair) {
-  const int idx = atomicAdd(&a.ctrl->overflow_count, 1);
-  a.overflow_list[idx] = (int32_t)pair;
-}
-
-__global__ void __launch_bounds__(kGeneralBlock) general_kernel(const AlignArgs a, int32_t* arena, long slot_ints,
-                                                                int nwarps) {
-  const int lane = threadIdx.x & 31;
-  const long wid = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (wid >= nwarps) return;  // the arena has exactly nwarps slots
-  int32_t* slot = arena + wid * slot_ints;
-  const ScaledPen pen{a.xs, a.oes, a.es};
-  const unsigned full = 0xffffffffu;
-  const volatile int32_t* count = &a.ctrl->defer_count;
-  for (;;) {
-    int idx = 0;
-    if (lane == 0) idx = atomicAdd(&a.ctrl->general_next, 1);
-    idx = __shfl_sync(full, idx, 0);
-    if (idx >= *count) break;
-    const int64_t pair = a.defer_list[idx];
-    const int n = a.plen[pair], m = a.tlen[pair];
-    const long nwp = (n + 31) / 32 + 1, nwt = (m + 31) / 32 + 1;
-    const long seq_ints = 2 * (nwp + nwt);
-    if (seq_ints + 64 > slot_ints) {
-      if (lane == 0) overflow_pair(a, pair);
-      __syncwarp();
-      continue;
-    }
-    uint64_t* pw = reinterpret_cast<uint64_t*>(slot);
-    uint64_t* tw = pw + nwp;
-    const bool okp = pack_seq<32>(a.pat + a.poff[pair], n, pw, lane, full);
-    const bool okt = pack_seq<32>(a.txt + a.toff[pair], m, tw, lane, full);
-    __syncwarp();
-    if (!(okp && okt)) {
-      if (lane == 0) write_result(a, pair, 2, -1, 0, 0);
-      __syncwarp();
-      continue;
-    }
-    ArenaView view{slot + seq_ints, slot + slot_ints, slot_ints - seq_ints};
-    int s = 0;
-    const int r = wfa_forward<32>(view, pw, tw, n, m, pen, a.s_cap, lane, full, &s);
-    if (lane == 0) {
-      if (r == kFwdOverflow) {
-        overflow_pair(a, pair);
-      } else if (r == kFwdLimit) {
-        write_result(a, pair, 1, -1, 0, 0);
-      } else if (a.score_only) {
-        write_result(a, pair, 0, s * a.g, 0, 0);
-      } else {
-        long bound = runs_bound_scaled(s, pen.x, pen.oe);
-        if (bound > (long)n + m + 1) bound = (long)n + m + 1;
-        const unsigned long long pos = atomicAdd(&a.ctrl->pool_top, (unsigned long long)bound);
-        if ((long long)(pos + bound) > a.pool_cap) {
-          atomicExch(&a.ctrl->pool_short, 1);
-          overflow_pair(a, pair);
-        } else {
-          const int64_t src = a.pool_base + (int64_t)pos;
-          const int nr = wfa_backtrace(view, n, m, pen, s, a.runs + src, (int)bound);
-          if (nr < 0) {
-            atomicExch(&a.ctrl->internal_error, 1);
-            write_result(a, pair, 0, s * a.g, 0, src);
-          } else {
-            write_result(a, pair, 0, s * a.g, nr, src);
-          }
-        }
-      }
-    }
-    __syncwarp();
-  }
+template <int WPP>
+__global__ void __launch_bounds__(WPP == 1 ? 128 : 32 * WPP)
+    arena_kernel(const AlignArgs a, const int32_t* list, const int32_t* count, int32_t* next, int32_t* overflow_count,
+                 unsigned char* arena, long slot_bytes, int nteams, int seq_words) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  arena_body<WPP>(a, list, count, next, overflow_count, arena, slot_bytes, nteams, seq_words, smem);
 }
 
 // ----------------------------------------------------------------- helpers
@@ -223,14 +159,15 @@ __global__ void __launch_bounds__(kScanBlock) scan_apply(const int32_t* in, int6
 // ---------------------------------------------------------------- compact
 
 __global__ void compact_kernel(int64_t n, const int32_t* nruns, const int64_t* run_src, const uint32_t* runs,
-                               const int64_t* off, uint32_t* out, int64_t cap) {
+                               const uint32_t* pool, const int64_t* off, uint32_t* out, int64_t cap) {
   if (off[n] > cap) return;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const int c = nruns[i];
     if (c <= 0) continue;
     const int64_t o = off[i], src = run_src[i];
-    for (int j = 0; j < c; ++j) out[o + j] = runs[src + c - 1 - j];
+    const uint32_t* r = src >= 0 ? runs + src : pool + (-src - 1);
+    for (int j = 0; j < c; ++j) out[o + j] = r[c - 1 - j];
   }
 }
 
@@ -318,7 +255,10 @@ cudaError_t short_plan(int device, ShortPlan* plan) {
   if ((e = plan_one<4, 255, 208, 31, int16_t>(device, &plan->v[i++], "g4_l255_c208_i16"))) return e;
   if ((e = plan_one<1, 127, 40, 15, int8_t>(device, &plan->v[i++], "g1_l127_c40_i8"))) return e;
   plan->count = i;
-  return cudaSuccess;
+  // the one-CTA arena kernel keeps two sequences of up to 32,768 bases in
+  // shared memory
+  const size_t arena_smem = sizeof(TeamShm) + 2 * (size_t)(32768 / 32 + 2) * sizeof(uint64_t);
+  return cudaFuncSetAttribute(arena_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)arena_smem);
 }
 
 cudaError_t launch_short(const AlignArgs& a, const ShortVariant& v, cudaStream_t st) {
@@ -331,10 +271,24 @@ cudaError_t launch_short(const AlignArgs& a, const ShortVariant& v, cudaStream_t
   return cudaLaunchKernel(v.kernel, dim3(grid), dim3(v.block), args, v.smem, st);
 }
 
-cudaError_t launch_general(const AlignArgs& a, int32_t* arena, long slot_ints, int nwarps, cudaStream_t st) {
-  const int wpb = kGeneralBlock / 32;
-  const int grid = (nwarps + wpb - 1) / wpb;
-  general_kernel<<<grid, kGeneralBlock, 0, st>>>(a, arena, slot_ints, nwarps);
+cudaError_t launch_arena(bool long_team, const AlignArgs& a, const int32_t* list, const int32_t* count,
+                         int32_t* next, int32_t* overflow_count, unsigned char* arena, long slot_bytes, int nteams,
+                         cudaStream_t st) {
+  if (nteams < 1) return cudaSuccess;
+  if (!long_team) {
+    // four one-warp teams per block; sequences of medium pairs in shared memory
+    const int seq_words = kMediumMaxLen / 32 + 2;
+    const size_t smem = 4 * (sizeof(TeamShm) + 2 * (size_t)seq_words * sizeof(uint64_t));
+    const int grid = (nteams + 3) / 4;
+    arena_kernel<1><<<grid, 128, smem, st>>>(a, list, count, next, overflow_count, arena, slot_bytes, nteams,
+                                            seq_words);
+  } else {
+    // one CTA per team; sequences up to 32,768 bases in shared memory
+    const int seq_words = 32768 / 32 + 2;
+    const size_t smem = sizeof(TeamShm) + 2 * (size_t)seq_words * sizeof(uint64_t);
+    arena_kernel<8><<<nteams, 256, smem, st>>>(a, list, count, next, overflow_count, arena, slot_bytes, nteams,
+                                              seq_words);
+  }
   return cudaGetLastError();
 }
 
@@ -357,9 +311,9 @@ cudaError_t launch_scan(const int32_t* in, int64_t n, int kind, int64_t* out, in
 }
 
 cudaError_t launch_compact(int64_t n, const int32_t* nruns, const int64_t* run_src, const uint32_t* runs,
-                           const int64_t* off, uint32_t* out, int64_t cap, cudaStream_t st) {
+                           const uint32_t* pool, const int64_t* off, uint32_t* out, int64_t cap, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  compact_kernel<<<aux_grid(n, current_device()), kAuxBlock, 0, st>>>(n, nruns, run_src, runs, off, out, cap);
+  compact_kernel<<<aux_grid(n, current_device()), kAuxBlock, 0, st>>>(n, nruns, run_src, runs, pool, off, out, cap);
   return cudaGetLastError();
 }
 

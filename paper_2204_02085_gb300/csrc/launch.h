@@ -13,9 +13,13 @@ namespace wfa {
 struct Ctrl {
   int32_t bad_input;        // a length or offset out of range
   int32_t internal_error;   // stored wavefronts inconsistent in a backtrace
-  int32_t defer_count;      // pairs handed to the arena kernel
-  int32_t general_next;     // work-queue head of the arena kernel
-  int32_t overflow_count;   // pairs the arena kernel could not fit
+  int32_t defer_count;      // pairs handed to the one-warp arena kernel
+  int32_t defer_long_count; // pairs handed to the one-CTA arena kernel
+  int32_t next_medium;      // work-queue heads of the arena kernels
+  int32_t next_long;
+  int32_t retry_count;      // pairs of the current retry list
+  int32_t next_retry;
+  int32_t overflow_count;   // pairs an arena kernel could not fit
   int32_t pool_short;       // the CIGAR pool ran out
   unsigned long long pool_top;  // words used in the CIGAR pool
   long long pat_extent;     // max(offset + length) over patterns
@@ -39,14 +43,20 @@ struct AlignArgs {
   int32_t* score;
   int8_t* status;
   int32_t* nruns;
-  int64_t* run_src;   // index of a pair's runs (last run first) in `runs`
-  uint32_t* runs;     // [n * kSlot] per-pair slots, then the pool
-  int64_t pool_base;  // index of the pool in `runs`
+  int64_t* run_src;   // where a pair's runs (last run first) are: >= 0 an
+                      // index into `runs`, < 0 the index -src-1 into `pool`
+  uint32_t* runs;     // [n * kSlot] per-pair slots of the short kernel
+  uint32_t* pool;     // runs of arena-kernel pairs, reserved by atomics
   int64_t pool_cap;   // words in the pool
-  int32_t* defer_list;     // [n]
-  int32_t* overflow_list;  // [n]
+  int32_t* defer_list;       // [n] pairs for the one-warp arena kernel
+  int32_t* defer_long_list;  // [n] pairs for the one-CTA arena kernel
+  int32_t* overflow_list;    // [n]
   Ctrl* ctrl;
 };
+
+// longest sequence handled by a one-warp arena team; longer pairs go to a
+// one-CTA team
+constexpr int kMediumMaxLen = 2048;
 
 constexpr int kSlot = 16;  // CIGAR runs a short-kernel pair may keep
 
@@ -68,9 +78,13 @@ struct ShortPlan {
 cudaError_t short_plan(int device, ShortPlan* plan);
 cudaError_t launch_short(const AlignArgs& a, const ShortVariant& v, cudaStream_t st);
 
-// Arena kernel for pairs deferred by the short kernel: one warp per pair,
-// `nwarps` warps, each with slot_ints int32 of scratch.
-cudaError_t launch_general(const AlignArgs& a, int32_t* arena, long slot_ints, int nwarps, cudaStream_t st);
+// Arena kernels for pairs deferred by the short kernel: pairs list[0 ..
+// *count), taken through the work-queue head *next; `nteams` teams (one
+// warp each when long_team is false, one CTA of 8 warps otherwise), each
+// with slot_bytes of the arena; pairs that do not fit go to a.overflow_list.
+cudaError_t launch_arena(bool long_team, const AlignArgs& a, const int32_t* list, const int32_t* count,
+                         int32_t* next, int32_t* overflow_count, unsigned char* arena, long slot_bytes, int nteams,
+                         cudaStream_t st);
 
 // Validate lengths / offsets, record max(offset + length) extents.
 cudaError_t launch_validate(int64_t n, const int64_t* poff, const int32_t* plen, const int64_t* toff,
@@ -82,10 +96,10 @@ cudaError_t launch_validate(int64_t n, const int64_t* poff, const int32_t* plen,
 int64_t scan_tmp_elems(int64_t n);
 cudaError_t launch_scan(const int32_t* in, int64_t n, int kind, int64_t* out, int64_t* tmp, cudaStream_t st);
 
-// CIGAR compaction: pair i's runs (stored last first at runs[run_src[i]])
-// to out[off[i] .. off[i+1]) in order; writes nothing if off[n] > cap.
+// CIGAR compaction: pair i's runs (stored last first, see run_src) to
+// out[off[i] .. off[i+1]) in order; writes nothing if off[n] > cap.
 cudaError_t launch_compact(int64_t n, const int32_t* nruns, const int64_t* run_src, const uint32_t* runs,
-                           const int64_t* off, uint32_t* out, int64_t cap, cudaStream_t st);
+                           const uint32_t* pool, const int64_t* off, uint32_t* out, int64_t cap, cudaStream_t st);
 
 // Standalone packer: sequence i -> words[woff[i] ..], invalid[i].
 cudaError_t launch_pack(int64_t n, const char* seqs, const int64_t* off, const int32_t* len, const int64_t* woff,

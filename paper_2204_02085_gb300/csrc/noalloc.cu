@@ -139,9 +139,11 @@ extern "C" int wfa_gpu_align_short_noalloc(void* stream, int64_t n, const char* 
   a.nruns = reinterpret_cast<int32_t*>(base + kOffNruns);
   a.run_src = reinterpret_cast<int64_t*>(base + kOffRunSrc);
   a.runs = reinterpret_cast<uint32_t*>(base + kOffRuns);
-  a.pool_base = 0;
+  a.pool = nullptr;
   a.pool_cap = 0;
+  // deferred pairs of either kind land in the one list; any makes the call fail
   a.defer_list = reinterpret_cast<int32_t*>(base + kOffDefer);
+  a.defer_long_list = a.defer_list;
   a.overflow_list = nullptr;
   a.ctrl = ctrl;
   if (wfa::launch_short(a, ds->plan.v[kVariant], st) != cudaSuccess) return WFA_GPU_ECUDA;
@@ -152,10 +154,11 @@ extern "C" int wfa_gpu_align_short_noalloc(void* stream, int64_t n, const char* 
       cudaStreamSynchronize(st) != cudaSuccess)
     return WFA_GPU_ECUDA;
   if (h.internal_error) return WFA_GPU_ECUDA;
-  if (h.defer_count > 0) return WFA_GPU_ENOMEM;  // a pair outgrew the short kernel's store
+  if (h.defer_count > 0 || h.defer_long_count > 0) return WFA_GPU_ENOMEM;  // a pair outgrew the short kernel
   if (total > cap) return WFA_GPU_ECIGAR_CAPACITY;
   if (total > 0) {
-    if (wfa::launch_compact(n, a.nruns, a.run_src, a.runs, out_cigar_offsets, out_cigars, cap, st) != cudaSuccess ||
+    if (wfa::launch_compact(n, a.nruns, a.run_src, a.runs, nullptr, out_cigar_offsets, out_cigars, cap, st) !=
+            cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       return WFA_GPU_ECUDA;
   }

@@ -10,9 +10,16 @@ namespace wfa {
 
 constexpr int kShortBlock = 128;
 
+// Hand a pair to the arena kernels: pairs with a sequence longer than
+// kMediumMaxLen to the one-CTA kernel, the rest to the one-warp kernel.
 __device__ __forceinline__ void defer_pair(const AlignArgs& a, int64_t pair) {
-  const int idx = atomicAdd(&a.ctrl->defer_count, 1);
-  a.defer_list[idx] = (int32_t)pair;
+  if (max(a.plen[pair], a.tlen[pair]) > kMediumMaxLen) {
+    const int idx = atomicAdd(&a.ctrl->defer_long_count, 1);
+    a.defer_long_list[idx] = (int32_t)pair;
+  } else {
+    const int idx = atomicAdd(&a.ctrl->defer_count, 1);
+    a.defer_list[idx] = (int32_t)pair;
+  }
 }
 
 __device__ __forceinline__ void write_result(const AlignArgs& a, int64_t pair, int status, int score, int nr,

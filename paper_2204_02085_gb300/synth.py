@@ -174,6 +174,84 @@ def random_pairs(n_pairs: int, min_len: int, max_len: int, seed: int,
     return from_pairs(pairs)
 
 
+def _edit_one_pass(rng: np.random.Generator, text: np.ndarray, k: int) -> np.ndarray:
+    """Pattern from text (codes 0..3) with k edit events in one left-to-right
+    pass: k positions drawn uniformly over the text (with replacement); each
+    event is a substitution (one of the three other bases), a deletion of the
+    base there, or an insertion of a uniform base before it, 1/3 each.
+    Draw order: positions, kinds, substitution offsets, inserted bases."""
+    L = len(text)
+    if k == 0 or L == 0:
+        return text.copy()
+    pos = np.sort(rng.integers(0, L, size=k))
+    kind = rng.integers(0, 3, size=k)
+    delta = rng.integers(1, 4, size=k).astype(np.uint8)
+    ins = rng.integers(0, 4, size=k).astype(np.uint8)
+    pat = text.copy()
+    sub = kind == 0
+    np.add.at(pat, pos[sub], delta[sub])
+    pat %= 4
+    keep = np.ones(L, dtype=bool)
+    keep[pos[kind == 2]] = False
+    ip = pos[kind == 1]
+    out = np.insert(pat, ip, ins[kind == 1])
+    return out[np.insert(keep, ip, True)]
+
+
+def _pairs_from_codes(texts, pats) -> Batch:
+    tl = np.array([len(t) for t in texts], dtype=np.int32)
+    pl = np.array([len(p) for p in pats], dtype=np.int32)
+    txt = ALPHABET[np.concatenate(texts)] if texts else np.zeros(0, np.uint8)
+    pat = ALPHABET[np.concatenate(pats)] if pats else np.zeros(0, np.uint8)
+    poff = np.zeros(len(pl), dtype=np.int64)
+    toff = np.zeros(len(tl), dtype=np.int64)
+    if len(pl) > 1:
+        np.cumsum(pl[:-1], out=poff[1:])
+        np.cumsum(tl[:-1], out=toff[1:])
+    return Batch(np.ascontiguousarray(pat), poff, pl, np.ascontiguousarray(txt), toff, tl)
+
+
+def long_reads(n_pairs: int, length: int = 10_000, rate_lo: float = 0.01, rate_hi: float = 0.05,
+               seed: int = 4) -> Batch:
+    """Long-read pairs: text = `length` uniform bases; pattern = text after
+    round(r * length) one-pass edit events, r ~ U[rate_lo, rate_hi] per pair
+    (see _edit_one_pass).  Per pair the draws are: text, r, then the edits."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    texts, pats = [], []
+    for _ in range(n_pairs):
+        t = rng.integers(0, 4, size=length).astype(np.uint8)
+        k = int(round(rng.uniform(rate_lo, rate_hi) * length))
+        texts.append(t)
+        pats.append(_edit_one_pass(rng, t, k))
+    return _pairs_from_codes(texts, pats)
+
+
+def mixed_reads(n_pairs: int, len_lo: int = 100, len_hi: int = 2000, rate_hi: float = 0.10,
+                repeat_frac: float = 0.05, seed: int = 3) -> Batch:
+    """Pairs of uneven length and divergence: text length log-uniform in
+    [len_lo, len_hi], edit rate r ~ U[0, rate_hi]; a fraction repeat_frac of
+    the texts carry a tandem repeat (a uniform 50-mer repeated u ~ U{2..6}
+    times, written over a uniform window of the text, clipped at its end)
+    before the one-pass edits.  Per pair the draws are: length, text, the
+    repeat coin (and repeat unit, count, start), r, then the edits."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    texts, pats = [], []
+    lo, hi = np.log(len_lo), np.log(len_hi)
+    for _ in range(n_pairs):
+        L = int(round(np.exp(rng.uniform(lo, hi))))
+        t = rng.integers(0, 4, size=L).astype(np.uint8)
+        if rng.random() < repeat_frac:
+            unit = rng.integers(0, 4, size=50).astype(np.uint8)
+            rep = np.tile(unit, int(rng.integers(2, 7)))
+            start = int(rng.integers(0, L))
+            span = min(len(rep), L - start)
+            t[start:start + span] = rep[:span]
+        k = int(round(rng.uniform(0.0, rate_hi) * L))
+        texts.append(t)
+        pats.append(_edit_one_pass(rng, t, k))
+    return _pairs_from_codes(texts, pats)
+
+
 def from_pairs(pairs) -> Batch:
     """Back-to-back batch from a list of (pattern bytes, text bytes)."""
     pl = np.array([len(p) for p, _ in pairs], dtype=np.int32)
