@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--short-variant", type=int, default=None,
                     help="force one short-read kernel variant (tuning; default: the library's autotuner)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-pointer (end-to-end) measurement")
+    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4],
+                    help="2: the paper's 5M x 100 bp workload (default); 3: 1M mixed-length pairs (100-2,000 bp, "
+                         "0-10%% edits, tandem repeats); 4: 20k long-read pairs (10 kbp, 1-5%% edits)")
     args = ap.parse_args()
     args.edits = tuple(int(e) for e in args.edits.split(","))
     return args
@@ -204,10 +207,84 @@ def run_reference(args):
     return 0
 
 
+def run_config(args):
+    """Configurations beside the headline one (rank 0 only): mixed-length
+    pairs (3) and long reads (4), timed like the headline workload with
+    device-resident inputs; long reads both score-only and score + CIGAR."""
+    import torch
+
+    import paper_2204_02085_gb300 as pkg
+    from paper_2204_02085_gb300 import build as gpu_build
+    from paper_2204_02085_gb300 import synth
+
+    gpu_build.build()
+    dev = torch.device("cuda:0")
+    if args.config == 3:
+        n = args.pairs if args.pairs != N_PAIRS else 1_000_000
+        b = synth.mixed_reads(n, 100, 2000, 0.10, 0.05, seed=3)
+        scratch, modes = 16 << 30, (False,)
+        workload = "%d pairs, text length log-uniform 100-2,000 bp, edit rate U[0,10%%], 5%% tandem repeats" % n
+    else:
+        n = args.pairs if args.pairs != N_PAIRS else 20_000
+        b = synth.long_reads(n, 10_000, 0.01, 0.05, seed=4)
+        scratch, modes = 64 << 30, (True, False)
+        workload = "%d pairs x 10 kbp, edit rate U[1%%,5%%]" % n
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    d = dict(pat=t(b.patterns), plen=t(b.pattern_lengths), txt=t(b.texts), tlen=t(b.text_lengths),
+             s=torch.empty(n, dtype=torch.int32, device=dev), st=torch.empty(n, dtype=torch.int8, device=dev),
+             off=torch.empty(n + 1, dtype=torch.int64, device=dev))
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    with pkg.Aligner(0, scratch_bytes=scratch) as al:
+        al.set_stream(stream)
+        for score_only in modes:
+            w = torch.empty(1, dtype=torch.int32, device=dev)
+            if not score_only:  # size the CIGAR output from a first call
+                al.align_device(d["pat"], None, d["plen"], d["txt"], None, d["tlen"], d["s"], d["st"], w, d["off"],
+                                pen=PEN)
+                w = torch.empty(int(d["off"][-1]) + 1, dtype=torch.int32, device=dev)
+
+            def call():
+                rc = al.align_device(d["pat"], None, d["plen"], d["txt"], None, d["tlen"], d["s"], d["st"],
+                                     None if score_only else w, d["off"], pen=PEN, score_only=score_only,
+                                     timing=True)
+                assert rc == pkg.WFA_GPU_OK
+                return al.timing()
+
+            for _ in range(args.warmup):
+                call()
+            torch.cuda.synchronize(dev)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ts = []
+            ev0.record(stream)
+            for _ in range(args.steps):
+                ts.append(call())
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = ev0.elapsed_time(ev1) / args.steps
+            st = d["st"].cpu().numpy()
+            res["score_only" if score_only else "score_cigar"] = {
+                "pairs_per_s": n / (ms / 1000.0), "ms_per_call": ms,
+                "phase_ms": {k: round(float(np.mean([x[k] for x in ts])), 3)
+                             for k in ("align_ms", "general_ms", "cigar_ms", "total_ms")},
+                "deferred_pairs": int(ts[-1]["deferred_pairs"]), "short_variant": int(ts[-1]["short_variant"]),
+                "status_ok": int((st == 0).sum()), "mean_score": float(d["s"].float().mean().item())}
+    main_mode = res.get("score_cigar")
+    line = {"metric": "pairs/s (config %d)" % args.config, "value": main_mode["pairs_per_s"], "unit": "pairs/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": main_mode["ms_per_call"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": workload, "penalties": "4/6/2",
+                                            "arena_bytes": scratch}, "modes": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config != 2:
+        return run_config(args)
 
     import torch
     import torch.distributed as dist

@@ -78,7 +78,16 @@ enum {
   WFA_GPU_SCORE_ONLY = 1u,  /* compute scores only; out_cigars may be NULL */
   WFA_GPU_DEVICE_PTRS = 2u, /* every input and output pointer is device memory on the
                                context's device (default: host memory) */
-  WFA_GPU_TIMING = 4u       /* record per-phase device times for wfa_gpu_last_timing */
+  WFA_GPU_TIMING = 4u,      /* record per-phase device times for wfa_gpu_last_timing */
+  WFA_GPU_PLAIN = 8u,       /* the plain path, kept as a baseline for comparisons: every
+                               pair on one-warp (or, above 2,048 bases, one-CTA) arena
+                               teams from a work queue, without the short-read kernel,
+                               its variants or the autotuner; same results */
+  WFA_GPU_GRAPH = 16u       /* with WFA_GPU_DEVICE_PTRS: for batches repeated with the same
+                               arguments (same sizes and buffers, new contents), the first
+                               call runs as usual and records the device work into a CUDA
+                               graph; identical later calls replay it with a single host
+                               synchronisation (one graph per context) */
 };
 
 /* Device-side times of the last wfa_gpu_align_batch call on a context,
@@ -124,7 +133,8 @@ int wfa_gpu_set_stream(wfa_gpu_ctx *ctx, void *stream);
  * max_score: if > 0, pairs whose optimal score exceeds it get status
  *   WFA_PAIR_SCORE_LIMIT (a score equal to max_score is reported); <= 0 means
  *   no bound.
- * flags: WFA_GPU_SCORE_ONLY | WFA_GPU_DEVICE_PTRS | WFA_GPU_TIMING.
+ * flags: WFA_GPU_SCORE_ONLY | WFA_GPU_DEVICE_PTRS | WFA_GPU_TIMING |
+ *   WFA_GPU_PLAIN | WFA_GPU_GRAPH.
  *
  * Outputs (caller-owned):
  *   out_scores[n]   int32 optimal score, -1 if status != OK

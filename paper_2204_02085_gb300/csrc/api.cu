@@ -5,6 +5,7 @@
 // independently, results gathered back).
 #include <algorithm>
 #include <climits>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -102,6 +103,10 @@ struct wfa_gpu_ctx {
   DevBuf<int8_t> tune_status;
   DevBuf<int64_t> tune_src;
   int32_t* h_tune = nullptr;  // pinned [kTuneSample]
+  // captured device work of a repeated WFA_GPU_GRAPH call
+  cudaGraphExec_t graph_exec = nullptr;
+  uint64_t graph_key[40] = {};
+  int graph_key_len = 0;
 };
 
 namespace {
@@ -260,6 +265,8 @@ int stage_inputs(wfa_gpu_ctx* c, Call& k, int64_t n, bool dev, const char* pat, 
   return 0;
 }
 
+int run_retries(wfa_gpu_ctx* c, Call& k, wfa::AlignArgs& a);
+
 // The arena kernels over the pairs the short kernel deferred (medium pairs
 // on one-warp teams, long ones on one-CTA teams), then retries of the pairs
 // that did not fit: fewer, larger arena slices on one-CTA teams, or a larger
@@ -279,6 +286,16 @@ int run_arena(wfa_gpu_ctx* c, Call& k, wfa::AlignArgs& a) {
                                     st)))
     return WFA_GPU_ECUDA;
   if (!k.ok(d2h(hc, dc, sizeof(wfa::Ctrl), st)) || !k.ok(cudaStreamSynchronize(st))) return WFA_GPU_ECUDA;
+  return run_retries(c, k, a);
+}
+
+// Retries of the pairs on the overflow list (h_ctrl mirrors the device
+// control block on entry).
+int run_retries(wfa_gpu_ctx* c, Call& k, wfa::AlignArgs& a) {
+  cudaStream_t st = c->stream;
+  wfa::Ctrl* hc = c->h_ctrl;
+  wfa::Ctrl* dc = c->ctrl;
+  const long arena = (long)c->arena_bytes;
   int teams = c->teams_long;
   int32_t* in = a.overflow_list;  // the pairs to retry
   int32_t* out = a.defer_list;    // free again: receives the next overflow
@@ -411,8 +428,24 @@ int wfa_gpu_create(wfa_gpu_ctx** out, int device, size_t scratch_bytes) {
     }
     int nsm = 1;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
-    c->teams_medium = std::max(1, nsm * 16);
-    c->teams_long = std::max(1, nsm * 2);
+    // as many teams as fit on the GPU at once, each with an arena slice of
+    // at least 256 KiB (one-warp teams) or 4 MiB (one-CTA teams); pairs that
+    // outgrow their slice are retried with larger ones
+    int tm = 16, tl = 2;
+    if (wfa::arena_occupancy(false, &tm) != cudaSuccess || wfa::arena_occupancy(true, &tl) != cudaSuccess) {
+      rc = WFA_GPU_ECUDA;
+      break;
+    }
+    const long arena_b = (long)c->arena_bytes;
+    c->teams_medium = (int)std::max(1L, std::min((long)nsm * tm, arena_b / (256L << 10)));
+    c->teams_long = (int)std::max(1L, std::min((long)nsm * tl, arena_b / (4L << 20)));
+    if (const char* ev = std::getenv("WFA_GPU_TEAMS")) {  // tuning override: "<medium>,<long>"
+      int a = 0, b = 0;
+      if (std::sscanf(ev, "%d,%d", &a, &b) == 2 && a > 0 && b > 0) {
+        c->teams_medium = a;
+        c->teams_long = b;
+      }
+    }
   } while (0);
   if (rc) {
     wfa_gpu_destroy(c);
@@ -428,13 +461,19 @@ int wfa_gpu_set_stream(wfa_gpu_ctx* ctx, void* stream) {
   return WFA_GPU_OK;
 }
 
-int wfa_gpu_align_batch(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t* pattern_offsets,
-                        const int32_t* pattern_lengths, const char* texts, const int64_t* text_offsets,
-                        const int32_t* text_lengths, wfa_gpu_penalties pen, int32_t max_score, uint32_t flags,
-                        int32_t* out_scores, int8_t* out_status, uint32_t* out_cigars, int64_t cap,
-                        int64_t* out_cigar_offsets) {
+}  // extern "C"
+
+namespace {
+
+int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t* pattern_offsets,
+                const int32_t* pattern_lengths, const char* texts, const int64_t* text_offsets,
+                const int32_t* text_lengths, wfa_gpu_penalties pen, int32_t max_score, uint32_t flags,
+                int32_t* out_scores, int8_t* out_status, uint32_t* out_cigars, int64_t cap,
+                int64_t* out_cigar_offsets) {
   if (!ctx || n < 0 || n > INT32_MAX || cap < 0 || !pen_ok(pen)) return WFA_GPU_EINVAL;
-  if (flags & ~(uint32_t)(WFA_GPU_SCORE_ONLY | WFA_GPU_DEVICE_PTRS | WFA_GPU_TIMING)) return WFA_GPU_EINVAL;
+  if (flags & ~(uint32_t)(WFA_GPU_SCORE_ONLY | WFA_GPU_DEVICE_PTRS | WFA_GPU_TIMING | WFA_GPU_PLAIN))
+    return WFA_GPU_EINVAL;
+  const bool plain = flags & WFA_GPU_PLAIN;
   const bool dev = flags & WFA_GPU_DEVICE_PTRS;
   const bool score_only = flags & WFA_GPU_SCORE_ONLY;
   if (n > 0 && (!patterns || !pattern_lengths || !texts || !text_lengths || !out_scores || !out_status))
@@ -506,13 +545,17 @@ int wfa_gpu_align_batch(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const
   a.overflow_list = ctx->overflow.p;
   a.ctrl = ctx->ctrl;
 
-  int vi = ctx->variant_mid;
-  if (ctx->h_ctrl->max_len <= 127) {
-    vi = autotune_short(ctx, k, a, n);
-    if (vi < 0) return fail_cuda(k);
+  if (plain) {
+    if (!k.launched(wfa::launch_route_all(a, st))) return fail_cuda(k);
+  } else {
+    int vi = ctx->variant_mid;
+    if (ctx->h_ctrl->max_len <= 127) {
+      vi = autotune_short(ctx, k, a, n);
+      if (vi < 0) return fail_cuda(k);
+    }
+    ctx->last_variant = vi;
+    if (!k.launched(wfa::launch_short(a, ctx->plan.v[vi], st))) return fail_cuda(k);
   }
-  ctx->last_variant = vi;
-  if (!k.launched(wfa::launch_short(a, ctx->plan.v[vi], st))) return fail_cuda(k);
   k.rec(2);
   if (!k.ok(d2h(ctx->h_ctrl, ctx->ctrl, sizeof(wfa::Ctrl), st)) || !k.ok(cudaStreamSynchronize(st)))
     return fail_cuda(k);
@@ -541,7 +584,8 @@ int wfa_gpu_align_batch(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const
         d_cig = ctx->cig.p;
       }
       if (!k.launched(
-              wfa::launch_compact(n, ctx->nruns.p, ctx->run_src.p, ctx->runs.p, ctx->pool.p, d_off, d_cig, cap, st)))
+              wfa::launch_compact(n, ctx->nruns.p, ctx->run_src.p, ctx->runs.p, ctx->pool.p, d_off, d_cig, cap,
+                                  ctx->ctrl, st)))
         return fail_cuda(k);
     }
   }
@@ -568,6 +612,206 @@ int wfa_gpu_align_batch(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const
     ctx->last.total_ms = elapsed(ctx, 0, 5);
   }
   return total > cap ? WFA_GPU_ECIGAR_CAPACITY : WFA_GPU_OK;
+}
+
+// The arguments the device work of a call runs with (device-pointer calls;
+// the internal buffers must already be large enough).
+wfa::AlignArgs device_args(wfa_gpu_ctx* c, int64_t n, const char* pat, const int64_t* poff, const int32_t* plen,
+                           const char* txt, const int64_t* toff, const int32_t* tlen, wfa_gpu_penalties pen,
+                           int32_t max_score, bool score_only, int32_t* out_scores, int8_t* out_status) {
+  const int g = gcd(pen.x, gcd(pen.o, pen.e));
+  wfa::AlignArgs a{};
+  a.n = n;
+  a.pat = pat; a.poff = poff; a.plen = plen;
+  a.txt = txt; a.toff = toff; a.tlen = tlen;
+  a.g = g;
+  a.xs = pen.x / g;
+  a.es = pen.e / g;
+  a.oes = (pen.o + pen.e) / g;
+  a.s_cap = max_score > 0 ? max_score / g : INT_MAX;
+  a.score_only = score_only ? 1 : 0;
+  a.score = out_scores;
+  a.status = out_status;
+  a.nruns = c->nruns.p;
+  a.run_src = c->run_src.p;
+  a.runs = c->runs.p;
+  a.pool = c->pool.p;
+  a.pool_cap = score_only ? 0 : (int64_t)c->pool.cap;
+  a.defer_list = c->defer.p;
+  a.defer_long_list = c->defer_long.p;
+  a.overflow_list = c->overflow.p;
+  a.ctrl = c->ctrl;
+  return a;
+}
+
+// Everything the device does for a device-pointer call, without a host
+// synchronisation: what a CUDA graph captures.  The short-kernel variant is
+// the one the preceding eager call chose.
+int enqueue_device_work(wfa_gpu_ctx* c, Call& k, int64_t n, const char* pat, const int64_t* poff,
+                        const int32_t* plen, const char* txt, const int64_t* toff, const int32_t* tlen,
+                        wfa_gpu_penalties pen, int32_t max_score, uint32_t flags, int32_t* out_scores,
+                        int8_t* out_status, uint32_t* out_cigars, int64_t cap, int64_t* out_off) {
+  cudaStream_t st = c->stream;
+  const bool score_only = flags & WFA_GPU_SCORE_ONLY;
+  if (!k.ok(cudaMemsetAsync(c->ctrl, 0, sizeof(wfa::Ctrl), st))) return WFA_GPU_ECUDA;
+  const int64_t* d_poff = poff;
+  const int64_t* d_toff = toff;
+  if (!d_poff) {
+    if (!k.launched(wfa::launch_scan(plen, n, 0, c->poff.p, c->scan_tmp.p, st), 3)) return WFA_GPU_ECUDA;
+    d_poff = c->poff.p;
+  }
+  if (!d_toff) {
+    if (!k.launched(wfa::launch_scan(tlen, n, 0, c->toff.p, c->scan_tmp.p, st), 3)) return WFA_GPU_ECUDA;
+    d_toff = c->toff.p;
+  }
+  if (!k.launched(wfa::launch_validate(n, d_poff, plen, d_toff, tlen, c->ctrl, st))) return WFA_GPU_ECUDA;
+  wfa::AlignArgs a = device_args(c, n, pat, d_poff, plen, txt, d_toff, tlen, pen, max_score, score_only,
+                                 out_scores, out_status);
+  if (flags & WFA_GPU_PLAIN) {
+    if (!k.launched(wfa::launch_route_all(a, st))) return WFA_GPU_ECUDA;
+  } else {
+    if (c->last_variant < 0) return WFA_GPU_ECUDA;
+    if (!k.launched(wfa::launch_short(a, c->plan.v[c->last_variant], st))) return WFA_GPU_ECUDA;
+  }
+  const long arena = (long)c->arena_bytes;
+  unsigned char* ab = reinterpret_cast<unsigned char*>(c->arena);
+  wfa::Ctrl* dc = c->ctrl;
+  if (!k.launched(wfa::launch_arena(false, a, a.defer_list, &dc->defer_count, &dc->next_medium, &dc->overflow_count,
+                                    ab, (arena / c->teams_medium) & ~255L, c->teams_medium, st)) ||
+      !k.launched(wfa::launch_arena(true, a, a.defer_long_list, &dc->defer_long_count, &dc->next_long,
+                                    &dc->overflow_count, ab, (arena / c->teams_long) & ~255L, c->teams_long, st)))
+    return WFA_GPU_ECUDA;
+  if (!score_only) {
+    if (!k.launched(wfa::launch_scan(c->nruns.p, n, 0, out_off, c->scan_tmp.p, st), 3) ||
+        !k.launched(wfa::launch_compact(n, c->nruns.p, c->run_src.p, c->runs.p, c->pool.p, out_off, out_cigars, cap,
+                                        c->ctrl, st)))
+      return WFA_GPU_ECUDA;
+  }
+  return 0;
+}
+
+// Key of a graph: the call's arguments and every internal buffer the
+// captured work uses (a reallocation forces a new capture).
+int graph_key(wfa_gpu_ctx* c, uint64_t* key, int64_t n, const void* const* ptrs, int nptrs, wfa_gpu_penalties pen,
+              int32_t max_score, uint32_t flags, int64_t cap) {
+  int l = 0;
+  key[l++] = (uint64_t)n;
+  for (int i = 0; i < nptrs; ++i) key[l++] = (uint64_t)(uintptr_t)ptrs[i];
+  key[l++] = ((uint64_t)(uint32_t)pen.x << 32) | (uint32_t)pen.o;
+  key[l++] = ((uint64_t)(uint32_t)pen.e << 32) | (uint32_t)max_score;
+  key[l++] = flags & ~(uint32_t)WFA_GPU_TIMING;
+  key[l++] = (uint64_t)cap;
+  key[l++] = (uint64_t)(uintptr_t)c->stream;
+  const void* bufs[] = {c->ctrl, c->poff.p, c->toff.p, c->scan_tmp.p, c->nruns.p, c->run_src.p, c->runs.p,
+                        c->pool.p, c->defer.p, c->defer_long.p, c->overflow.p, c->arena};
+  for (const void* b : bufs) key[l++] = (uint64_t)(uintptr_t)b;
+  key[l++] = c->pool.cap;
+  key[l++] = ((uint64_t)(uint32_t)c->teams_medium << 32) | (uint32_t)c->teams_long;
+  return l;
+}
+
+// WFA_GPU_GRAPH: the first call of a kind runs eagerly and then captures
+// its device work; later identical calls replay the capture and check the
+// outcome once (retrying overflowed pairs eagerly if any).
+int align_graph(wfa_gpu_ctx* ctx, int64_t n, const char* pat, const int64_t* poff, const int32_t* plen,
+                const char* txt, const int64_t* toff, const int32_t* tlen, wfa_gpu_penalties pen, int32_t max_score,
+                uint32_t flags, int32_t* out_scores, int8_t* out_status, uint32_t* out_cigars, int64_t cap,
+                int64_t* out_off) {
+  const uint32_t base = flags & ~(uint32_t)WFA_GPU_GRAPH;
+  if (!ctx || !(flags & WFA_GPU_DEVICE_PTRS)) return WFA_GPU_EINVAL;
+  const bool score_only = flags & WFA_GPU_SCORE_ONLY;
+  const void* ptrs[] = {pat, poff, plen, txt, toff, tlen, out_scores, out_status, out_cigars, out_off};
+  uint64_t key[40];
+  int kl = graph_key(ctx, key, n, ptrs, 10, pen, max_score, flags, cap);
+  const bool hit = ctx->graph_exec && n > 0 && kl == ctx->graph_key_len &&
+                   std::memcmp(key, ctx->graph_key, kl * sizeof(uint64_t)) == 0;
+  if (!hit) {
+    const int rc = align_eager(ctx, n, pat, poff, plen, txt, toff, tlen, pen, max_score, base, out_scores,
+                               out_status, out_cigars, cap, out_off);
+    if ((rc != WFA_GPU_OK && rc != WFA_GPU_ECIGAR_CAPACITY) || n == 0) return rc;
+    if (ctx->graph_exec) {
+      cudaGraphExecDestroy(ctx->graph_exec);
+      ctx->graph_exec = nullptr;
+      ctx->graph_key_len = 0;
+    }
+    cudaStream_t st = ctx->stream;
+    Call k{ctx, false};
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return WFA_GPU_ECUDA;
+    const int erc = enqueue_device_work(ctx, k, n, pat, poff, plen, txt, toff, tlen, pen, max_score, base,
+                                        out_scores, out_status, out_cigars, cap, out_off);
+    const cudaError_t ee = cudaStreamEndCapture(st, &g);
+    if (erc || ee != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return WFA_GPU_ECUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return WFA_GPU_ECUDA;
+    ctx->graph_exec = exec;
+    kl = graph_key(ctx, key, n, ptrs, 10, pen, max_score, flags, cap);
+    std::memcpy(ctx->graph_key, key, kl * sizeof(uint64_t));
+    ctx->graph_key_len = kl;
+    return rc;
+  }
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return WFA_GPU_ECUDA;
+  const int variant = ctx->last_variant;
+  std::memset(&ctx->last, 0, sizeof ctx->last);
+  ctx->last_variant = variant;
+  cudaStream_t st = ctx->stream;
+  Call k{ctx, (flags & WFA_GPU_TIMING) != 0};
+  k.rec(0);
+  if (!k.ok(cudaGraphLaunch(ctx->graph_exec, st))) return WFA_GPU_ECUDA;
+  k.launches += 14;
+  int64_t total = 0;
+  if (!k.ok(d2h(ctx->h_ctrl, ctx->ctrl, sizeof(wfa::Ctrl), st))) return WFA_GPU_ECUDA;
+  if (!score_only && !k.ok(d2h(ctx->h_total, out_off + n, sizeof(int64_t), st))) return WFA_GPU_ECUDA;
+  if (!k.ok(cudaStreamSynchronize(st))) return WFA_GPU_ECUDA;
+  if (ctx->h_ctrl->bad_input) return WFA_GPU_EINVAL;
+  ctx->last.deferred_pairs = (int64_t)ctx->h_ctrl->defer_count + ctx->h_ctrl->defer_long_count;
+  if (ctx->h_ctrl->overflow_count > 0) {
+    // rare: pairs that outgrew their arena slice, retried outside the graph
+    const int64_t* d_poff = poff ? poff : ctx->poff.p;
+    const int64_t* d_toff = toff ? toff : ctx->toff.p;
+    wfa::AlignArgs a = device_args(ctx, n, pat, d_poff, plen, txt, d_toff, tlen, pen, max_score, score_only,
+                                   out_scores, out_status);
+    const int rc = run_retries(ctx, k, a);
+    if (rc) return rc;
+    if (!score_only) {
+      if (!k.launched(wfa::launch_scan(ctx->nruns.p, n, 0, out_off, ctx->scan_tmp.p, st), 3) ||
+          !k.launched(wfa::launch_compact(n, ctx->nruns.p, ctx->run_src.p, ctx->runs.p, ctx->pool.p, out_off,
+                                          out_cigars, cap, ctx->ctrl, st)) ||
+          !k.ok(d2h(ctx->h_total, out_off + n, sizeof(int64_t), st)))
+        return WFA_GPU_ECUDA;
+    }
+    if (!k.ok(cudaStreamSynchronize(st))) return WFA_GPU_ECUDA;
+  }
+  if (ctx->h_ctrl->internal_error) return WFA_GPU_ECUDA;
+  if (!score_only) total = *ctx->h_total;
+  k.rec(5);
+  if (!k.ok(cudaStreamSynchronize(st))) return WFA_GPU_ECUDA;
+  ctx->last.kernel_launches = k.launches;
+  ctx->last.short_variant = ctx->last_variant;
+  if (k.timing) ctx->last.total_ms = elapsed(ctx, 0, 5);
+  return total > cap ? WFA_GPU_ECIGAR_CAPACITY : WFA_GPU_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int wfa_gpu_align_batch(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t* pattern_offsets,
+                        const int32_t* pattern_lengths, const char* texts, const int64_t* text_offsets,
+                        const int32_t* text_lengths, wfa_gpu_penalties pen, int32_t max_score, uint32_t flags,
+                        int32_t* out_scores, int8_t* out_status, uint32_t* out_cigars, int64_t cap,
+                        int64_t* out_cigar_offsets) {
+  if (flags & WFA_GPU_GRAPH)
+    return align_graph(ctx, n, patterns, pattern_offsets, pattern_lengths, texts, text_offsets, text_lengths, pen,
+                       max_score, flags, out_scores, out_status, out_cigars, cap, out_cigar_offsets);
+  return align_eager(ctx, n, patterns, pattern_offsets, pattern_lengths, texts, text_offsets, text_lengths, pen,
+                     max_score, flags, out_scores, out_status, out_cigars, cap, out_cigar_offsets);
 }
 
 int wfa_gpu_pack2bit(wfa_gpu_ctx* ctx, int64_t n, const char* seqs, const int64_t* offsets, const int32_t* lengths,
@@ -694,6 +938,7 @@ void wfa_gpu_destroy(wfa_gpu_ctx* c) {
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
   if (c->h_total) cudaFreeHost(c->h_total);
   if (c->h_tune) cudaFreeHost(c->h_tune);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   c->tune_score.release(); c->tune_aux.release(); c->tune_status.release(); c->tune_src.release();
   for (int i = 0; i < kEvents; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);

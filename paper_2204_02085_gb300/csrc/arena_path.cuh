@@ -229,9 +229,13 @@ __device__ __forceinline__ bool team_pack(const char* __restrict__ seq, int len,
   return Team<WPP>::reduce_or(bad ? 1 : 0, flags, round) == 0;
 }
 
+// A pair that did not fit: onto the overflow list, with no CIGAR until a
+// retry aligns it (so that a compaction run before the retry reads nothing).
 __device__ __forceinline__ void overflow_pair_to(const AlignArgs& a, int64_t pair, int32_t* count) {
   const int idx = atomicAdd(count, 1);
   a.overflow_list[idx] = (int32_t)pair;
+  a.nruns[pair] = 0;
+  a.run_src[pair] = 0;
 }
 
 // After the forward pass of a pair (single thread): its outcome, and for a
@@ -279,6 +283,7 @@ __device__ void arena_body(const AlignArgs& a, const int32_t* list, const int32_
   using T = Team<WPP>;
   const int team = WPP == 1 ? (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) : (int)blockIdx.x;
   if (team >= nteams) return;  // whole team: uniform
+  if (*(volatile const int32_t*)&a.ctrl->bad_input) return;  // inputs rejected by the validation kernel
   const int team_in_block = WPP == 1 ? (int)(threadIdx.x >> 5) : 0;
   const size_t team_smem = sizeof(TeamShm) + 2 * (size_t)seq_words * sizeof(uint64_t);
   unsigned char* my = smem + team_in_block * team_smem;

@@ -39,6 +39,13 @@ __global__ void __launch_bounds__(WPP == 1 ? 128 : 32 * WPP)
   arena_body<WPP>(a, list, count, next, overflow_count, arena, slot_bytes, nteams, seq_words, smem);
 }
 
+// Every pair onto the arena work lists (the plain path), by length.
+__global__ void route_all_kernel(const AlignArgs a) {
+  if (*(volatile const int32_t*)&a.ctrl->bad_input) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) defer_pair(a, i);
+}
+
 // ----------------------------------------------------------------- helpers
 
 constexpr int kAuxBlock = 256;
@@ -159,8 +166,9 @@ __global__ void __launch_bounds__(kScanBlock) scan_apply(const int32_t* in, int6
 // ---------------------------------------------------------------- compact
 
 __global__ void compact_kernel(int64_t n, const int32_t* nruns, const int64_t* run_src, const uint32_t* runs,
-                               const uint32_t* pool, const int64_t* off, uint32_t* out, int64_t cap) {
-  if (off[n] > cap) return;
+                               const uint32_t* pool, const int64_t* off, uint32_t* out, int64_t cap,
+                               const Ctrl* ctrl) {
+  if (off[n] > cap || (ctrl && *(volatile const int32_t*)&ctrl->bad_input)) return;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const int c = nruns[i];
@@ -271,6 +279,29 @@ cudaError_t launch_short(const AlignArgs& a, const ShortVariant& v, cudaStream_t
   return cudaLaunchKernel(v.kernel, dim3(grid), dim3(v.block), args, v.smem, st);
 }
 
+cudaError_t launch_route_all(const AlignArgs& a, cudaStream_t st) {
+  if (a.n <= 0) return cudaSuccess;
+  route_all_kernel<<<aux_grid(a.n, current_device()), kAuxBlock, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t arena_occupancy(bool long_team, int* teams_per_sm) {
+  int per_sm = 0;
+  cudaError_t e;
+  if (!long_team) {
+    const int seq_words = kMediumMaxLen / 32 + 2;
+    const size_t smem = 4 * (sizeof(TeamShm) + 2 * (size_t)seq_words * sizeof(uint64_t));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, arena_kernel<1>, 128, smem);
+    *teams_per_sm = 4 * per_sm;
+  } else {
+    const size_t smem = sizeof(TeamShm) + 2 * (size_t)(32768 / 32 + 2) * sizeof(uint64_t);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, arena_kernel<8>, 256, smem);
+    *teams_per_sm = per_sm;
+  }
+  if (*teams_per_sm < 1) *teams_per_sm = 1;
+  return e;
+}
+
 cudaError_t launch_arena(bool long_team, const AlignArgs& a, const int32_t* list, const int32_t* count,
                          int32_t* next, int32_t* overflow_count, unsigned char* arena, long slot_bytes, int nteams,
                          cudaStream_t st) {
@@ -311,9 +342,11 @@ cudaError_t launch_scan(const int32_t* in, int64_t n, int kind, int64_t* out, in
 }
 
 cudaError_t launch_compact(int64_t n, const int32_t* nruns, const int64_t* run_src, const uint32_t* runs,
-                           const uint32_t* pool, const int64_t* off, uint32_t* out, int64_t cap, cudaStream_t st) {
+                           const uint32_t* pool, const int64_t* off, uint32_t* out, int64_t cap, const Ctrl* ctrl,
+                           cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  compact_kernel<<<aux_grid(n, current_device()), kAuxBlock, 0, st>>>(n, nruns, run_src, runs, pool, off, out, cap);
+  compact_kernel<<<aux_grid(n, current_device()), kAuxBlock, 0, st>>>(n, nruns, run_src, runs, pool, off, out, cap,
+                                                                       ctrl);
   return cudaGetLastError();
 }
 

@@ -82,6 +82,11 @@ cudaError_t launch_short(const AlignArgs& a, const ShortVariant& v, cudaStream_t
 // *count), taken through the work-queue head *next; `nteams` teams (one
 // warp each when long_team is false, one CTA of 8 warps otherwise), each
 // with slot_bytes of the arena; pairs that do not fit go to a.overflow_list.
+// The plain path: every pair onto the arena work lists.
+cudaError_t launch_route_all(const AlignArgs& a, cudaStream_t st);
+
+// Resident teams per SM of an arena kernel (occupancy calculator).
+cudaError_t arena_occupancy(bool long_team, int* teams_per_sm);
 cudaError_t launch_arena(bool long_team, const AlignArgs& a, const int32_t* list, const int32_t* count,
                          int32_t* next, int32_t* overflow_count, unsigned char* arena, long slot_bytes, int nteams,
                          cudaStream_t st);
@@ -97,9 +102,11 @@ int64_t scan_tmp_elems(int64_t n);
 cudaError_t launch_scan(const int32_t* in, int64_t n, int kind, int64_t* out, int64_t* tmp, cudaStream_t st);
 
 // CIGAR compaction: pair i's runs (stored last first, see run_src) to
-// out[off[i] .. off[i+1]) in order; writes nothing if off[n] > cap.
+// out[off[i] .. off[i+1]) in order; writes nothing if off[n] > cap or the
+// inputs were rejected (ctrl may be NULL).
 cudaError_t launch_compact(int64_t n, const int32_t* nruns, const int64_t* run_src, const uint32_t* runs,
-                           const uint32_t* pool, const int64_t* off, uint32_t* out, int64_t cap, cudaStream_t st);
+                           const uint32_t* pool, const int64_t* off, uint32_t* out, int64_t cap, const Ctrl* ctrl,
+                           cudaStream_t st);
 
 // Standalone packer: sequence i -> words[woff[i] ..], invalid[i].
 cudaError_t launch_pack(int64_t n, const char* seqs, const int64_t* off, const int32_t* len, const int64_t* woff,

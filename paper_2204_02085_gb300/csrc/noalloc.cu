@@ -157,7 +157,7 @@ extern "C" int wfa_gpu_align_short_noalloc(void* stream, int64_t n, const char* 
   if (h.defer_count > 0 || h.defer_long_count > 0) return WFA_GPU_ENOMEM;  // a pair outgrew the short kernel
   if (total > cap) return WFA_GPU_ECIGAR_CAPACITY;
   if (total > 0) {
-    if (wfa::launch_compact(n, a.nruns, a.run_src, a.runs, nullptr, out_cigar_offsets, out_cigars, cap, st) !=
+    if (wfa::launch_compact(n, a.nruns, a.run_src, a.runs, nullptr, out_cigar_offsets, out_cigars, cap, ctrl, st) !=
             cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       return WFA_GPU_ECUDA;

@@ -71,6 +71,7 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
   constexpr int P = C::P;
   constexpr int NUL = NullOf<Off>::value;
   constexpr unsigned FULL = 0xffffffffu;
+  if (*(volatile int32_t*)&a.ctrl->bad_input) return;  // inputs rejected by the validation kernel
   int& s_last = *s_last_shared;
   UGeo* tab = reinterpret_cast<UGeo*>(smem);
   const int warp = threadIdx.x >> 5, lane32 = threadIdx.x & 31;
