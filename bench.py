@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--short-variant", type=int, default=None,
                     help="force one short-read kernel variant (tuning; default: the library's autotuner)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-pointer (end-to-end) measurement")
+    ap.add_argument("--arena-gb", type=float, default=None,
+                    help="scratch arena size for configs 3 and 4 (default: 16 and 64 GiB)")
     ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4],
                     help="2: the paper's 5M x 100 bp workload (default); 3: 1M mixed-length pairs (100-2,000 bp, "
                          "0-10%% edits, tandem repeats); 4: 20k long-read pairs (10 kbp, 1-5%% edits)")
@@ -229,15 +231,20 @@ def run_config(args):
         b = synth.long_reads(n, 10_000, 0.01, 0.05, seed=4)
         scratch, modes = 64 << 30, (True, False)
         workload = "%d pairs x 10 kbp, edit rate U[1%%,5%%]" % n
+    if args.arena_gb is not None:
+        scratch = int(args.arena_gb * (1 << 30))
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     d = dict(pat=t(b.patterns), plen=t(b.pattern_lengths), txt=t(b.texts), tlen=t(b.text_lengths),
              s=torch.empty(n, dtype=torch.int32, device=dev), st=torch.empty(n, dtype=torch.int8, device=dev),
              off=torch.empty(n + 1, dtype=torch.int64, device=dev))
-    stream = torch.cuda.current_stream(dev)
+    stream = torch.cuda.Stream(dev)
     res = {}
+    runs = [(so, {}) for so in modes]
+    if args.config == 3:  # batched (graph replay) and the plain baseline beside the eager path
+        runs = [(False, {}), (False, dict(graph=True)), (False, dict(plain=True))]
     with pkg.Aligner(0, scratch_bytes=scratch) as al:
         al.set_stream(stream)
-        for score_only in modes:
+        for score_only, extra in runs:
             w = torch.empty(1, dtype=torch.int32, device=dev)
             if not score_only:  # size the CIGAR output from a first call
                 al.align_device(d["pat"], None, d["plen"], d["txt"], None, d["tlen"], d["s"], d["st"], w, d["off"],
@@ -247,7 +254,7 @@ def run_config(args):
             def call():
                 rc = al.align_device(d["pat"], None, d["plen"], d["txt"], None, d["tlen"], d["s"], d["st"],
                                      None if score_only else w, d["off"], pen=PEN, score_only=score_only,
-                                     timing=True)
+                                     timing=True, **extra)
                 assert rc == pkg.WFA_GPU_OK
                 return al.timing()
 
@@ -263,13 +270,18 @@ def run_config(args):
             torch.cuda.synchronize(dev)
             ms = ev0.elapsed_time(ev1) / args.steps
             st = d["st"].cpu().numpy()
-            res["score_only" if score_only else "score_cigar"] = {
+            label = "score_only" if score_only else "score_cigar"
+            if extra:
+                label += "_" + "_".join(k for k in extra)
+            res[label] = {
                 "pairs_per_s": n / (ms / 1000.0), "ms_per_call": ms,
                 "phase_ms": {k: round(float(np.mean([x[k] for x in ts])), 3)
                              for k in ("align_ms", "general_ms", "cigar_ms", "total_ms")},
                 "deferred_pairs": int(ts[-1]["deferred_pairs"]), "short_variant": int(ts[-1]["short_variant"]),
                 "status_ok": int((st == 0).sum()), "mean_score": float(d["s"].float().mean().item())}
-    main_mode = res.get("score_cigar")
+    main_mode = res.get("score_cigar_graph") or res.get("score_cigar")
+    if "score_cigar_plain" in res:
+        res["batched_over_plain"] = main_mode["pairs_per_s"] / res["score_cigar_plain"]["pairs_per_s"]
     line = {"metric": "pairs/s (config %d)" % args.config, "value": main_mode["pairs_per_s"], "unit": "pairs/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": main_mode["ms_per_call"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
@@ -306,7 +318,8 @@ def main():
     batches = make_batches(args.pairs, rank, args.edits)
     if args.short_variant is not None:
         os.environ["WFA_GPU_SHORT_VARIANT"] = str(args.short_variant)
-    stream = torch.cuda.current_stream(dev)
+    # one non-default stream for the library's work and the timing events
+    stream = torch.cuda.Stream(dev)
     al = pkg.Aligner(dev.index)
     al.set_stream(stream)
 
@@ -323,37 +336,57 @@ def main():
             off=torch.empty(n + 1, dtype=torch.int64, device=dev),
             w=torch.empty(CIGAR_WORDS_PER_PAIR * n, dtype=torch.int32, device=dev)))
 
-    def device_step(collect=None):
+    torch.cuda.synchronize(dev)
+
+    # modes: "batched" = the default path with each batch's device work
+    # replayed from a CUDA graph (captured on the first call); "eager" = the
+    # default path launched call by call; "plain" = the baseline path (every
+    # pair on one-warp arena teams, no short-read kernel)
+    MODES = {"batched": dict(graph=True), "eager": {}, "plain": dict(plain=True)}
+
+    def device_step(mode, collect=None):
         for d in dbat:
             rc = al.align_device(d["pat"], None, d["plen"], d["txt"], None, d["tlen"], d["s"], d["st"], d["w"],
-                                 d["off"], pen=PEN, timing=True)
+                                 d["off"], pen=PEN, timing=True, **MODES[mode])
             if rc != pkg.WFA_GPU_OK:
                 raise RuntimeError("CIGAR capacity too small: %d words needed" % int(d["off"][-1]))
             if collect is not None:
                 collect.append(al.timing())
 
-    for _ in range(args.warmup):
-        device_step()
-    torch.cuda.synchronize(dev)
+    def timed(mode, steps, sample_clocks=False):
+        for _ in range(args.warmup):
+            device_step(mode)
+        torch.cuda.synchronize(dev)
+        sampler = ClockSampler(dev.index) if (rank == 0 and sample_clocks) else None
+        if sampler:
+            sampler.start()
+        ts = []
+        sharding.barrier()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            device_step(mode, ts)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        sharding.barrier()
+        clk = sampler.stop() if sampler else None
+        return sharding.max_over_ranks(e0.elapsed_time(e1)), ts, clk
 
-    sampler = ClockSampler(dev.index) if rank == 0 else None
-    if sampler:
-        sampler.start()
-    timings = []
-    sharding.barrier()
-    torch.cuda.synchronize(dev)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        device_step(timings)
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    sharding.barrier()
-    clocks = sampler.stop() if sampler else None
-    ms_local = ev0.elapsed_time(ev1)
-    ms = sharding.max_over_ranks(ms_local)
+    ms, timings, clocks = timed("batched", args.steps, sample_clocks=True)
     pairs_per_step = sum(b.n for b in batches)
     value = pairs_per_step * world * args.steps / (ms / 1000.0)
+    other_modes = {}
+    for mode, steps in (("eager", args.steps), ("plain", max(2, args.steps // 4))):
+        mms, mts, _ = timed(mode, steps)
+        other_modes[mode] = {"pairs_per_s": pairs_per_step * world * steps / (mms / 1000.0),
+                             "ms_per_step": mms / steps, "steps": steps,
+                             "align_kernel_ms": [round(float(np.mean([t["align_ms"] for t in mts[i::len(batches)]])),
+                                                       3) for i in range(len(batches))],
+                             "arena_ms": [round(float(np.mean([t["general_ms"] for t in mts[i::len(batches)]])), 3)
+                                          for i in range(len(batches))]}
+    device_step("batched")  # the outputs read below come from the headline mode
+    torch.cuda.synchronize(dev)
 
     # per-edit-rate figures and the dominant kernel
     per_batch = {}
@@ -495,6 +528,8 @@ def main():
                                                 "total_ms")} if e2e_phases else None},
         "gpu_launches": launches,
         "clocks": clocks,
+        "mode": "batched: default path, each batch's device work replayed from a CUDA graph",
+        "vs_plain": {"batched_over_plain": value / other_modes["plain"]["pairs_per_s"], **other_modes},
         "by_edit_rate": {"E=%d%%" % e: {"pairs_per_s_kernel_path": batches[i].n / (per_batch[e]["total_ms"] / 1000.0),
                                          "align_kernel_ms": per_batch[e]["align_ms"],
                                          "call_ms": per_batch[e]["total_ms"],

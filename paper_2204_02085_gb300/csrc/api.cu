@@ -103,10 +103,17 @@ struct wfa_gpu_ctx {
   DevBuf<int8_t> tune_status;
   DevBuf<int64_t> tune_src;
   int32_t* h_tune = nullptr;  // pinned [kTuneSample]
-  // captured device work of a repeated WFA_GPU_GRAPH call
-  cudaGraphExec_t graph_exec = nullptr;
-  uint64_t graph_key[40] = {};
-  int graph_key_len = 0;
+  // captured device work of repeated WFA_GPU_GRAPH calls (a few kinds of
+  // call, replaced round robin)
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    uint64_t key[40] = {};
+    int key_len = 0;
+    int variant = -1;
+  };
+  static constexpr int kGraphs = 4;
+  Graph graphs[kGraphs];
+  int graph_next = 0;
 };
 
 namespace {
@@ -138,7 +145,10 @@ int map_alloc(cudaError_t e) { return e == cudaErrorMemoryAllocation ? WFA_GPU_E
 
 float elapsed(wfa_gpu_ctx* c, int a, int b) {
   float ms = 0.f;
-  if (cudaEventElapsedTime(&ms, c->ev[a], c->ev[b]) != cudaSuccess) return 0.f;
+  if (cudaEventElapsedTime(&ms, c->ev[a], c->ev[b]) != cudaSuccess) {
+    cudaGetLastError();  // not a failure of the call: leave no error behind
+    return 0.f;
+  }
   return ms;
 }
 
@@ -653,6 +663,8 @@ int enqueue_device_work(wfa_gpu_ctx* c, Call& k, int64_t n, const char* pat, con
                         int8_t* out_status, uint32_t* out_cigars, int64_t cap, int64_t* out_off) {
   cudaStream_t st = c->stream;
   const bool score_only = flags & WFA_GPU_SCORE_ONLY;
+  // external event records become graph nodes: replays time their phases
+  if (!k.ok(cudaEventRecordWithFlags(c->ev[0], st, cudaEventRecordExternal))) return WFA_GPU_ECUDA;
   if (!k.ok(cudaMemsetAsync(c->ctrl, 0, sizeof(wfa::Ctrl), st))) return WFA_GPU_ECUDA;
   const int64_t* d_poff = poff;
   const int64_t* d_toff = toff;
@@ -665,6 +677,7 @@ int enqueue_device_work(wfa_gpu_ctx* c, Call& k, int64_t n, const char* pat, con
     d_toff = c->toff.p;
   }
   if (!k.launched(wfa::launch_validate(n, d_poff, plen, d_toff, tlen, c->ctrl, st))) return WFA_GPU_ECUDA;
+  if (!k.ok(cudaEventRecordWithFlags(c->ev[1], st, cudaEventRecordExternal))) return WFA_GPU_ECUDA;
   wfa::AlignArgs a = device_args(c, n, pat, d_poff, plen, txt, d_toff, tlen, pen, max_score, score_only,
                                  out_scores, out_status);
   if (flags & WFA_GPU_PLAIN) {
@@ -673,6 +686,7 @@ int enqueue_device_work(wfa_gpu_ctx* c, Call& k, int64_t n, const char* pat, con
     if (c->last_variant < 0) return WFA_GPU_ECUDA;
     if (!k.launched(wfa::launch_short(a, c->plan.v[c->last_variant], st))) return WFA_GPU_ECUDA;
   }
+  if (!k.ok(cudaEventRecordWithFlags(c->ev[2], st, cudaEventRecordExternal))) return WFA_GPU_ECUDA;
   const long arena = (long)c->arena_bytes;
   unsigned char* ab = reinterpret_cast<unsigned char*>(c->arena);
   wfa::Ctrl* dc = c->ctrl;
@@ -681,12 +695,14 @@ int enqueue_device_work(wfa_gpu_ctx* c, Call& k, int64_t n, const char* pat, con
       !k.launched(wfa::launch_arena(true, a, a.defer_long_list, &dc->defer_long_count, &dc->next_long,
                                     &dc->overflow_count, ab, (arena / c->teams_long) & ~255L, c->teams_long, st)))
     return WFA_GPU_ECUDA;
+  if (!k.ok(cudaEventRecordWithFlags(c->ev[3], st, cudaEventRecordExternal))) return WFA_GPU_ECUDA;
   if (!score_only) {
     if (!k.launched(wfa::launch_scan(c->nruns.p, n, 0, out_off, c->scan_tmp.p, st), 3) ||
         !k.launched(wfa::launch_compact(n, c->nruns.p, c->run_src.p, c->runs.p, c->pool.p, out_off, out_cigars, cap,
                                         c->ctrl, st)))
       return WFA_GPU_ECUDA;
   }
+  if (!k.ok(cudaEventRecordWithFlags(c->ev[4], st, cudaEventRecordExternal))) return WFA_GPU_ECUDA;
   return 0;
 }
 
@@ -723,17 +739,21 @@ int align_graph(wfa_gpu_ctx* ctx, int64_t n, const char* pat, const int64_t* pof
   const void* ptrs[] = {pat, poff, plen, txt, toff, tlen, out_scores, out_status, out_cigars, out_off};
   uint64_t key[40];
   int kl = graph_key(ctx, key, n, ptrs, 10, pen, max_score, flags, cap);
-  const bool hit = ctx->graph_exec && n > 0 && kl == ctx->graph_key_len &&
-                   std::memcmp(key, ctx->graph_key, kl * sizeof(uint64_t)) == 0;
+  wfa_gpu_ctx::Graph* hit = nullptr;
+  for (auto& gr : ctx->graphs)
+    if (gr.exec && n > 0 && kl == gr.key_len && std::memcmp(key, gr.key, kl * sizeof(uint64_t)) == 0) hit = &gr;
   if (!hit) {
     const int rc = align_eager(ctx, n, pat, poff, plen, txt, toff, tlen, pen, max_score, base, out_scores,
                                out_status, out_cigars, cap, out_off);
     if ((rc != WFA_GPU_OK && rc != WFA_GPU_ECIGAR_CAPACITY) || n == 0) return rc;
-    if (ctx->graph_exec) {
-      cudaGraphExecDestroy(ctx->graph_exec);
-      ctx->graph_exec = nullptr;
-      ctx->graph_key_len = 0;
+    wfa_gpu_ctx::Graph& slot = ctx->graphs[ctx->graph_next];
+    ctx->graph_next = (ctx->graph_next + 1) % wfa_gpu_ctx::kGraphs;
+    if (slot.exec) {
+      cudaGraphExecDestroy(slot.exec);
+      slot.exec = nullptr;
+      slot.key_len = 0;
     }
+    const wfa_gpu_timing eager_timing = ctx->last;
     cudaStream_t st = ctx->stream;
     Call k{ctx, false};
     cudaGraph_t g = nullptr;
@@ -750,21 +770,21 @@ int align_graph(wfa_gpu_ctx* ctx, int64_t n, const char* pat, const int64_t* pof
     const cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
     if (ie != cudaSuccess) return WFA_GPU_ECUDA;
-    ctx->graph_exec = exec;
+    slot.exec = exec;
+    slot.variant = ctx->last_variant;
     kl = graph_key(ctx, key, n, ptrs, 10, pen, max_score, flags, cap);
-    std::memcpy(ctx->graph_key, key, kl * sizeof(uint64_t));
-    ctx->graph_key_len = kl;
+    std::memcpy(slot.key, key, kl * sizeof(uint64_t));
+    slot.key_len = kl;
+    ctx->last = eager_timing;
     return rc;
   }
   if (cudaSetDevice(ctx->device) != cudaSuccess) return WFA_GPU_ECUDA;
-  const int variant = ctx->last_variant;
   std::memset(&ctx->last, 0, sizeof ctx->last);
-  ctx->last_variant = variant;
+  ctx->last_variant = hit->variant;
   cudaStream_t st = ctx->stream;
   Call k{ctx, (flags & WFA_GPU_TIMING) != 0};
-  k.rec(0);
-  if (!k.ok(cudaGraphLaunch(ctx->graph_exec, st))) return WFA_GPU_ECUDA;
-  k.launches += 14;
+  if (!k.ok(cudaGraphLaunch(hit->exec, st))) return WFA_GPU_ECUDA;
+  k.launches += score_only ? 10 : 14;
   int64_t total = 0;
   if (!k.ok(d2h(ctx->h_ctrl, ctx->ctrl, sizeof(wfa::Ctrl), st))) return WFA_GPU_ECUDA;
   if (!score_only && !k.ok(d2h(ctx->h_total, out_off + n, sizeof(int64_t), st))) return WFA_GPU_ECUDA;
@@ -790,11 +810,15 @@ int align_graph(wfa_gpu_ctx* ctx, int64_t n, const char* pat, const int64_t* pof
   }
   if (ctx->h_ctrl->internal_error) return WFA_GPU_ECUDA;
   if (!score_only) total = *ctx->h_total;
-  k.rec(5);
-  if (!k.ok(cudaStreamSynchronize(st))) return WFA_GPU_ECUDA;
   ctx->last.kernel_launches = k.launches;
   ctx->last.short_variant = ctx->last_variant;
-  if (k.timing) ctx->last.total_ms = elapsed(ctx, 0, 5);
+  if (k.timing) {
+    // events recorded by the graph itself
+    ctx->last.align_ms = elapsed(ctx, 1, 2);
+    ctx->last.general_ms = elapsed(ctx, 2, 3);
+    ctx->last.cigar_ms = elapsed(ctx, 3, 4);
+    ctx->last.total_ms = elapsed(ctx, 0, 4);
+  }
   return total > cap ? WFA_GPU_ECIGAR_CAPACITY : WFA_GPU_OK;
 }
 
@@ -938,7 +962,8 @@ void wfa_gpu_destroy(wfa_gpu_ctx* c) {
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
   if (c->h_total) cudaFreeHost(c->h_total);
   if (c->h_tune) cudaFreeHost(c->h_tune);
-  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  for (auto& gr : c->graphs)
+    if (gr.exec) cudaGraphExecDestroy(gr.exec);
   c->tune_score.release(); c->tune_aux.release(); c->tune_status.release(); c->tune_src.release();
   for (int i = 0; i < kEvents; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
