@@ -87,6 +87,8 @@ struct ArenaViewT {
     (void)top;
   }
   __device__ __forceinline__ const OffT* blk(const Geo& g) const { return end - g.base; }
+  // first cell of component c (0 M, 1 I, 2 D) of a stored wavefront
+  __device__ __forceinline__ const OffT* comp(const Geo& g, int c) const { return end - g.base + c * g.w; }
   __device__ __forceinline__ int getM(const Geo& g, int i) const { return blk(g)[i]; }
   __device__ __forceinline__ int getI(const Geo& g, int i) const { return blk(g)[g.w + i]; }
   __device__ __forceinline__ int getD(const Geo& g, int i) const { return blk(g)[2 * g.w + i]; }
@@ -131,6 +133,7 @@ struct RingView {
     (void)b;
     (void)top;
   }
+  __device__ __forceinline__ const OffT* comp(const Geo& g, int c) const { return cells + g.base + c * W; }
   __device__ __forceinline__ int getM(const Geo& g, int i) const { return cells[g.base + i]; }
   __device__ __forceinline__ int getI(const Geo& g, int i) const { return cells[g.base + W + i]; }
   __device__ __forceinline__ int getD(const Geo& g, int i) const { return cells[g.base + 2 * W + i]; }
@@ -140,11 +143,31 @@ struct RingView {
   }
 };
 
-// The score loop for one pair on a team (same recurrences, range rules and
-// outcomes as wfa_forward).  Metadata of each score is written by every
-// warp's lane 0 (identical values), so each warp reads its own writes.
+// One source of the recurrences for a step: cells of one component of one
+// stored wavefront, diagonals [lo, lo + w) (w == 0: absent).
+template <typename OffT>
+struct Src {
+  const OffT* p;
+  int lo;
+  unsigned w;
+  __device__ __forceinline__ int at(int k, int null_v) const {
+    const unsigned i = (unsigned)(k - lo);
+    return i < w ? (int)p[i] : null_v;
+  }
+};
+
+template <class V>
+__device__ __forceinline__ Src<typename V::Off> src_of(const V& view, const Geo& g, int c) {
+  return Src<typename V::Off>{g.w ? view.comp(g, c) : nullptr, g.lo, (unsigned)g.w};
+}
+
+// The score loop for one pair on a team (the recurrences, range rules and
+// outcomes of the short kernel's loop, with per-score ranges from the stored
+// metadata).  Metadata of each score is written by every warp's lane 0
+// (identical values), so each warp reads its own writes.  Packed sequences
+// are 32-bit words (16 bases).
 template <int WPP, class V>
-__device__ int team_forward(V& view, const uint64_t* pw, const uint64_t* tw, int n, int m, ScaledPen p, int s_cap,
+__device__ int team_forward(V& view, const uint32_t* pw, const uint32_t* tw, int n, int m, ScaledPen p, int s_cap,
                             int* flags, int& round, int* s_out) {
   using Off = typename V::Off;
   using T = Team<WPP>;
@@ -154,7 +177,7 @@ __device__ int team_forward(V& view, const uint64_t* pw, const uint64_t* tw, int
   const int kf = m - n;
   int top = 0, b0 = 0;
   if (!view.alloc(0, 1, top, b0)) return kFwdOverflow;
-  if (r == 0) view.put(b0, 1, 0, extend_diag(pw, tw, n, m, 0, 0), NUL, NUL);
+  if (r == 0) view.put(b0, 1, 0, extend_diag32(pw, tw, n, m, 0, 0, 1), NUL, NUL);
   if (leader) view.set_meta(0, 0, 0, b0, 1);
   T::sync();
   if (kf == 0 && view.getM(Geo{0, 1, b0}, 0) == m) {
@@ -184,12 +207,14 @@ __device__ int team_forward(V& view, const uint64_t* pw, const uint64_t* tw, int
     int b = 0;
     if (!view.alloc(s, w, top, b)) return kFwdOverflow;
     int bits = 0;
+    const Src<Off> sx = src_of(view, gx, 0), so = src_of(view, go, 0);
+    const Src<Off> si = src_of(view, gi, 1), sd = src_of(view, gd, 2);
     for (int k = lo + r; k <= hi; k += T::kSize) {
-      const int mx = get_off<V, 0>(view, gx, k, NUL);
-      const int ml = get_off<V, 0>(view, go, k - 1, NUL);
-      const int mr = get_off<V, 0>(view, go, k + 1, NUL);
-      const int il = get_off<V, 1>(view, gi, k - 1, NUL);
-      const int dr = get_off<V, 2>(view, gd, k + 1, NUL);
+      const int mx = sx.at(k, NUL);
+      const int ml = so.at(k - 1, NUL);
+      const int mr = so.at(k + 1, NUL);
+      const int il = si.at(k - 1, NUL);
+      const int dr = sd.at(k + 1, NUL);
       int iv = max(ml, il) + 1;
       if (iv < 0 || iv > m) iv = NUL;
       int dv = max(mr, dr);
@@ -198,7 +223,7 @@ __device__ int team_forward(V& view, const uint64_t* pw, const uint64_t* tw, int
       if (mx < 0 || xv > m || xv - k > n) xv = NUL;
       int mv = max(xv, max(iv, dv));
       if (mv >= 0) {
-        mv = extend_diag(pw, tw, n, m, k, mv);
+        mv = extend_diag32(pw, tw, n, m, k, mv, 1);
         bits |= 1;
       } else {
         mv = NUL;
@@ -217,15 +242,31 @@ __device__ int team_forward(V& view, const uint64_t* pw, const uint64_t* tw, int
   }
 }
 
-// Team packing of one sequence into out[0 .. ceil(len/32)] (64-bit words,
-// last one zero).  Returns, for every member, whether every byte is valid.
+// Team packing of one sequence into out[0 .. ceil(len/16)] (32-bit words of
+// 16 bases, first base in the top bits, last word zero); each word reads the
+// one or two aligned 16-byte chunks holding its bases.  Returns, for every
+// member, whether every byte is A/C/G/T.
 template <int WPP>
-__device__ __forceinline__ bool team_pack(const char* __restrict__ seq, int len, uint64_t* out, int* flags,
-                                          int& round) {
-  const int nwords = (len + 31) >> 5;
+__device__ __forceinline__ bool team_pack32(const char* __restrict__ seq, int len, uint32_t* out, int* flags,
+                                            int& round) {
+  const int nw = (len + 15) >> 4;
+  const unsigned long long a = reinterpret_cast<uintptr_t>(seq);
   bool bad = false;
-  for (int w = Team<WPP>::rank(); w <= nwords; w += Team<WPP>::kSize)
-    out[w] = (w < nwords) ? pack_word(seq, len, w, &bad) : 0ull;
+  for (int j = Team<WPP>::rank(); j <= nw; j += Team<WPP>::kSize) {
+    uint32_t word = 0u;
+    if (j < nw) {
+      const unsigned long long w0 = a + 16ull * j, b0 = w0 & ~15ull;
+      const int h = (int)(w0 - b0), rem = min(16, len - 16 * j);
+      uint32_t m0, m1 = 0u, c1 = 0u;
+      const uint32_t c0 = code16_bad(__ldg(reinterpret_cast<const uint4*>(b0)), &m0);
+      if (h + rem > 16) c1 = code16_bad(__ldg(reinterpret_cast<const uint4*>(b0 + 16)), &m1);
+      word = __funnelshift_l(c1, c0, 2 * h);
+      if (rem < 16) word &= ~0u << (32 - 2 * rem);
+      const uint32_t in = (rem >= 16 ? 0xFFFFu : ((1u << rem) - 1u)) << h;
+      if ((m0 | (m1 << 16)) & in) bad = true;
+    }
+    out[j] = word;
+  }
   return Team<WPP>::reduce_or(bad ? 1 : 0, flags, round) == 0;
 }
 
@@ -285,11 +326,13 @@ __device__ void arena_body(const AlignArgs& a, const int32_t* list, const int32_
   if (team >= nteams) return;  // whole team: uniform
   if (*(volatile const int32_t*)&a.ctrl->bad_input) return;  // inputs rejected by the validation kernel
   const int team_in_block = WPP == 1 ? (int)(threadIdx.x >> 5) : 0;
+  // seq_words 64-bit words per sequence = 2 * seq_words 32-bit words
   const size_t team_smem = sizeof(TeamShm) + 2 * (size_t)seq_words * sizeof(uint64_t);
   unsigned char* my = smem + team_in_block * team_smem;
   TeamShm* ts = reinterpret_cast<TeamShm*>(my);
-  uint64_t* spw = reinterpret_cast<uint64_t*>(my + sizeof(TeamShm));
-  uint64_t* stw = spw + seq_words;
+  const int sw32 = 2 * seq_words;
+  uint32_t* spw = reinterpret_cast<uint32_t*>(my + sizeof(TeamShm));
+  uint32_t* stw = spw + sw32;
   const int r = T::rank();
   if (r == 0) ts->flags[0] = ts->flags[1] = ts->flags[2] = 0;
   T::sync();
@@ -301,20 +344,20 @@ __device__ void arena_body(const AlignArgs& a, const int32_t* list, const int32_
     if (idx >= *(volatile const int32_t*)count) break;
     const int64_t pair = list[idx];
     const int n = a.plen[pair], m = a.tlen[pair];
-    const long nwp = (n + 31) / 32 + 1, nwt = (m + 31) / 32 + 1;
+    const long nwp = (n + 15) / 16 + 1, nwt = (m + 15) / 16 + 1;  // 32-bit words incl. the zero pad
     // sequences in shared memory if they fit, else at the slice's start
-    const bool in_smem = nwp <= seq_words && nwt <= seq_words;
-    uint64_t* pw = in_smem ? spw : reinterpret_cast<uint64_t*>(slot);
-    uint64_t* tw = in_smem ? stw : reinterpret_cast<uint64_t*>(slot) + nwp;
-    const long seq_bytes = in_smem ? 0 : 8L * (nwp + nwt);
+    const bool in_smem = nwp <= sw32 && nwt <= sw32;
+    uint32_t* pw = in_smem ? spw : reinterpret_cast<uint32_t*>(slot);
+    uint32_t* tw = in_smem ? stw : reinterpret_cast<uint32_t*>(slot) + nwp;
+    const long seq_bytes = in_smem ? 0 : (4L * (nwp + nwt) + 15) & ~15L;
     const long room = slot_bytes - seq_bytes;
     if (room < 1024) {
       if (r == 0) overflow_pair_to(a, pair, overflow_count);
       T::sync();
       continue;
     }
-    const bool okp = team_pack<WPP>(a.pat + a.poff[pair], n, pw, ts->flags, round);
-    const bool okt = team_pack<WPP>(a.txt + a.toff[pair], m, tw, ts->flags, round);
+    const bool okp = team_pack32<WPP>(a.pat + a.poff[pair], n, pw, ts->flags, round);
+    const bool okt = team_pack32<WPP>(a.txt + a.toff[pair], m, tw, ts->flags, round);
     if (!(okp && okt)) {
       if (r == 0) write_result(a, pair, 2, -1, 0, 0);
       T::sync();
