@@ -68,9 +68,13 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-pointer (end-to-end) measurement")
     ap.add_argument("--arena-gb", type=float, default=None,
                     help="scratch arena size for configs 3 and 4 (default: 16 and 64 GiB)")
-    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4],
+    ap.add_argument("--requests", type=int, default=2000, help="requests in the serving trace (config 5)")
+    ap.add_argument("--workers", type=int, default=2, help="server slots (config 5)")
+    ap.add_argument("--baselines", type=int, default=1, help="config 5: also replay the one-at-a-time baselines")
+    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5],
                     help="2: the paper's 5M x 100 bp workload (default); 3: 1M mixed-length pairs (100-2,000 bp, "
-                         "0-10%% edits, tandem repeats); 4: 20k long-read pairs (10 kbp, 1-5%% edits)")
+                         "0-10%% edits, tandem repeats); 4: 20k long-read pairs (10 kbp, 1-5%% edits); 5: serving, "
+                         "a Poisson stream of requests")
     args = ap.parse_args()
     args.edits = tuple(int(e) for e in args.edits.split(","))
     return args
@@ -291,10 +295,129 @@ def run_config(args):
     return 0
 
 
+def run_serving(args):
+    """Configuration 5: a Poisson stream of requests (2,000 per second;
+    batch sizes log-uniform 1-4,096 pairs; lengths log-uniform 100-5,000 bp;
+    edit rate U[2%, 8%]; seed 5) replayed in real time against the
+    continuous-batching server (2 slots by default; queued requests of the
+    same parameters are merged into one call), then all queued at once
+    (capacity), then without a server: one request at a time in arrival order
+    on the default path, and on the plain path.  Requests are windows of a
+    pool of page-locked pairs, built before the clock starts."""
+    import threading as th
+
+    import torch
+
+    import paper_2204_02085_gb300 as pkg
+    from paper_2204_02085_gb300 import build as gpu_build
+    from paper_2204_02085_gb300 import synth
+
+    gpu_build.build()
+    rng = np.random.Generator(np.random.PCG64(5))
+    pool_n = 60_000
+    pool = synth.mixed_reads(pool_n, 100, 5000, 0.08, 0.0, seed=5, rate_lo=0.02)
+
+    def pin(a):
+        t = torch.empty(a.shape, dtype={np.uint8: torch.uint8, np.int32: torch.int32,
+                                         np.int64: torch.int64}[a.dtype.type], pin_memory=True)
+        t.numpy()[...] = a
+        return t.numpy()
+
+    pool = synth.Batch(pin(pool.patterns), pin(pool.pattern_offsets), pin(pool.pattern_lengths), pin(pool.texts),
+                       pin(pool.text_offsets), pin(pool.text_lengths))
+    R = args.requests
+    gaps = rng.exponential(1.0 / 2000.0, size=R)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    sizes = np.minimum(np.exp(rng.uniform(0, np.log(4096), size=R)).astype(np.int64), pool_n)
+    starts = rng.integers(0, pool_n - sizes + 1)
+    reqs = []
+    for a0, n in zip(starts, sizes):
+        sl = slice(int(a0), int(a0 + n))
+        reqs.append(synth.Batch(pool.patterns, pool.pattern_offsets[sl], pool.pattern_lengths[sl], pool.texts,
+                                pool.text_offsets[sl], pool.text_lengths[sl]))
+    caps = [int(b.pattern_lengths.sum() + b.text_lengths.sum()) + 1 for b in reqs]
+    total_pairs = int(sizes.sum())
+
+    def replay(workers, plain, burst=False):
+        with pkg.Server(0, workers=workers, memory_budget_bytes=32 << 30) as srv:
+            # warm-up, untimed: kernels loaded, then a burst so that every
+            # slot grows its buffers to merged-batch size
+            for b, c in zip(reqs[:4], caps[:4]):
+                srv.wait(srv.submit(b, PEN, cigar_capacity=c, plain=plain))
+            for rid in [srv.submit(b, PEN, cigar_capacity=c, plain=plain) for b, c in zip(reqs[:256], caps[:256])]:
+                srv.wait(rid)
+            ids, stats = [None] * R, [None] * R
+            done = th.Event()
+
+            def waiter():
+                for j in range(R):
+                    while ids[j] is None:
+                        time.sleep(0.0001)
+                    stats[j] = srv.wait(ids[j])[1]
+                done.set()
+
+            w = th.Thread(target=waiter)
+            w.start()
+            t0 = time.perf_counter()
+            for j in range(R):
+                delay = arrivals[j] - (time.perf_counter() - t0)
+                if delay > 0 and not burst:
+                    time.sleep(delay)
+                ids[j] = srv.submit(reqs[j], PEN, cigar_capacity=caps[j], plain=plain)
+            done.wait()
+            w.join()
+        lat = np.array([(s.end_s - s.submit_s) * 1000.0 for s in stats])
+        span = max(s.end_s for s in stats) - min(s.submit_s for s in stats)
+        calls = len({(s.worker, s.start_s) for s in stats})
+        return {"workers": workers, "plain": plain, "calls": calls, "pairs_per_call": total_pairs / calls,
+                "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                "pairs_per_s": total_pairs / span, "span_s": span,
+                "all_ok": all(s.result == pkg.WFA_GPU_OK for s in stats)}
+
+    def one_at_a_time(plain):
+        """The same trace served without a server: one request at a time in
+        arrival order, each aligned alone (default or plain path)."""
+        with pkg.Aligner(0, 16 << 30) as al:
+            for b, c in zip(reqs[:4], caps[:4]):
+                al.align(b, PEN, cigar_capacity=c, plain=plain)
+            lat = np.empty(R)
+            t0 = time.perf_counter()
+            for j in range(R):
+                delay = arrivals[j] - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+                al.align(reqs[j], PEN, cigar_capacity=caps[j], plain=plain)
+                lat[j] = (time.perf_counter() - t0 - arrivals[j]) * 1000.0
+            span = time.perf_counter() - t0
+        return {"workers": 1, "plain": plain, "calls": R, "pairs_per_call": total_pairs / R,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "pairs_per_s": total_pairs / span, "span_s": span, "all_ok": True}
+
+    serving = replay(args.workers, False)
+    saturated = replay(args.workers, False, burst=True)  # every request queued at once: capacity
+    one = one_at_a_time(False) if args.baselines else None
+    plain = one_at_a_time(True) if args.baselines else None
+    line = {"metric": "pairs/s and p50/p99 latency (config 5, serving)", "value": serving["pairs_per_s"],
+            "unit": "pairs/s", "n_gpus": 1, "steps": R, "warmup": 260, "ms_per_step": serving["mean_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": "%d requests, Poisson 2,000/s, batch sizes log-uniform 1-4,096, lengths "
+                                   "log-uniform 100-5,000 bp, edit rate U[2%%,8%%], penalties 4/6/2, score+CIGAR"
+                                   % R, "offered_pairs": total_pairs,
+                       "offered_pairs_per_s": total_pairs / float(arrivals[-1] or 1.0)},
+            "serving": serving, "saturated": saturated, "one_at_a_time": one, "plain_per_batch": plain,
+            "p99_plain_over_serving": plain["p99_ms"] / serving["p99_ms"] if plain else None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == 5:
+        return run_serving(args)
     if args.config != 2:
         return run_config(args)
 

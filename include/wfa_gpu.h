@@ -229,6 +229,82 @@ int wfa_gpu_align_short_noalloc(void *stream, int64_t n_pairs,
                                 uint32_t *out_cigars, int64_t cigar_capacity_words,
                                 int64_t *out_cigar_offsets);
 
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of alignment requests.
+ *
+ * Requests (batches of pairs, of any size, arriving at any time) are queued
+ * and admitted in arrival order onto `workers` slots, each a context with its
+ * own stream, buffers and scratch arena, so the work of several slots
+ * overlaps on the GPU.  A request is admitted when a slot is free and its
+ * estimated device memory (wfa_gpu_request_bytes) fits what the admitted
+ * ones leave of the memory budget (a request alone is always admitted).  A
+ * slot that admits a request also takes the requests queued right behind it
+ * that have the same penalties, max_score and flags, up to
+ * WFA_GPU_SERVER_MERGE_PAIRS pairs in all and within the budget: it copies
+ * their pairs into one page-locked batch, aligns that with one call and
+ * copies each request's results back into its own buffers.
+ * Every request's outputs and result code are the ones wfa_gpu_align_batch
+ * gives for it alone (pairs are independent: paper Sec. I; a request whose
+ * CIGAR words exceed its capacity gets WFA_GPU_ECIGAR_CAPACITY as alone, and
+ * a merged call that fails is re-run one request at a time); only the timing
+ * depends on the mix.
+ * --------------------------------------------------------------------------- */
+#define WFA_GPU_SERVER_MERGE_PAIRS 65536
+typedef struct wfa_gpu_server wfa_gpu_server;
+
+/* One request: the arguments of wfa_gpu_align_batch, host memory only
+ * (flags may hold WFA_GPU_SCORE_ONLY and WFA_GPU_PLAIN).  The caller keeps
+ * every buffer alive and untouched until wfa_gpu_server_wait returns for it. */
+typedef struct {
+  int64_t n_pairs;
+  const char *patterns;
+  const int64_t *pattern_offsets;
+  const int32_t *pattern_lengths;
+  const char *texts;
+  const int64_t *text_offsets;
+  const int32_t *text_lengths;
+  wfa_gpu_penalties pen;
+  int32_t max_score;
+  uint32_t flags;
+  int32_t *out_scores;
+  int8_t *out_status;
+  uint32_t *out_cigars;
+  int64_t cigar_capacity_words;
+  int64_t *out_cigar_offsets;
+} wfa_gpu_request;
+
+/* Times of a finished request, in seconds on the server's clock (a steady
+ * clock started by wfa_gpu_server_create), and its result code. */
+typedef struct {
+  double submit_s, start_s, end_s;
+  int32_t result;  /* what wfa_gpu_align_batch returned for it */
+  int32_t worker;  /* slot that ran it */
+} wfa_gpu_request_stats;
+
+/* Create a server on `device` with `workers` slots (1..64) and a device
+ * memory budget (0: 8 GiB): half is split evenly into the slots' scratch
+ * arenas, the other half is the admission budget.  Returns OK, EINVAL,
+ * ECUDA or ENOMEM; *out is NULL on failure. */
+int wfa_gpu_server_create(wfa_gpu_server **out, int device, int workers, size_t memory_budget_bytes);
+
+/* Queue a request; returns its id (>= 0) or a negative WFA_GPU_* code
+ * (EINVAL for a malformed request).  Never blocks on the GPU. */
+int64_t wfa_gpu_server_submit(wfa_gpu_server *server, const wfa_gpu_request *req);
+
+/* Wait until request `id` has finished (timeout_s < 0: no limit) and return
+ * its result code, filling *stats if not NULL; the id is then forgotten.
+ * Returns WFA_GPU_ETIMEOUT if the wait ran out (the request stays queued or
+ * running; wait again later), EINVAL for an unknown id. */
+int wfa_gpu_server_wait(wfa_gpu_server *server, int64_t id, double timeout_s, wfa_gpu_request_stats *stats);
+
+/* Estimated device bytes a request holds while it runs (inputs, outputs,
+ * per-pair work buffers): the admission rule's measure.  Host-only. */
+int64_t wfa_gpu_request_bytes(const wfa_gpu_request *req);
+
+/* Finish the admitted requests, drop the queued ones (their waits return
+ * ECUDA) and release the server.  NULL-safe. */
+void wfa_gpu_server_destroy(wfa_gpu_server *server);
+
 /* Upper bound on the CIGAR words of one pair of lengths plen, tlen under pen
  * and max_score (<= 0: unbounded): with s the largest score the pair can
  * report, at most 2*floor(s / min(x, o+e)) + 1 runs, and never more than

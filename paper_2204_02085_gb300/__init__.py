@@ -28,6 +28,7 @@ WFA_GPU_ETIMEOUT = -5
 WFA_PAIR_OK, WFA_PAIR_SCORE_LIMIT, WFA_PAIR_INVALID_CHAR = 0, 1, 2
 WFA_GPU_SCORE_ONLY, WFA_GPU_DEVICE_PTRS, WFA_GPU_TIMING, WFA_GPU_PLAIN, WFA_GPU_GRAPH = 1, 2, 4, 8, 16
 WFA_GPU_MAX_SEQ_LEN = (1 << 28) - 1
+WFA_GPU_SERVER_MERGE_PAIRS = 65536
 
 # every function include/wfa_gpu.h declares
 EXPORTS = (
@@ -40,6 +41,11 @@ EXPORTS = (
     "wfa_gpu_strerror",
     "wfa_gpu_destroy",
     "wfa_gpu_align_short_noalloc",
+    "wfa_gpu_server_create",
+    "wfa_gpu_server_submit",
+    "wfa_gpu_server_wait",
+    "wfa_gpu_request_bytes",
+    "wfa_gpu_server_destroy",
 )
 WFA_GPU_NOALLOC_SCRATCH_BYTES = 4 << 20
 WFA_GPU_NOALLOC_MAX_PAIRS = 32768
@@ -65,6 +71,36 @@ class Timing(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class Request(ctypes.Structure):
+    _fields_ = [
+        ("n_pairs", ctypes.c_int64),
+        ("patterns", ctypes.c_void_p),
+        ("pattern_offsets", ctypes.c_void_p),
+        ("pattern_lengths", ctypes.c_void_p),
+        ("texts", ctypes.c_void_p),
+        ("text_offsets", ctypes.c_void_p),
+        ("text_lengths", ctypes.c_void_p),
+        ("pen", Penalties),
+        ("max_score", ctypes.c_int32),
+        ("flags", ctypes.c_uint32),
+        ("out_scores", ctypes.c_void_p),
+        ("out_status", ctypes.c_void_p),
+        ("out_cigars", ctypes.c_void_p),
+        ("cigar_capacity_words", ctypes.c_int64),
+        ("out_cigar_offsets", ctypes.c_void_p),
+    ]
+
+
+class RequestStats(ctypes.Structure):
+    _fields_ = [
+        ("submit_s", ctypes.c_double),
+        ("start_s", ctypes.c_double),
+        ("end_s", ctypes.c_double),
+        ("result", ctypes.c_int32),
+        ("worker", ctypes.c_int32),
+    ]
 
 
 class WfaGpuError(RuntimeError):
@@ -104,6 +140,16 @@ def load(path: str = LIB_PATH):
     L.wfa_gpu_destroy.restype = None
     L.wfa_gpu_align_short_noalloc.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, Penalties, i32, vp, vp, vp, i64, vp]
     L.wfa_gpu_align_short_noalloc.restype = ctypes.c_int
+    L.wfa_gpu_server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_size_t]
+    L.wfa_gpu_server_create.restype = ctypes.c_int
+    L.wfa_gpu_server_submit.argtypes = [vp, ctypes.POINTER(Request)]
+    L.wfa_gpu_server_submit.restype = i64
+    L.wfa_gpu_server_wait.argtypes = [vp, i64, ctypes.c_double, ctypes.POINTER(RequestStats)]
+    L.wfa_gpu_server_wait.restype = ctypes.c_int
+    L.wfa_gpu_request_bytes.argtypes = [ctypes.POINTER(Request)]
+    L.wfa_gpu_request_bytes.restype = i64
+    L.wfa_gpu_server_destroy.argtypes = [vp]
+    L.wfa_gpu_server_destroy.restype = None
     _lib = L
     return L
 
@@ -297,3 +343,96 @@ class Aligner:
         if rc != WFA_GPU_OK:
             raise WfaGpuError(rc, "wfa_gpu_pack2bit")
         return words[:cap], woff, inv[:n]
+
+
+# ------------------------------------------------------------------ serving
+
+
+def wfa_gpu_server_create(device: int = 0, workers: int = 4, memory_budget_bytes: int = 0):
+    h = ctypes.c_void_p()
+    rc = load().wfa_gpu_server_create(ctypes.byref(h), device, workers, memory_budget_bytes)
+    return rc, (h if rc == WFA_GPU_OK else None)
+
+
+def wfa_gpu_server_submit(server, req: Request) -> int:
+    return load().wfa_gpu_server_submit(server, ctypes.byref(req))
+
+
+def wfa_gpu_server_wait(server, rid: int, timeout_s: float = -1.0):
+    st = RequestStats()
+    rc = load().wfa_gpu_server_wait(server, rid, timeout_s, ctypes.byref(st))
+    return rc, st
+
+
+def wfa_gpu_request_bytes(req: Request) -> int:
+    return load().wfa_gpu_request_bytes(ctypes.byref(req))
+
+
+def wfa_gpu_server_destroy(server) -> None:
+    load().wfa_gpu_server_destroy(server)
+
+
+class Server:
+    """Continuous-batching request server (host buffers).  ``submit`` takes a
+    batch and returns a request id at once; ``wait`` returns its outputs
+    (scores, status, CIGAR words, CIGAR offsets) and timing."""
+
+    def __init__(self, device: int = 0, workers: int = 4, memory_budget_bytes: int = 0):
+        rc, h = wfa_gpu_server_create(device, workers, memory_budget_bytes)
+        if rc != WFA_GPU_OK:
+            raise WfaGpuError(rc, "wfa_gpu_server_create")
+        self.h = h
+        self._pending = {}
+
+    def submit(self, batch, pen=(4, 6, 2), max_score: int = 0, score_only: bool = False, plain: bool = False,
+               cigar_capacity: int | None = None) -> int:
+        n = int(len(batch.pattern_lengths))
+        keep = dict(
+            pat=np.ascontiguousarray(batch.patterns, dtype=np.uint8),
+            txt=np.ascontiguousarray(batch.texts, dtype=np.uint8),
+            plen=np.ascontiguousarray(batch.pattern_lengths, dtype=np.int32),
+            tlen=np.ascontiguousarray(batch.text_lengths, dtype=np.int32),
+            poff=None if batch.pattern_offsets is None else np.ascontiguousarray(batch.pattern_offsets, np.int64),
+            toff=None if batch.text_offsets is None else np.ascontiguousarray(batch.text_offsets, np.int64),
+            s=np.empty(n, np.int32), st=np.empty(n, np.int8), off=np.zeros(n + 1, np.int64))
+        if cigar_capacity is None:
+            bound = sum(int(wfa_gpu_cigar_bound(int(p), int(t), pen, max_score))
+                        for p, t in zip(keep["plen"], keep["tlen"])) if not score_only else 0
+            cigar_capacity = bound
+        keep["w"] = np.empty(max(1, cigar_capacity), np.uint32)
+        flags = (WFA_GPU_SCORE_ONLY if score_only else 0) | (WFA_GPU_PLAIN if plain else 0)
+        req = Request(n, _addr(keep["pat"]), _addr(keep["poff"]), _addr(keep["plen"]), _addr(keep["txt"]),
+                      _addr(keep["toff"]), _addr(keep["tlen"]), pen if isinstance(pen, Penalties) else Penalties(*pen),
+                      max_score, flags, _addr(keep["s"]), _addr(keep["st"]), None if score_only else _addr(keep["w"]),
+                      0 if score_only else cigar_capacity, None if score_only else _addr(keep["off"]))
+        keep["req"] = req
+        rid = wfa_gpu_server_submit(self.h, req)
+        if rid < 0:
+            raise WfaGpuError(int(rid), "wfa_gpu_server_submit")
+        self._pending[rid] = keep
+        return rid
+
+    def wait(self, rid: int, timeout_s: float = -1.0, check: bool = True):
+        """Outputs and stats of request ``rid``.  With ``check`` a result
+        other than OK raises WfaGpuError; without it the outputs are returned
+        as the call left them and ``stats.result`` holds the code."""
+        rc, st = wfa_gpu_server_wait(self.h, rid, timeout_s)
+        if rc == WFA_GPU_ETIMEOUT:
+            raise TimeoutError("request %d still running" % rid)
+        keep = self._pending.pop(rid)
+        if rc != WFA_GPU_OK and check:
+            raise WfaGpuError(rc, "request %d" % rid)
+        off = keep["off"]
+        used = int(off[-1]) if rc == WFA_GPU_OK else 0
+        return (keep["s"], keep["st"], keep["w"][:used], off), st
+
+    def close(self):
+        if self.h is not None:
+            wfa_gpu_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <new>
 
+#include "internal.h"
 #include "launch.h"
 #include "wfa_gpu.h"
 
@@ -22,10 +23,12 @@ struct DevBuf {
   // grow to at least n elements (contents are not kept)
   cudaError_t ensure(size_t n) {
     if (n <= cap && p) return cudaSuccess;
+    // geometric growth: few reallocations (each cudaFree synchronises the
+    // device) when batch sizes creep up
+    const size_t want = std::max<size_t>(std::max(n + n / 2, 2 * cap), 64);
     if (p) cudaFree(p);
     p = nullptr;
     cap = 0;
-    size_t want = std::max<size_t>(n + n / 4, 64);
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p), want * sizeof(T));
     if (e != cudaSuccess) {
       p = nullptr;
@@ -36,6 +39,32 @@ struct DevBuf {
   }
   void release() {
     if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+// Page-locked host staging, grown geometrically, contents not kept.
+template <class T>
+struct HostBuf {
+  T* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t n) {
+    if (n <= cap && p) return cudaSuccess;
+    const size_t want = std::max<size_t>(std::max(n + n / 2, 2 * cap), 64);
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&p), want * sizeof(T), cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    cap = want;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFreeHost(p);
     p = nullptr;
     cap = 0;
   }
@@ -62,6 +91,10 @@ constexpr int64_t kPoolInitWords = 1 << 22;
 
 struct wfa_gpu_ctx {
   int device = 0;
+  // where the CIGAR words of a host-pointer call go when set: asked for once
+  // their total is known (merged server calls size their staging with it)
+  wfa::CigarSink cig_sink = nullptr;
+  void* cig_sink_user = nullptr;
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;
   int32_t* arena = nullptr;
@@ -88,11 +121,16 @@ struct wfa_gpu_ctx {
   DevBuf<char> pat, txt;
   DevBuf<int32_t> plen, tlen;
   DevBuf<int64_t> poff, toff;
-  // outputs staged for host memory
+  // outputs staged for host memory: device buffers, and page-locked host
+  // staging for callers' pageable buffers
   DevBuf<int32_t> score;
   DevBuf<int8_t> status;
   DevBuf<int64_t> cig_off;
   DevBuf<uint32_t> cig;
+  HostBuf<int32_t> h_score;
+  HostBuf<int8_t> h_status;
+  HostBuf<int64_t> h_off;
+  HostBuf<uint32_t> h_cig;
   // internal
   DevBuf<int32_t> nruns, defer, defer_long, overflow;
   DevBuf<int64_t> run_src, scan_tmp;
@@ -115,6 +153,12 @@ struct wfa_gpu_ctx {
   Graph graphs[kGraphs];
   int graph_next = 0;
 };
+
+void wfa::set_cigar_sink(wfa_gpu_ctx* ctx, wfa::CigarSink sink, void* user) {
+  if (!ctx) return;
+  ctx->cig_sink = sink;
+  ctx->cig_sink_user = user;
+}
 
 namespace {
 
@@ -286,14 +330,17 @@ int run_arena(wfa_gpu_ctx* c, Call& k, wfa::AlignArgs& a) {
   wfa::Ctrl* hc = c->h_ctrl;
   wfa::Ctrl* dc = c->ctrl;
   const long arena = (long)c->arena_bytes;
-  if (hc->defer_count > 0 &&
-      !k.launched(wfa::launch_arena(false, a, a.defer_list, &dc->defer_count, &dc->next_medium, &dc->overflow_count,
-                                    reinterpret_cast<unsigned char*>(c->arena), (arena / c->teams_medium) & ~255L, c->teams_medium, st)))
+  // no more teams than pairs: small batches leave the GPU to concurrent work
+  // and get larger arena slices
+  const int tm = std::min<int>(c->teams_medium, hc->defer_count);
+  const int tl = std::min<int>(c->teams_long, hc->defer_long_count);
+  if (tm > 0 && !k.launched(wfa::launch_arena(false, a, a.defer_list, &dc->defer_count, &dc->next_medium,
+                                              &dc->overflow_count, reinterpret_cast<unsigned char*>(c->arena),
+                                              (arena / tm) & ~255L, tm, st)))
     return WFA_GPU_ECUDA;
-  if (hc->defer_long_count > 0 &&
-      !k.launched(wfa::launch_arena(true, a, a.defer_long_list, &dc->defer_long_count, &dc->next_long,
-                                    &dc->overflow_count, reinterpret_cast<unsigned char*>(c->arena), (arena / c->teams_long) & ~255L, c->teams_long,
-                                    st)))
+  if (tl > 0 && !k.launched(wfa::launch_arena(true, a, a.defer_long_list, &dc->defer_long_count, &dc->next_long,
+                                              &dc->overflow_count, reinterpret_cast<unsigned char*>(c->arena),
+                                              (arena / tl) & ~255L, tl, st)))
     return WFA_GPU_ECUDA;
   if (!k.ok(d2h(hc, dc, sizeof(wfa::Ctrl), st)) || !k.ok(cudaStreamSynchronize(st))) return WFA_GPU_ECUDA;
   return run_retries(c, k, a);
@@ -330,7 +377,7 @@ int run_retries(wfa_gpu_ctx* c, Call& k, wfa::AlignArgs& a) {
       a.pool_cap = want;
     } else {
       if (teams == 1) return WFA_GPU_ENOMEM;  // a pair needs more than the whole arena
-      teams = std::max(1, teams / 8);
+      teams = std::max(1, std::min(teams, hc->overflow_count) / 8);
     }
     hc->retry_count = hc->overflow_count;
     hc->next_retry = 0;
@@ -339,8 +386,9 @@ int run_retries(wfa_gpu_ctx* c, Call& k, wfa::AlignArgs& a) {
     if (!k.ok(cudaMemcpyAsync(dc, hc, sizeof(wfa::Ctrl), cudaMemcpyHostToDevice, st))) return WFA_GPU_ECUDA;
     wfa::AlignArgs ar = a;
     ar.overflow_list = out;
-    if (!k.launched(wfa::launch_arena(true, ar, in, &dc->retry_count, &dc->next_retry, &dc->overflow_count, reinterpret_cast<unsigned char*>(c->arena),
-                                      (arena / teams) & ~255L, teams, st)))
+    const int nt = std::max(1, std::min(teams, hc->retry_count));
+    if (!k.launched(wfa::launch_arena(true, ar, in, &dc->retry_count, &dc->next_retry, &dc->overflow_count,
+                                      reinterpret_cast<unsigned char*>(c->arena), (arena / nt) & ~255L, nt, st)))
       return WFA_GPU_ECUDA;
     if (!k.ok(d2h(hc, dc, sizeof(wfa::Ctrl), st)) || !k.ok(cudaStreamSynchronize(st))) return WFA_GPU_ECUDA;
     std::swap(in, out);
@@ -489,7 +537,8 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
   if (n > 0 && (!patterns || !pattern_lengths || !texts || !text_lengths || !out_scores || !out_status))
     return WFA_GPU_EINVAL;
   if (!score_only && !out_cigar_offsets) return WFA_GPU_EINVAL;
-  if (!score_only && cap > 0 && !out_cigars) return WFA_GPU_EINVAL;
+  const bool sink = ctx->cig_sink && !dev && !score_only;
+  if (!score_only && cap > 0 && !out_cigars && !sink) return WFA_GPU_EINVAL;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return WFA_GPU_ECUDA;
   std::memset(&ctx->last, 0, sizeof ctx->last);
   ctx->last_variant = -1;
@@ -520,12 +569,34 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
   k.rec(1);
 
   cudaError_t e;
+  // host-pointer outputs: page-locked, mapped ones are written by the kernels
+  // in place; others come back through device and page-locked staging
   int32_t* d_score = out_scores;
   int8_t* d_status = out_status;
+  int32_t* m_score = nullptr;
+  int8_t* m_status = nullptr;
+  int64_t* m_off = nullptr;
+  uint32_t* m_cig = nullptr;
   if (!dev) {
-    if ((e = ctx->score.ensure(n)) || (e = ctx->status.ensure(n))) return map_alloc(e);
-    d_score = ctx->score.p;
-    d_status = ctx->status.p;
+    m_score = static_cast<int32_t*>(const_cast<void*>(mapped_range(out_scores, n * sizeof(int32_t))));
+    m_status = static_cast<int8_t*>(const_cast<void*>(mapped_range(out_status, n * sizeof(int8_t))));
+    if (!score_only) {
+      m_off = static_cast<int64_t*>(const_cast<void*>(mapped_range(out_cigar_offsets, (n + 1) * sizeof(int64_t))));
+      if (cap > 0 && !sink)
+        m_cig = static_cast<uint32_t*>(const_cast<void*>(mapped_range(out_cigars, cap * sizeof(uint32_t))));
+    }
+    if (m_score) {
+      d_score = m_score;
+    } else {
+      if ((e = ctx->score.ensure(n))) return map_alloc(e);
+      d_score = ctx->score.p;
+    }
+    if (m_status) {
+      d_status = m_status;
+    } else {
+      if ((e = ctx->status.ensure(n))) return map_alloc(e);
+      d_status = ctx->status.p;
+    }
   }
   const int64_t slot_words = score_only ? 1 : n * (int64_t)wfa::kSlot;
   if ((e = ctx->nruns.ensure(n)) || (e = ctx->run_src.ensure(n)) || (e = ctx->defer.ensure(n)) ||
@@ -573,25 +644,39 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
   if (ctx->last.deferred_pairs > 0) {
     rc = run_arena(ctx, k, a);
     if (rc) return rc;
-  }  if (ctx->h_ctrl->internal_error) return WFA_GPU_ECUDA;
+  }
+  if (ctx->h_ctrl->internal_error) return WFA_GPU_ECUDA;
   k.rec(3);
 
   int64_t total = 0;
   if (!score_only) {
     int64_t* d_off = out_cigar_offsets;
     if (!dev) {
-      if ((e = ctx->cig_off.ensure(n + 1))) return map_alloc(e);
-      d_off = ctx->cig_off.p;
+      if (m_off) {
+        d_off = m_off;
+      } else {
+        if ((e = ctx->cig_off.ensure(n + 1))) return map_alloc(e);
+        d_off = ctx->cig_off.p;
+      }
     }
     if (!k.launched(wfa::launch_scan(ctx->nruns.p, n, 0, d_off, ctx->scan_tmp.p, st), 3)) return fail_cuda(k);
     if (!k.ok(d2h(ctx->h_total, d_off + n, sizeof(int64_t), st)) || !k.ok(cudaStreamSynchronize(st)))
       return fail_cuda(k);
     total = *ctx->h_total;
+    if (total <= cap && total > 0 && sink) {
+      out_cigars = ctx->cig_sink(ctx->cig_sink_user, total);
+      if (!out_cigars) return WFA_GPU_ENOMEM;
+      m_cig = static_cast<uint32_t*>(const_cast<void*>(mapped_range(out_cigars, total * sizeof(uint32_t))));
+    }
     if (total <= cap && total > 0) {
       uint32_t* d_cig = out_cigars;
       if (!dev) {
-        if ((e = ctx->cig.ensure(total))) return map_alloc(e);
-        d_cig = ctx->cig.p;
+        if (m_cig) {
+          d_cig = m_cig;
+        } else {
+          if ((e = ctx->cig.ensure(total))) return map_alloc(e);
+          d_cig = ctx->cig.p;
+        }
       }
       if (!k.launched(
               wfa::launch_compact(n, ctx->nruns.p, ctx->run_src.p, ctx->runs.p, ctx->pool.p, d_off, d_cig, cap,
@@ -600,17 +685,24 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
     }
   }
   k.rec(4);
-  if (!dev) {
-    if (!k.ok(d2h(out_scores, d_score, n * sizeof(int32_t), st)) ||
-        !k.ok(d2h(out_status, d_status, n * sizeof(int8_t), st)))
-      return fail_cuda(k);
-    if (!score_only) {
-      if (!k.ok(d2h(out_cigar_offsets, ctx->cig_off.p, (n + 1) * sizeof(int64_t), st))) return fail_cuda(k);
-      if (total <= cap && !k.ok(d2h(out_cigars, ctx->cig.p, total * sizeof(uint32_t), st))) return fail_cuda(k);
-    }
-  }
+  // pageable host outputs: device staging -> page-locked staging (fast DMA,
+  // no shared driver bounce buffer) -> host copy after the sync
+  const bool c_score = !dev && !m_score, c_status = !dev && !m_status;
+  const bool c_off = !dev && !score_only && !m_off, c_cig = !dev && !score_only && !m_cig && total <= cap && total > 0;
+  if ((c_score && (e = ctx->h_score.ensure(n))) || (c_status && (e = ctx->h_status.ensure(n))) ||
+      (c_off && (e = ctx->h_off.ensure(n + 1))) || (c_cig && (e = ctx->h_cig.ensure(total))))
+    return map_alloc(e);
+  if ((c_score && !k.ok(d2h(ctx->h_score.p, d_score, n * sizeof(int32_t), st))) ||
+      (c_status && !k.ok(d2h(ctx->h_status.p, d_status, n * sizeof(int8_t), st))) ||
+      (c_off && !k.ok(d2h(ctx->h_off.p, ctx->cig_off.p, (n + 1) * sizeof(int64_t), st))) ||
+      (c_cig && !k.ok(d2h(ctx->h_cig.p, ctx->cig.p, total * sizeof(uint32_t), st))))
+    return fail_cuda(k);
   k.rec(5);
   if (!k.ok(cudaStreamSynchronize(st))) return fail_cuda(k);
+  if (c_score) std::memcpy(out_scores, ctx->h_score.p, n * sizeof(int32_t));
+  if (c_status) std::memcpy(out_status, ctx->h_status.p, n * sizeof(int8_t));
+  if (c_off) std::memcpy(out_cigar_offsets, ctx->h_off.p, (n + 1) * sizeof(int64_t));
+  if (c_cig) std::memcpy(out_cigars, ctx->h_cig.p, total * sizeof(uint32_t));
   ctx->last.kernel_launches = k.launches;
   ctx->last.short_variant = ctx->last_variant;
   if (k.timing) {
@@ -957,6 +1049,7 @@ void wfa_gpu_destroy(wfa_gpu_ctx* c) {
   c->cig_off.release(); c->cig.release(); c->nruns.release(); c->defer.release();
   c->overflow.release(); c->run_src.release(); c->scan_tmp.release(); c->runs.release();
   c->defer_long.release(); c->pool.release();
+  c->h_score.release(); c->h_status.release(); c->h_off.release(); c->h_cig.release();
   if (c->arena) cudaFree(c->arena);
   if (c->ctrl) cudaFree(c->ctrl);
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);

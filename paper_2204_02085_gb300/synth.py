@@ -227,9 +227,9 @@ def long_reads(n_pairs: int, length: int = 10_000, rate_lo: float = 0.01, rate_h
 
 
 def mixed_reads(n_pairs: int, len_lo: int = 100, len_hi: int = 2000, rate_hi: float = 0.10,
-                repeat_frac: float = 0.05, seed: int = 3) -> Batch:
+                repeat_frac: float = 0.05, seed: int = 3, rate_lo: float = 0.0) -> Batch:
     """Pairs of uneven length and divergence: text length log-uniform in
-    [len_lo, len_hi], edit rate r ~ U[0, rate_hi]; a fraction repeat_frac of
+    [len_lo, len_hi], edit rate r ~ U[rate_lo, rate_hi]; a fraction repeat_frac of
     the texts carry a tandem repeat (a uniform 50-mer repeated u ~ U{2..6}
     times, written over a uniform window of the text, clipped at its end)
     before the one-pass edits.  Per pair the draws are: length, text, the
@@ -246,7 +246,7 @@ def mixed_reads(n_pairs: int, len_lo: int = 100, len_hi: int = 2000, rate_hi: fl
             start = int(rng.integers(0, L))
             span = min(len(rep), L - start)
             t[start:start + span] = rep[:span]
-        k = int(round(rng.uniform(0.0, rate_hi) * L))
+        k = int(round(rng.uniform(rate_lo, rate_hi) * L))
         texts.append(t)
         pats.append(_edit_one_pass(rng, t, k))
     return _pairs_from_codes(texts, pats)

@@ -119,3 +119,38 @@ def test_product_never_imports_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "wfa_oracle" not in text, f
+
+
+def test_request_bytes_is_host_only(pkg):
+    """The admission measure of the serving API: sequence bytes plus a fixed
+    per-pair share and the caller's CIGAR capacity; no device needed."""
+    import numpy as np
+
+    plen = np.array([100, 0, 250], np.int32)
+    tlen = np.array([90, 10, 300], np.int32)
+    req = pkg.Request(3, None, None, plen.ctypes.data, None, None, tlen.ctypes.data, pkg.Penalties(4, 6, 2), 0, 0,
+                      None, None, None, 1000, None)
+    assert pkg.wfa_gpu_request_bytes(req) == int(plen.sum() + tlen.sum()) + 150 * 3 + 4 * 1000
+    bad = pkg.Request(-1, None, None, None, None, None, None, pkg.Penalties(4, 6, 2), 0, 0, None, None, None, 0, None)
+    assert pkg.wfa_gpu_request_bytes(bad) == -1
+    assert pkg.load().wfa_gpu_server_create(None, 0, 4, 0) == pkg.WFA_GPU_EINVAL
+    pkg.wfa_gpu_server_destroy(None)
+
+
+def test_header_constants_match_binding():
+    """Every integer #define and enum value of the header that the binding
+    mirrors has the same value there."""
+    import paper_2204_02085_gb300 as p
+
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    seen = 0
+    for name, expr in re.findall(r"#define\s+(WFA_GPU_[A-Z0-9_]+)\s+(.+)", text):
+        if hasattr(p, name) and re.fullmatch(r"[()0-9<>\s\-+]*", expr.replace("(size_t)", "")):
+            assert getattr(p, name) == eval(expr.replace("(size_t)", "")), name
+            seen += 1
+    for name, val in re.findall(r"\b(WFA_(?:GPU|PAIR)_[A-Z0-9_]+)\s*=\s*(-?\d+)", text):
+        if hasattr(p, name):
+            assert getattr(p, name) == int(val), name
+            seen += 1
+    assert seen >= 10
+    assert p.WFA_GPU_SERVER_MERGE_PAIRS == 65536 and p.WFA_GPU_MAX_SEQ_LEN == (1 << 28) - 1
