@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--pairs", type=int, default=N_PAIRS, help="pairs per batch (default: the paper's 5M)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=400_000, help="pairs per edit rate for the CPU baseline")
+    ap.add_argument("--cpu-sample", type=int, default=N_PAIRS, help="pairs per edit rate for the CPU baseline")
     ap.add_argument("--edits", default="2,4", help="edit counts of the batches (default: the paper's 2%% and 4%%)")
     ap.add_argument("--short-variant", type=int, default=None,
                     help="force one short-read kernel variant (tuning; default: the library's autotuner)")
@@ -159,14 +159,15 @@ def make_batches(n_pairs: int, rank: int, edits=EDITS):
     return [synth.uniform_reads(n_pairs, LENGTH, e, seed=sharding.shard_seed(SEED, rank)) for e in edits]
 
 
-def cpu_oracle_run(batches, sample: int):
+def cpu_oracle_run(batches, sample: int, threads: int | None = None):
     """The oracle (plain CPU WFA, score + CIGAR) on the first `sample` pairs
-    of each batch, all host cores.  Returns (pairs, seconds, threads, counts)."""
+    of each batch, all host cores (or `threads`).  Returns (pairs, seconds,
+    threads, counts)."""
     import oracle
     from paper_2204_02085_gb300 import synth
 
     oracle.build()
-    threads = host_cores()
+    threads = threads or host_cores()
     pairs = 0
     cnt = oracle.Counts()
     t0 = time.perf_counter()
@@ -589,9 +590,13 @@ def main():
     cnt = None
     if not args.no_cpu_baseline:
         cp, cdt, cthreads, cnt = cpu_oracle_run(batches, min(args.cpu_sample, args.pairs))
+        one = min(100_000, args.pairs)
+        cp1, cdt1, _, _ = cpu_oracle_run(batches, one, threads=1)
         cpu = {"value": cp / cdt, "unit": "pairs/s", "cores": cthreads, "kind": "oracle",
                "sample": "first %d pairs of each of the two 5M-pair batches (E=2%%, E=4%%), score+CIGAR, "
-                         "%d threads, %.1f s wall" % (min(args.cpu_sample, args.pairs), cthreads, cdt)}
+                         "%d threads, %.1f s wall" % (min(args.cpu_sample, args.pairs), cthreads, cdt),
+               "single_thread": {"value": cp1 / cdt1, "unit": "pairs/s",
+                                 "sample": "first %d pairs of each batch, 1 thread, %.1f s" % (one, cdt1)}}
 
     # algorithmic bytes per pair: 2L ASCII in, lengths in, score + status +
     # CIGAR offset + 4 bytes per CIGAR run out

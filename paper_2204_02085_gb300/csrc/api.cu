@@ -127,10 +127,8 @@ struct wfa_gpu_ctx {
   DevBuf<int8_t> status;
   DevBuf<int64_t> cig_off;
   DevBuf<uint32_t> cig;
-  HostBuf<int32_t> h_score;
-  HostBuf<int8_t> h_status;
-  HostBuf<int64_t> h_off;
-  HostBuf<uint32_t> h_cig;
+  // page-locked staging of pageable host outputs (bytes)
+  HostBuf<unsigned char> h_score, h_status, h_off, h_cig;
   // internal
   DevBuf<int32_t> nruns, defer, defer_long, overflow;
   DevBuf<int64_t> run_src, scan_tmp;
@@ -569,34 +567,15 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
   k.rec(1);
 
   cudaError_t e;
-  // host-pointer outputs: page-locked, mapped ones are written by the kernels
-  // in place; others come back through device and page-locked staging
+  // host-pointer outputs come back through device buffers and one bulk copy
+  // each (kernel stores straight into mapped host memory cross the C2C link
+  // in small pieces and measured several times slower)
   int32_t* d_score = out_scores;
   int8_t* d_status = out_status;
-  int32_t* m_score = nullptr;
-  int8_t* m_status = nullptr;
-  int64_t* m_off = nullptr;
-  uint32_t* m_cig = nullptr;
   if (!dev) {
-    m_score = static_cast<int32_t*>(const_cast<void*>(mapped_range(out_scores, n * sizeof(int32_t))));
-    m_status = static_cast<int8_t*>(const_cast<void*>(mapped_range(out_status, n * sizeof(int8_t))));
-    if (!score_only) {
-      m_off = static_cast<int64_t*>(const_cast<void*>(mapped_range(out_cigar_offsets, (n + 1) * sizeof(int64_t))));
-      if (cap > 0 && !sink)
-        m_cig = static_cast<uint32_t*>(const_cast<void*>(mapped_range(out_cigars, cap * sizeof(uint32_t))));
-    }
-    if (m_score) {
-      d_score = m_score;
-    } else {
-      if ((e = ctx->score.ensure(n))) return map_alloc(e);
-      d_score = ctx->score.p;
-    }
-    if (m_status) {
-      d_status = m_status;
-    } else {
-      if ((e = ctx->status.ensure(n))) return map_alloc(e);
-      d_status = ctx->status.p;
-    }
+    if ((e = ctx->score.ensure(n)) || (e = ctx->status.ensure(n))) return map_alloc(e);
+    d_score = ctx->score.p;
+    d_status = ctx->status.p;
   }
   const int64_t slot_words = score_only ? 1 : n * (int64_t)wfa::kSlot;
   if ((e = ctx->nruns.ensure(n)) || (e = ctx->run_src.ensure(n)) || (e = ctx->defer.ensure(n)) ||
@@ -649,15 +628,12 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
   k.rec(3);
 
   int64_t total = 0;
+  int64_t* d_off = out_cigar_offsets;
+  uint32_t* d_cig = out_cigars;
   if (!score_only) {
-    int64_t* d_off = out_cigar_offsets;
     if (!dev) {
-      if (m_off) {
-        d_off = m_off;
-      } else {
-        if ((e = ctx->cig_off.ensure(n + 1))) return map_alloc(e);
-        d_off = ctx->cig_off.p;
-      }
+      if ((e = ctx->cig_off.ensure(n + 1))) return map_alloc(e);
+      d_off = ctx->cig_off.p;
     }
     if (!k.launched(wfa::launch_scan(ctx->nruns.p, n, 0, d_off, ctx->scan_tmp.p, st), 3)) return fail_cuda(k);
     if (!k.ok(d2h(ctx->h_total, d_off + n, sizeof(int64_t), st)) || !k.ok(cudaStreamSynchronize(st)))
@@ -666,17 +642,11 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
     if (total <= cap && total > 0 && sink) {
       out_cigars = ctx->cig_sink(ctx->cig_sink_user, total);
       if (!out_cigars) return WFA_GPU_ENOMEM;
-      m_cig = static_cast<uint32_t*>(const_cast<void*>(mapped_range(out_cigars, total * sizeof(uint32_t))));
     }
     if (total <= cap && total > 0) {
-      uint32_t* d_cig = out_cigars;
       if (!dev) {
-        if (m_cig) {
-          d_cig = m_cig;
-        } else {
-          if ((e = ctx->cig.ensure(total))) return map_alloc(e);
-          d_cig = ctx->cig.p;
-        }
+        if ((e = ctx->cig.ensure(total))) return map_alloc(e);
+        d_cig = ctx->cig.p;
       }
       if (!k.launched(
               wfa::launch_compact(n, ctx->nruns.p, ctx->run_src.p, ctx->runs.p, ctx->pool.p, d_off, d_cig, cap,
@@ -685,24 +655,35 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
     }
   }
   k.rec(4);
-  // pageable host outputs: device staging -> page-locked staging (fast DMA,
-  // no shared driver bounce buffer) -> host copy after the sync
-  const bool c_score = !dev && !m_score, c_status = !dev && !m_status;
-  const bool c_off = !dev && !score_only && !m_off, c_cig = !dev && !score_only && !m_cig && total <= cap && total > 0;
-  if ((c_score && (e = ctx->h_score.ensure(n))) || (c_status && (e = ctx->h_status.ensure(n))) ||
-      (c_off && (e = ctx->h_off.ensure(n + 1))) || (c_cig && (e = ctx->h_cig.ensure(total))))
-    return map_alloc(e);
-  if ((c_score && !k.ok(d2h(ctx->h_score.p, d_score, n * sizeof(int32_t), st))) ||
-      (c_status && !k.ok(d2h(ctx->h_status.p, d_status, n * sizeof(int8_t), st))) ||
-      (c_off && !k.ok(d2h(ctx->h_off.p, ctx->cig_off.p, (n + 1) * sizeof(int64_t), st))) ||
-      (c_cig && !k.ok(d2h(ctx->h_cig.p, ctx->cig.p, total * sizeof(uint32_t), st))))
-    return fail_cuda(k);
+  // host outputs: one copy each, straight into a page-locked destination,
+  // else into page-locked staging (fast DMA, no shared driver bounce buffer)
+  // and a host copy after the sync
+  struct Back {
+    void* dst;
+    const void* src;
+    size_t bytes;
+    HostBuf<unsigned char>* stage;
+    bool later;
+  };
+  Back back[4] = {{out_scores, d_score, (size_t)n * sizeof(int32_t), &ctx->h_score, false},
+                  {out_status, d_status, (size_t)n * sizeof(int8_t), &ctx->h_status, false},
+                  {out_cigar_offsets, d_off, (size_t)(n + 1) * sizeof(int64_t), &ctx->h_off, false},
+                  {out_cigars, d_cig, (size_t)total * sizeof(uint32_t), &ctx->h_cig, false}};
+  const int nback = dev ? 0 : score_only ? 2 : (total <= cap && total > 0) ? 4 : 3;
+  for (int j = 0; j < nback; ++j) {
+    Back& b = back[j];
+    void* to = b.dst;
+    if (!mapped_range(b.dst, b.bytes)) {
+      if ((e = b.stage->ensure(b.bytes))) return map_alloc(e);
+      to = b.stage->p;
+      b.later = true;
+    }
+    if (!k.ok(d2h(to, b.src, b.bytes, st))) return fail_cuda(k);
+  }
   k.rec(5);
   if (!k.ok(cudaStreamSynchronize(st))) return fail_cuda(k);
-  if (c_score) std::memcpy(out_scores, ctx->h_score.p, n * sizeof(int32_t));
-  if (c_status) std::memcpy(out_status, ctx->h_status.p, n * sizeof(int8_t));
-  if (c_off) std::memcpy(out_cigar_offsets, ctx->h_off.p, (n + 1) * sizeof(int64_t));
-  if (c_cig) std::memcpy(out_cigars, ctx->h_cig.p, total * sizeof(uint32_t));
+  for (int j = 0; j < nback; ++j)
+    if (back[j].later) std::memcpy(back[j].dst, back[j].stage->p, back[j].bytes);
   ctx->last.kernel_launches = k.launches;
   ctx->last.short_variant = ctx->last_variant;
   if (k.timing) {
