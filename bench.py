@@ -51,6 +51,24 @@ N_SM = 152
 OPS_PER_CELL = 32
 OPS_PER_EXTRA_WINDOW = 18
 OPS_PER_BT_STEP = 12
+# DRAM traffic of the short kernel (dram__bytes_read.sum + dram__bytes_write.sum
+# from ncu on 1M-pair launches of the same workload, per pair; the traffic of
+# a launch grows in proportion to its pairs), valid for the device sources
+# whose digest is "sha" (kernel_sources_digest); any change to them voids it
+NCU_TRAFFIC = {"sha": "4dd1db24c1fdc816", "bytes_per_pair": {2: 288.41, 4: 297.57},
+               "summary": "profiles/short_kernel_1Mx100bp_E2_E4_ncu_full.md"}
+KERNEL_SOURCES = ("wfa_device.cuh", "short_path.cuh", "arena_path.cuh", "kernels.cu", "launch.h")
+
+
+def kernel_sources_digest() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2204_02085_gb300", "csrc", f),
+                  "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -636,6 +654,9 @@ def main():
     roof["bytes_per_pair"] = bpp
     roof["avg_launch_ms"] = align_ms
     roof["traffic"] = None
+    if kernel_sources_digest() == NCU_TRAFFIC["sha"] and all(e in NCU_TRAFFIC["bytes_per_pair"] for e in args.edits):
+        roof["traffic"] = float(np.mean([NCU_TRAFFIC["bytes_per_pair"][e] * b.n for e, b in zip(args.edits, batches)]))
+        roof["traffic_source"] = "ncu dram bytes of 1M-pair launches scaled to the launch (%s)" % NCU_TRAFFIC["summary"]
 
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
