@@ -233,7 +233,7 @@ const void* mapped_range(const void* p, size_t bytes) {
 int stage_inputs(wfa_gpu_ctx* c, Call& k, int64_t n, bool dev, const char* pat, const int64_t* poff,
                  const int32_t* plen, const char* txt, const int64_t* toff, const int32_t* tlen,
                  const char** d_pat, const int64_t** d_poff, const int32_t** d_plen, const char** d_txt,
-                 const int64_t** d_toff, const int32_t** d_tlen) {
+                 const int64_t** d_toff, const int32_t** d_tlen, bool* host_seqs = nullptr) {
   cudaStream_t st = c->stream;
   cudaError_t e;
   if (dev) {
@@ -299,6 +299,7 @@ int stage_inputs(wfa_gpu_ctx* c, Call& k, int64_t n, bool dev, const char* pat, 
     const size_t pe = (size_t)c->h_ctrl->pat_extent, te = (size_t)c->h_ctrl->txt_extent;
     const void* mp = mapped_range(pat, pe);
     const void* mt = mapped_range(txt, te);
+    if (host_seqs) *host_seqs = mp || mt;
     if (mp || pe == 0) {
       *d_pat = mp ? static_cast<const char*>(mp) : pat;
     } else {
@@ -561,8 +562,9 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
   const char *d_pat, *d_txt;
   const int64_t *d_poff, *d_toff;
   const int32_t *d_plen, *d_tlen;
+  bool host_seqs = false;
   int rc = stage_inputs(ctx, k, n, dev, patterns, pattern_offsets, pattern_lengths, texts, text_offsets,
-                        text_lengths, &d_pat, &d_poff, &d_plen, &d_txt, &d_toff, &d_tlen);
+                        text_lengths, &d_pat, &d_poff, &d_plen, &d_txt, &d_toff, &d_tlen, &host_seqs);
   if (rc) return rc;
   k.rec(1);
 
@@ -593,6 +595,7 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
   a.oes = (pen.o + pen.e) / g;
   a.s_cap = max_score > 0 ? max_score / g : INT_MAX;
   a.score_only = score_only ? 1 : 0;
+  a.host_seqs = host_seqs ? 1 : 0;
   a.score = d_score;
   a.status = d_status;
   a.nruns = ctx->nruns.p;

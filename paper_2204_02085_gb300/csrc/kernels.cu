@@ -23,7 +23,7 @@ namespace {
 // ------------------------------------------------------------ short kernel
 
 template <int G, int LMAX, int CELLS, int SCAP, typename Off>
-__global__ void __launch_bounds__(kShortBlock) short_kernel(const AlignArgs a) {
+__global__ void __launch_bounds__(kShortBlock, 8) short_kernel(const AlignArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_last;
   short_body<G, LMAX, CELLS, SCAP, Off>(a, smem, &s_last);

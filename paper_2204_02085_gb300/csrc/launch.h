@@ -40,6 +40,7 @@ struct AlignArgs {
   int g;            // gcd(x, o, e)
   int s_cap;        // largest scaled score reported (INT_MAX: none)
   int score_only;
+  int host_seqs;  // sequences read in place from page-locked host memory
   int32_t* score;
   int8_t* status;
   int32_t* nruns;

@@ -47,15 +47,62 @@ struct ShortCfg {
     Off M[CELLS * P];
     Off I[CELLS * P];
     Off D[CELLS * P];
+    int16_t nl[P], ml[P];  // pair lengths, readable by every lane
+    uint8_t act[P];        // slots of the pairs still running, ascending
   };
-  // the packer's span scratch (codes + bad-byte masks of up to P
-  // back-to-back sequences) borrows the cell arrays, unused while packing
-  static constexpr int SPAN = (P * LMAX + 15) / 16 + 1;
-  static_assert((SPAN + 1) * (sizeof(uint32_t) + sizeof(uint16_t)) <= 3 * CELLS * P * sizeof(Off),
-                "packer scratch does not fit the cell arrays");
+  // the packer's span scratch (the raw bytes of up to P back-to-back
+  // sequences, 16-byte chunks) borrows the cell arrays, unused while
+  // packing; longer spans take the packer's per-slot path
+  static constexpr int kSpanAll = (P * LMAX + 15) / 16 + 1;
+  static constexpr int kSpanFit = (int)(3 * CELLS * P * sizeof(Off) / 16);
+  static constexpr int SPAN = kSpanAll < kSpanFit ? kSpanAll : kSpanFit;
+  static_assert(16 * SPAN <= 3 * CELLS * P * sizeof(Off), "packer scratch does not fit the cell arrays");
   static constexpr size_t kTabBytes = ((SCAP + 1) * sizeof(UGeo) + 15) / 16 * 16;
   static constexpr size_t kWarpBytes = (sizeof(WarpShm) + 15) / 16 * 16;
   static constexpr size_t smem_bytes(int warps) { return kTabBytes + (size_t)warps * kWarpBytes; }
+};
+
+// One wavefront cell of the flattened score loop: item f of na running
+// pairs (pair index fastest) at the score whose geometry is g; load()
+// gathers its sources and applies the recurrences (the mismatch, insertion
+// and deletion candidates, each null past the sequence ends) giving the
+// offset h to extend, store() writes M, I and D.
+template <typename Off, int P>
+struct Cell {
+  int r, i, k, n, m, h, iv, dv;
+  __device__ __forceinline__ void load(const Off* M, const Off* I, const Off* D, const uint8_t* act,
+                                       const int16_t* nl, const int16_t* ml, const UGeo* tab, const UGeo& g,
+                                       const Geo& gx, const Geo& go, const Geo& ge, int f, int na,
+                                       unsigned inv_na) {
+    constexpr int NUL = NullOf<Off>::value;
+    i = na > 1 ? (int)__umulhi((unsigned)f, inv_na) : f;
+    r = act[f - i * na];
+    n = nl[r];
+    m = ml[r];
+    k = g.lo + i;
+    const UView<Off, P> v{tab, const_cast<Off*>(M), const_cast<Off*>(I), const_cast<Off*>(D), r};
+    const int mx = get_off<UView<Off, P>, 0>(v, gx, k, NUL);
+    const int mlo = get_off<UView<Off, P>, 0>(v, go, k - 1, NUL);
+    const int mro = get_off<UView<Off, P>, 0>(v, go, k + 1, NUL);
+    const int il = get_off<UView<Off, P>, 1>(v, ge, k - 1, NUL);
+    const int dr = get_off<UView<Off, P>, 2>(v, ge, k + 1, NUL);
+    // a null source stays negative through the +1 steps of the stored
+    // scores, so only the far end needs testing; negative = null
+    iv = max(mlo, il) + 1;
+    if (iv > m) iv = NUL;
+    dv = max(mro, dr);
+    if (dv - k > n) dv = NUL;
+    int xv = mx + 1;
+    if (xv > m || xv - k > n) xv = NUL;
+    h = __vimax3_s32(xv, iv, dv);
+  }
+  __device__ __forceinline__ void store(Off* M, Off* I, Off* D, const UGeo& g) const {
+    constexpr int NUL = NullOf<Off>::value;
+    const int c = (g.base + i) * P + r;
+    M[c] = (Off)(h >= 0 ? h : NUL);
+    I[c] = (Off)iv;
+    D[c] = (Off)dv;
+  }
 };
 
 // Fused short-read kernel: G lanes per pair, 32/G pairs per warp advancing
@@ -70,6 +117,7 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
   using C = ShortCfg<G, LMAX, CELLS, SCAP, Off>;
   constexpr int P = C::P;
   constexpr int NUL = NullOf<Off>::value;
+  static_assert(NUL + SCAP + 1 < 0, "a null offset must stay negative over the stored scores");
   constexpr unsigned FULL = 0xffffffffu;
   if (*(volatile int32_t*)&a.ctrl->bad_input) return;  // inputs rejected by the validation kernel
   int& s_last = *s_last_shared;
@@ -105,13 +153,17 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
       // all lanes take part: the warp reads its pairs' sequences together
       uint32_t* scratch = reinterpret_cast<uint32_t*>(W->M);
       const bool okp = pack_warp32<G, C::SPAN>(active ? a.pat + a.poff[pair] : nullptr, n, active, pw, PS, scratch,
-                                               lane, gmask);
+                                               lane, gmask, !a.host_seqs);
       const bool okt = pack_warp32<G, C::SPAN>(active ? a.txt + a.toff[pair] : nullptr, m, active, tw, PS, scratch,
-                                               lane, gmask);
+                                               lane, gmask, !a.host_seqs);
       if (active && !(okp && okt)) {
         if (lane == 0) write_result(a, pair, 2, -1, 0, 0);
         active = false;
       }
+    }
+    if (lane == 0) {
+      W->nl[q] = (int16_t)n;
+      W->ml[q] = (int16_t)m;
     }
     __syncwarp();
     const int kf = m - n;
@@ -122,35 +174,42 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
       s_fin = 0;
       active = false;
     }
-    for (int s = 1; s <= s_hi && __any_sync(FULL, active); ++s) {
+    // The running pairs share the warp's lanes: at each score the cells of
+    // all of them are spread over the 32 lanes, pair index fastest (cell
+    // (i, j) of the j-th running pair is item i * na + j), so a pair that has
+    // finished costs nothing while the others go on.
+    unsigned amask = __ballot_sync(FULL, active && lane == 0);
+    int na = __popc(amask);
+    unsigned inv_na = 0;  // ceil(2^32 / na): item / na by one __umulhi
+    auto relist = [&]() {
+      if (active && lane == 0) W->act[__popc(amask & ((1u << lane32) - 1u))] = (uint8_t)q;
+      inv_na = na > 1 ? 0xffffffffu / (unsigned)na + 1u : 0u;
+      __syncwarp();
+    };
+    relist();
+    for (int s = 1; s <= s_hi && na > 0; ++s) {
       const UGeo g = tab[s];
       if (!g.ex) continue;
-      if (active) {
-        const Geo gx = geo_of(view, s - pen.x, 1);
-        const Geo go = geo_of(view, s - pen.oe, 1);
-        const Geo ge = geo_of(view, s - pen.e, 2);
-        for (int i = lane; i < g.w; i += G) {
-          const int k = g.lo + i;
-          const int mx = get_off<UView<Off, P>, 0>(view, gx, k, NUL);
-          const int ml = get_off<UView<Off, P>, 0>(view, go, k - 1, NUL);
-          const int mr = get_off<UView<Off, P>, 0>(view, go, k + 1, NUL);
-          const int il = get_off<UView<Off, P>, 1>(view, ge, k - 1, NUL);
-          const int dr = get_off<UView<Off, P>, 2>(view, ge, k + 1, NUL);
-          int iv = max(ml, il) + 1;
-          if (iv < 0 || iv > m) iv = NUL;
-          int dv = max(mr, dr);
-          if (dv < 0 || dv - k > n) dv = NUL;
-          int xv = mx + 1;
-          if (mx < 0 || xv > m || xv - k > n) xv = NUL;
-          int mv = max(xv, max(iv, dv));
-          mv = mv >= 0 ? extend_diag32(pw, tw, n, m, k, mv, PS) : NUL;
-          view.put(g.base, i, mv, iv, dv);
-        }
+      const Geo gx = geo_of(view, s - pen.x, 1);
+      const Geo go = geo_of(view, s - pen.oe, 1);
+      const Geo ge = geo_of(view, s - pen.e, 2);
+      const int items = na * g.w;
+      for (int f = lane32; f < items; f += 32) {
+        Cell<Off, P> c;
+        c.load(W->M, W->I, W->D, W->act, W->nl, W->ml, tab, g, gx, go, ge, f, na, inv_na);
+        if (c.h >= 0) c.h = extend_diag32(W->pw + c.r, W->tw + c.r, c.n, c.m, c.k, c.h, PS);
+        c.store(W->M, W->I, W->D, g);
       }
       __syncwarp();
       if (active && kf >= g.lo && kf < g.lo + g.w && view.getM(Geo{g.lo, g.w, g.base}, kf - g.lo) == m) {
         s_fin = s;
         active = false;
+      }
+      const unsigned now = __ballot_sync(FULL, active && lane == 0);
+      if (now != amask) {
+        amask = now;
+        na = __popc(amask);
+        relist();
       }
     }
     if (lane == 0) {

@@ -173,18 +173,29 @@ __device__ __forceinline__ uint32_t code16_bad(uint4 v, uint32_t* bad16) {
   return code;
 }
 
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte
+// aligned) and the wait for all of this thread's copies.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Warp-cooperative packing of one sequence per pair slot of a warp (P pair
 // slots of G lanes).  When the active slots' sequences lie in one span of at
-// most 16 * SPAN_CHUNKS bytes, the warp reads the span once with coalesced
-// 16-byte loads into shared scratch (codes + bad-byte masks) and every slot
-// cuts its 32-bit words (16 bases, first base in the top bits) from it;
-// otherwise every slot reads its own chunks.  Slot q writes words
-// 0 .. ceil(len/16) (the last one zero) to out[j * stride].  scratch holds
-// SPAN_CHUNKS + 1 uint32 codes then SPAN_CHUNKS + 1 uint16 masks.  Returns, per
-// slot, whether every byte of its sequence is A/C/G/T.  All 32 lanes call it.
+// most 16 * SPAN_CHUNKS bytes (aligned 16-byte chunks), the warp copies the
+// span once into shared scratch and converts it there to (2-bit codes,
+// bad-byte mask) per chunk, and every slot cuts its 32-bit words (16 bases,
+// first base in the top bits) from that; otherwise every slot reads its own
+// chunks.  Slot q writes words 0 .. ceil(len/16) (the last one zero) to
+// out[j * stride].  scratch: 16 * SPAN_CHUNKS bytes, 16-byte aligned.
+// async_copy: stage the span with asynchronous copies (device memory) rather
+// than plain loads (host memory read over the link).
+// Returns, per slot, whether every byte of its sequence is A/C/G/T.  All 32
+// lanes call it.
 template <int G, int SPAN_CHUNKS>
 __device__ __forceinline__ bool pack_warp32(const char* seq, int len, bool active, uint32_t* out, int stride,
-                                            uint32_t* scratch, int lane, unsigned gmask) {
+                                            uint32_t* scratch, int lane, unsigned gmask, bool async_copy) {
   constexpr unsigned FULL = 0xffffffffu;
   const int lane32 = threadIdx.x & 31;
   const unsigned long long a = reinterpret_cast<uintptr_t>(seq);
@@ -201,16 +212,39 @@ __device__ __forceinline__ bool pack_warp32(const char* seq, int len, bool activ
   if (hi > lo && hi - (lo & ~15ull) <= 16ull * SPAN_CHUNKS) {
     const unsigned long long base = lo & ~15ull;
     const int nch = (int)((hi - base + 15) >> 4);
-    uint16_t* masks = reinterpret_cast<uint16_t*>(scratch + SPAN_CHUNKS + 1);
-    for (int c = lane32; c < nch; c += 32) {
-      uint32_t b16;
-      scratch[c] = code16_bad(__ldg(reinterpret_cast<const uint4*>(base + 16ull * c)), &b16);
-      masks[c] = (uint16_t)b16;
+    uint2* ent = reinterpret_cast<uint2*>(scratch);  // (2-bit codes, bad-byte mask) per chunk
+    if (async_copy) {
+      // device memory: every chunk of the span is copied to shared memory
+      // asynchronously (all loads in flight at once), then converted in
+      // place, 32 chunks a round: a round writes its 8-byte entries below
+      // the raw bytes of the rounds still to come
+      for (int c = lane32; c < nch; c += 32)
+        cp_async16(scratch + 4 * c, reinterpret_cast<const void*>(base + 16ull * c));
+      cp_async_wait_all();
+      __syncwarp();
+      const uint4* raw = reinterpret_cast<const uint4*>(scratch);
+      for (int c0 = 0; c0 < nch; c0 += 32) {
+        const int c = c0 + lane32;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (c < nch) v = raw[c];
+        __syncwarp();
+        if (c < nch) {
+          uint32_t b16;
+          const uint32_t code = code16_bad(v, &b16);
+          ent[c] = make_uint2(code, b16);
+        }
+      }
+    } else {
+      // page-locked host memory read in place: plain coalesced loads (the
+      // asynchronous copies measured slower over the host link)
+      for (int c = lane32; c < nch; c += 32) {
+        uint32_t b16;
+        const uint32_t code = code16_bad(__ldg(reinterpret_cast<const uint4*>(base + 16ull * c)), &b16);
+        ent[c] = make_uint2(code, b16);
+      }
     }
-    if (lane32 == 0) {
-      scratch[nch] = 0u;
-      masks[nch] = 0;
-    }
+    __syncwarp();
+    if (lane32 == 0) ent[nch] = make_uint2(0u, 0u);
     __syncwarp();
     if (active) {
       const int off = (int)(a - base);  // bytes from the span start
@@ -218,11 +252,12 @@ __device__ __forceinline__ bool pack_warp32(const char* seq, int len, bool activ
       for (int j = lane; j <= nw; j += G) {
         uint32_t word = 0u;
         if (j < nw) {
-          word = __funnelshift_l(scratch[c0 + j + 1], scratch[c0 + j], r);
+          const uint2 e0 = ent[c0 + j], e1 = ent[c0 + j + 1];
+          word = __funnelshift_l(e1.x, e0.x, r);
           const int rem = len - 16 * j;
           if (rem < 16) word &= ~0u << (32 - 2 * rem);
           // bad bytes among this word's 16 (at most 2 chunks)
-          const uint32_t m2 = (uint32_t)masks[c0 + j] | ((uint32_t)masks[c0 + j + 1] << 16);
+          const uint32_t m2 = e0.y | (e1.y << 16);
           const int nb = min(16, rem);
           const uint32_t in = (nb >= 16 ? 0xFFFFu : ((1u << nb) - 1u)) << (off & 15);
           if (m2 & in) bad = true;
