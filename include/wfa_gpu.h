@@ -305,6 +305,13 @@ int64_t wfa_gpu_request_bytes(const wfa_gpu_request *req);
  * ECUDA) and release the server.  NULL-safe. */
 void wfa_gpu_server_destroy(wfa_gpu_server *server);
 
+/* Name of short-kernel variant `index` of the context (the index that
+ * wfa_gpu_timing.short_variant reports), e.g. "g2_l127_c208_i8" (2 lanes
+ * per pair, sequences up to 127 bases, 208 stored cells per pair, int8
+ * offsets) or "..._lin" (gap-linear model, M only); NULL if there is no
+ * such variant.  The string is static.  Host-only. */
+const char *wfa_gpu_short_variant_name(const wfa_gpu_ctx *ctx, int index);
+
 /* Upper bound on the CIGAR words of one pair of lengths plen, tlen under pen
  * and max_score (<= 0: unbounded): with s the largest score the pair can
  * report, at most 2*floor(s / min(x, o+e)) + 1 runs, and never more than

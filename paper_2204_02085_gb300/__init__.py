@@ -46,6 +46,7 @@ EXPORTS = (
     "wfa_gpu_server_wait",
     "wfa_gpu_request_bytes",
     "wfa_gpu_server_destroy",
+    "wfa_gpu_short_variant_name",
 )
 WFA_GPU_NOALLOC_SCRATCH_BYTES = 4 << 20
 WFA_GPU_NOALLOC_MAX_PAIRS = 32768
@@ -138,6 +139,8 @@ def load(path: str = LIB_PATH):
     L.wfa_gpu_strerror.restype = ctypes.c_char_p
     L.wfa_gpu_destroy.argtypes = [vp]
     L.wfa_gpu_destroy.restype = None
+    L.wfa_gpu_short_variant_name.argtypes = [vp, ctypes.c_int]
+    L.wfa_gpu_short_variant_name.restype = ctypes.c_char_p
     L.wfa_gpu_align_short_noalloc.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, Penalties, i32, vp, vp, vp, i64, vp]
     L.wfa_gpu_align_short_noalloc.restype = ctypes.c_int
     L.wfa_gpu_server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_size_t]
@@ -189,6 +192,11 @@ def wfa_gpu_cigar_bound(plen: int, tlen: int, pen, max_score: int = 0) -> int:
     if not isinstance(pen, Penalties):
         pen = Penalties(*pen)
     return load().wfa_gpu_cigar_bound(plen, tlen, pen, max_score)
+
+
+def wfa_gpu_short_variant_name(ctx, index: int) -> str | None:
+    r = load().wfa_gpu_short_variant_name(ctx, index)
+    return None if r is None else r.decode()
 
 
 def wfa_gpu_last_timing(ctx) -> Timing:
@@ -274,6 +282,10 @@ class Aligner:
 
     def timing(self) -> dict:
         return wfa_gpu_last_timing(self.ctx).as_dict()
+
+    def variant_name(self, index: int) -> str | None:
+        """Name of short-kernel variant `index` (as timing()["short_variant"])."""
+        return wfa_gpu_short_variant_name(self.ctx, index)
 
     def align(self, batch, pen=(4, 6, 2), max_score: int = 0, score_only: bool = False,
               cigar_capacity: int | None = None, timing: bool = False, use_offsets: bool = True,

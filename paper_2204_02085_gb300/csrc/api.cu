@@ -102,14 +102,14 @@ struct wfa_gpu_ctx {
   int teams_medium = 1;  // one-warp arena teams
   int teams_long = 1;    // one-CTA arena teams
   wfa::ShortPlan plan{};
-  // short-kernel variants (indices into plan.v): for sequences <= 127 bases
-  // a small-store variant and a large-store one, chosen per batch from a
-  // sampled score distribution; for <= 255 bases an int16 variant
-  // candidates for sequences <= 127 bases, smallest store first; the last
-  // one (largest store) scores the autotuner's sample
-  int variants_small[3] = {7, 4, 1};
-  int variant_big = 1;
-  int variant_mid = 6;
+  // short-kernel variants (indices into plan.v), per penalty model (0
+  // gap-affine, 1 gap-linear): candidates for sequences <= 127 bases,
+  // smallest store first, chosen per batch from a sampled score
+  // distribution (the largest store scores the sample); for <= 255 bases an
+  // int16 variant
+  int variants_small[2][3] = {{7, 4, 1}, {8, 9, 9}};
+  int variant_big[2] = {1, 9};
+  int variant_mid[2] = {6, 10};
   int variant_forced = -1;  // tuning override (WFA_GPU_SHORT_VARIANT)
   int last_variant = -1;
   wfa::Ctrl* ctrl = nullptr;    // device
@@ -403,18 +403,21 @@ constexpr int64_t kTuneSample = 8192;
 // small one (more pairs resident per SM) runs the batch.  Returns the
 // variant index, or -1 on a CUDA error.
 int autotune_short(wfa_gpu_ctx* c, Call& k, const wfa::AlignArgs& a_in, int64_t n) {
-  if (c->variant_forced >= 0) return c->variant_forced;
+  const int model = a_in.oes == a_in.es ? 1 : 0;  // o = 0: gap-linear
+  if (c->variant_forced >= 0 && c->plan.v[c->variant_forced].linear == model) return c->variant_forced;
+  const int* small = c->variants_small[model];
+  const int big = c->variant_big[model];
   wfa::UGeo tab[64];
   const wfa::ScaledPen pen{a_in.xs, a_in.oes, a_in.es};
   int s_store[3];
   for (int j = 0; j < 3; ++j) {
-    const wfa::ShortVariant& v = c->plan.v[c->variants_small[j]];
+    const wfa::ShortVariant& v = c->plan.v[small[j]];
     s_store[j] = wfa::build_ugeo(tab, v.scap, v.cells, pen);
   }
   const int64_t m = std::min(n, kTuneSample);
   cudaStream_t st = c->stream;
   if (c->tune_score.ensure(m) || c->tune_status.ensure(m) || c->tune_aux.ensure(m) || c->tune_src.ensure(m))
-    return c->variant_big;
+    return big;
   wfa::AlignArgs a = a_in;
   a.n = m;
   a.s_cap = std::min(a_in.s_cap, 1 << 20);
@@ -428,7 +431,7 @@ int autotune_short(wfa_gpu_ctx* c, Call& k, const wfa::AlignArgs& a_in, int64_t 
   if (!k.ok(cudaMemsetAsync(a.ctrl, 0, sizeof(wfa::Ctrl), st))) return -1;
   // pairs the sample run defers keep score -1
   if (!k.ok(cudaMemsetAsync(a.score, 0xff, m * sizeof(int32_t), st))) return -1;
-  if (!k.launched(wfa::launch_short(a, c->plan.v[c->variant_big], st))) return -1;
+  if (!k.launched(wfa::launch_short(a, c->plan.v[big], st))) return -1;
   if (!k.ok(d2h(c->h_tune, c->tune_score.p, m * sizeof(int32_t), st)) || !k.ok(cudaStreamSynchronize(st))) return -1;
   int64_t fit[3] = {0, 0, 0}, tot = 0;
   for (int64_t i = 0; i < m; ++i) {
@@ -438,8 +441,8 @@ int autotune_short(wfa_gpu_ctx* c, Call& k, const wfa::AlignArgs& a_in, int64_t 
     for (int j = 0; j < 3; ++j) fit[j] += (sc / a.g <= s_store[j]);
   }
   for (int j = 0; j < 3; ++j)
-    if (tot == 0 || fit[j] * 100 >= tot * 99) return c->variants_small[j];
-  return c->variant_big;
+    if (tot == 0 || fit[j] * 100 >= tot * 99) return small[j];
+  return big;
 }
 
 }  // namespace
@@ -611,7 +614,7 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
   if (plain) {
     if (!k.launched(wfa::launch_route_all(a, st))) return fail_cuda(k);
   } else {
-    int vi = ctx->variant_mid;
+    int vi = ctx->variant_mid[pen.o == 0 ? 1 : 0];
     if (ctx->h_ctrl->max_len <= 127) {
       vi = autotune_short(ctx, k, a, n);
       if (vi < 0) return fail_cuda(k);
@@ -912,6 +915,11 @@ int wfa_gpu_align_batch(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const
                        max_score, flags, out_scores, out_status, out_cigars, cap, out_cigar_offsets);
   return align_eager(ctx, n, patterns, pattern_offsets, pattern_lengths, texts, text_offsets, text_lengths, pen,
                      max_score, flags, out_scores, out_status, out_cigars, cap, out_cigar_offsets);
+}
+
+const char* wfa_gpu_short_variant_name(const wfa_gpu_ctx* ctx, int index) {
+  if (!ctx || index < 0 || index >= ctx->plan.count) return nullptr;
+  return ctx->plan.v[index].name;
 }
 
 int wfa_gpu_pack2bit(wfa_gpu_ctx* ctx, int64_t n, const char* seqs, const int64_t* offsets, const int32_t* lengths,

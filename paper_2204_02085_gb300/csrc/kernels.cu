@@ -22,11 +22,11 @@ namespace {
 
 // ------------------------------------------------------------ short kernel
 
-template <int G, int LMAX, int CELLS, int SCAP, typename Off>
+template <int G, int LMAX, int CELLS, int SCAP, typename Off, bool LIN>
 __global__ void __launch_bounds__(kShortBlock, 8) short_kernel(const AlignArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_last;
-  short_body<G, LMAX, CELLS, SCAP, Off>(a, smem, &s_last);
+  short_body<G, LMAX, CELLS, SCAP, Off, LIN>(a, smem, &s_last);
 }
 
 // ----------------------------------------------------------- arena kernels
@@ -223,10 +223,10 @@ int current_device() {
 
 namespace {
 
-template <int G, int LMAX, int CELLS, int SCAP, typename Off>
+template <int G, int LMAX, int CELLS, int SCAP, typename Off, bool LIN = false>
 cudaError_t plan_one(int device, ShortVariant* v, const char* name) {
-  using C = ShortCfg<G, LMAX, CELLS, SCAP, Off>;
-  auto k = short_kernel<G, LMAX, CELLS, SCAP, Off>;
+  using C = ShortCfg<G, LMAX, CELLS, SCAP, Off, LIN>;
+  auto k = short_kernel<G, LMAX, CELLS, SCAP, Off, LIN>;
   const int warps = kShortBlock / 32;
   const size_t smem = C::smem_bytes(warps);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -244,13 +244,14 @@ cudaError_t plan_one(int device, ShortVariant* v, const char* name) {
   v->name = name;
   v->cells = CELLS;
   v->scap = SCAP;
+  v->linear = LIN ? 1 : 0;
   return cudaSuccess;
 }
 
 }  // namespace
 
 // The short-kernel variants: (lanes per pair, longest sequence, cells per
-// pair, largest score index, offset type).
+// pair, largest score index, offset type, gap-linear model).
 cudaError_t short_plan(int device, ShortPlan* plan) {
   cudaError_t e;
   int i = 0;
@@ -262,6 +263,10 @@ cudaError_t short_plan(int device, ShortPlan* plan) {
   if ((e = plan_one<2, 255, 208, 31, int16_t>(device, &plan->v[i++], "g2_l255_c208_i16"))) return e;
   if ((e = plan_one<4, 255, 208, 31, int16_t>(device, &plan->v[i++], "g4_l255_c208_i16"))) return e;
   if ((e = plan_one<1, 127, 40, 15, int8_t>(device, &plan->v[i++], "g1_l127_c40_i8"))) return e;
+  // gap-linear model (o = 0): M only, so a third of the store per cell
+  if ((e = plan_one<1, 127, 64, 15, int8_t, true>(device, &plan->v[i++], "g1_l127_c64_lin"))) return e;
+  if ((e = plan_one<2, 127, 256, 31, int8_t, true>(device, &plan->v[i++], "g2_l127_c256_lin"))) return e;
+  if ((e = plan_one<2, 255, 256, 31, int16_t, true>(device, &plan->v[i++], "g2_l255_c256_lin_i16"))) return e;
   plan->count = i;
   // the one-CTA arena kernel keeps two sequences of up to 32,768 bases in
   // shared memory

@@ -71,6 +71,7 @@ struct ShortVariant {
   int max_len;  // longest sequence the variant takes
   int cells;    // wavefront cells stored per pair
   int scap;     // largest score index of the geometry table
+  int linear;   // 1: gap-linear model only (o = 0; M stored, I and D derived)
 };
 struct ShortPlan {
   ShortVariant v[12];

@@ -33,7 +33,7 @@ __device__ __forceinline__ void write_result(const AlignArgs& a, int64_t pair, i
 // Shared-memory layout of the short kernel: the geometry table, then one
 // region per warp holding its P = 32/G pairs' packed sequences and M/I/D
 // cells, interleaved by pair (element c of pair slot q at [c * P + q]).
-template <int G, int LMAX, int CELLS, int SCAP, typename Off>
+template <int G, int LMAX, int CELLS, int SCAP, typename Off, bool LIN = false>
 struct ShortCfg {
   static constexpr int P = 32 / G;
   // packed sequence: 32-bit words (16 bases), data + two zero pad words,
@@ -45,8 +45,8 @@ struct ShortCfg {
     uint32_t pw[NW * PS];
     uint32_t tw[NW * PS];
     Off M[CELLS * P];
-    Off I[CELLS * P];
-    Off D[CELLS * P];
+    Off I[LIN ? 4 : CELLS * P];  // gap-linear model: I and D follow from M
+    Off D[LIN ? 4 : CELLS * P];
     int16_t nl[P], ml[P];  // pair lengths, readable by every lane
     uint8_t act[P];        // slots of the pairs still running, ascending
   };
@@ -54,9 +54,10 @@ struct ShortCfg {
   // sequences, 16-byte chunks) borrows the cell arrays, unused while
   // packing; longer spans take the packer's per-slot path
   static constexpr int kSpanAll = (P * LMAX + 15) / 16 + 1;
-  static constexpr int kSpanFit = (int)(3 * CELLS * P * sizeof(Off) / 16);
+  static constexpr int kCellBytes = (int)(sizeof(Off) * (LIN ? CELLS * P : 3 * CELLS * P));
+  static constexpr int kSpanFit = kCellBytes / 16;
   static constexpr int SPAN = kSpanAll < kSpanFit ? kSpanAll : kSpanFit;
-  static_assert(16 * SPAN <= 3 * CELLS * P * sizeof(Off), "packer scratch does not fit the cell arrays");
+  static_assert(16 * SPAN <= kCellBytes, "packer scratch does not fit the cell arrays");
   static constexpr size_t kTabBytes = ((SCAP + 1) * sizeof(UGeo) + 15) / 16 * 16;
   static constexpr size_t kWarpBytes = (sizeof(WarpShm) + 15) / 16 * 16;
   static constexpr size_t smem_bytes(int warps) { return kTabBytes + (size_t)warps * kWarpBytes; }
@@ -67,7 +68,7 @@ struct ShortCfg {
 // gathers its sources and applies the recurrences (the mismatch, insertion
 // and deletion candidates, each null past the sequence ends) giving the
 // offset h to extend, store() writes M, I and D.
-template <typename Off, int P>
+template <typename Off, int P, bool LIN = false>
 struct Cell {
   int r, i, k, n, m, h, iv, dv;
   __device__ __forceinline__ void load(const Off* M, const Off* I, const Off* D, const uint8_t* act,
@@ -84,8 +85,11 @@ struct Cell {
     const int mx = get_off<UView<Off, P>, 0>(v, gx, k, NUL);
     const int mlo = get_off<UView<Off, P>, 0>(v, go, k - 1, NUL);
     const int mro = get_off<UView<Off, P>, 0>(v, go, k + 1, NUL);
-    const int il = get_off<UView<Off, P>, 1>(v, ge, k - 1, NUL);
-    const int dr = get_off<UView<Off, P>, 2>(v, ge, k + 1, NUL);
+    // gap-linear model (o = 0): I[s-e][k-1] <= M[s-e][k-1] and D[s-e][k+1] <=
+    // M[s-e][k+1] (M is the maximum over them), so the M sources alone give
+    // the same I and D
+    const int il = LIN ? NUL : get_off<UView<Off, P>, 1>(v, ge, k - 1, NUL);
+    const int dr = LIN ? NUL : get_off<UView<Off, P>, 2>(v, ge, k + 1, NUL);
     // a null source stays negative through the +1 steps of the stored
     // scores, so only the far end needs testing; negative = null
     iv = max(mlo, il) + 1;
@@ -100,21 +104,46 @@ struct Cell {
     constexpr int NUL = NullOf<Off>::value;
     const int c = (g.base + i) * P + r;
     M[c] = (Off)(h >= 0 ? h : NUL);
-    I[c] = (Off)iv;
-    D[c] = (Off)dv;
+    if (!LIN) {
+      I[c] = (Off)iv;
+      D[c] = (Off)dv;
+    }
   }
 };
 
-// Fused short-read kernel: G lanes per pair, 32/G pairs per warp advancing
-// through the scores in lockstep; per pair: pack both sequences (2 bits per
-// base) into shared memory, run the wavefront recurrences with cells in
-// shared memory, then walk the backtrace and write the CIGAR runs (last
-// first) into the pair's slot.  Pairs longer than LMAX, or whose score
-// passes the last storable wavefront (but not the caller's max_score), are
-// deferred to the arena kernel.
-template <int G, int LMAX, int CELLS, int SCAP, typename Off>
+// The short kernel's store seen by the backtrace under the gap-linear model
+// (o = 0): only M is kept, and I_s[k] = M_{s-e}[k-1] + 1, D_s[k] =
+// M_{s-e}[k+1] (each null past the sequence ends), which is what the
+// gap-affine recurrences give when o = 0.
+template <typename Off, int P>
+struct LinUView : UView<Off, P> {
+  int n, m, e;
+};
+template <typename Off, int P>
+__device__ __forceinline__ int bt_I(const LinUView<Off, P>& v, int s, int k) {
+  constexpr int NUL = NullOf<Off>::value;
+  const int ml = get_off<UView<Off, P>, 0>(v, geo_of(v, s - v.e, 1), k - 1, NUL);
+  return ml >= 0 && ml + 1 <= v.m ? ml + 1 : NUL;
+}
+template <typename Off, int P>
+__device__ __forceinline__ int bt_D(const LinUView<Off, P>& v, int s, int k) {
+  constexpr int NUL = NullOf<Off>::value;
+  const int mr = get_off<UView<Off, P>, 0>(v, geo_of(v, s - v.e, 1), k + 1, NUL);
+  return mr >= 0 && mr - k <= v.n ? mr : NUL;
+}
+
+// Fused short-read kernel: 32/G pairs per warp advance through the scores
+// together; per pair: pack both sequences (2 bits per base, G lanes) into
+// shared memory, run the wavefront recurrences with cells in shared memory
+// (at each score the cells of the pairs still running are spread over all
+// 32 lanes), then walk the backtrace (the pair's first lane) and write the
+// CIGAR runs (last first) into the pair's slot.  Pairs longer than LMAX, or
+// whose score passes the last storable wavefront (but not the caller's
+// max_score), are deferred to the arena kernel.  LIN: the gap-linear model
+// (o = 0, the edit distance at x = e = 1), only M stored.
+template <int G, int LMAX, int CELLS, int SCAP, typename Off, bool LIN = false>
 __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* smem, int* s_last_shared) {
-  using C = ShortCfg<G, LMAX, CELLS, SCAP, Off>;
+  using C = ShortCfg<G, LMAX, CELLS, SCAP, Off, LIN>;
   constexpr int P = C::P;
   constexpr int NUL = NullOf<Off>::value;
   static_assert(NUL + SCAP + 1 < 0, "a null offset must stay negative over the stored scores");
@@ -168,7 +197,11 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
     __syncwarp();
     const int kf = m - n;
     int s_fin = -1;
-    if (active && lane == 0) view.put(0, 0, extend_diag32(pw, tw, n, m, 0, 0, PS), NUL, NUL);
+    if (active && lane == 0) {
+      const int h0 = extend_diag32(pw, tw, n, m, 0, 0, PS);
+      if constexpr (LIN) W->M[q] = (Off)h0;  // no I/D store under the gap-linear model
+      else view.put(0, 0, h0, NUL, NUL);
+    }
     __syncwarp();
     if (active && kf == 0 && view.getM(Geo{0, 1, 0}, 0) == m) {
       s_fin = 0;
@@ -195,7 +228,7 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
       const Geo ge = geo_of(view, s - pen.e, 2);
       const int items = na * g.w;
       for (int f = lane32; f < items; f += 32) {
-        Cell<Off, P> c;
+        Cell<Off, P, LIN> c;
         c.load(W->M, W->I, W->D, W->act, W->nl, W->ml, tab, g, gx, go, ge, f, na, inv_na);
         if (c.h >= 0) c.h = extend_diag32(W->pw + c.r, W->tw + c.r, c.n, c.m, c.k, c.h, PS);
         c.store(W->M, W->I, W->D, g);
@@ -223,7 +256,13 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
           write_result(a, pair, 0, s_fin * a.g, 0, 0);
         } else {
           const int64_t src = pair * kSlot;
-          const int nr = wfa_backtrace(view, n, m, pen, s_fin, a.runs + src, kSlot);
+          int nr;
+          if constexpr (LIN) {
+            LinUView<Off, P> lv{view, n, m, pen.e};
+            nr = wfa_backtrace(lv, n, m, pen, s_fin, a.runs + src, kSlot);
+          } else {
+            nr = wfa_backtrace(view, n, m, pen, s_fin, a.runs + src, kSlot);
+          }
           if (nr == -1) {
             defer_pair(a, pair);  // more runs than a slot holds
           } else if (nr < 0) {

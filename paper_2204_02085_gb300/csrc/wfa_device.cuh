@@ -608,6 +608,17 @@ __device__ int wfa_forward(V& view, const uint64_t* pw, const uint64_t* tw, int 
 
 // -------------------------------------------------------------- backtrace
 
+// I_s[k] and D_s[k] as the backtrace reads them (null past the stored
+// range); views that do not store I and D overload these.
+template <class V>
+__device__ __forceinline__ int bt_I(const V& view, int s, int k) {
+  return get_off<V, 1>(view, geo_of(view, s, 2), k, NullOf<typename V::Off>::value);
+}
+template <class V>
+__device__ __forceinline__ int bt_D(const V& view, int s, int k) {
+  return get_off<V, 2>(view, geo_of(view, s, 4), k, NullOf<typename V::Off>::value);
+}
+
 // Walk back from (M, s_final, m-n, m) and write run-length CIGAR words into
 // runs[0 ..), LAST run first.  Returns the number of runs, -1 if more than
 // cap runs are needed, -2 if the stored wavefronts are inconsistent (which
@@ -649,8 +660,8 @@ __device__ int wfa_backtrace(const V& view, int n, int m, ScaledPen p, int s_fin
       } else {
         xv = NUL;
       }
-      const int iv = get_off<V, 1>(view, geo_of(view, s, 2), k, NUL);
-      const int dv = get_off<V, 2>(view, geo_of(view, s, 4), k, NUL);
+      const int iv = bt_I(view, s, k);
+      const int dv = bt_D(view, s, k);
       int pick, c;
       if (xv >= 0 && xv >= iv && xv >= dv) {
         pick = kOpX; c = xv;
@@ -673,7 +684,7 @@ __device__ int wfa_backtrace(const V& view, int n, int m, ScaledPen p, int s_fin
       }
     } else if (state == kOpI) {
       emit(kOpI, 1);
-      if (get_off<V, 1>(view, geo_of(view, s - p.e, 2), k - 1, NUL) == h - 1) {
+      if (bt_I(view, s - p.e, k - 1) == h - 1) {
         s -= p.e;
       } else {
         s -= p.oe;
@@ -683,7 +694,7 @@ __device__ int wfa_backtrace(const V& view, int n, int m, ScaledPen p, int s_fin
       h -= 1;
     } else {
       emit(kOpD, 1);
-      if (get_off<V, 2>(view, geo_of(view, s - p.e, 4), k + 1, NUL) == h) {
+      if (bt_D(view, s - p.e, k + 1) == h) {
         s -= p.e;
       } else {
         s -= p.oe;

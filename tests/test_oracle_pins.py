@@ -21,7 +21,9 @@ import random
 import numpy as np
 import pytest
 
-PENALTY_SETS = [(4, 6, 2), (1, 0, 1), (2, 3, 1), (5, 1, 3), (3, 2, 2), (16, 6, 2)]
+# gap-affine sets, and gap-linear ones (o = 0: every gap column costs e; the
+# edit distance at x = e = 1)
+PENALTY_SETS = [(4, 6, 2), (1, 0, 1), (2, 3, 1), (5, 1, 3), (3, 2, 2), (16, 6, 2), (3, 0, 2), (2, 0, 3)]
 
 
 def all_seqs(max_len):
@@ -64,7 +66,7 @@ def check_pair(oracle, p, t, pen):
     assert wops == gops == bops, (p, t, pen, bops, gops, wops)
 
 
-@pytest.mark.parametrize("pen", [(4, 6, 2), (1, 0, 1), (16, 6, 2)])
+@pytest.mark.parametrize("pen", [(4, 6, 2), (1, 0, 1), (16, 6, 2), (3, 0, 2)])
 def test_exhaustive_lengths_upto_4(oracle_mod, pen):
     """Every pair of A/C/G/T strings of length <= 4 (341^2 pairs): brute
     force, Gotoh and WFA agree on the score and on the canonical alignment."""
