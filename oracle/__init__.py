@@ -20,7 +20,9 @@ Functions (each follows the paper's method, WFA, Sec. I, run unmodified):
 * ``wfa_batch(...)``        ``wfa`` over many pairs on POSIX threads
 
 Penalties are ``(x, o, e)``: mismatch x, a gap run of length L costs o + L*e,
-match 0.  Alignments are op strings over ``M X I D`` (I consumes text, D
+match 0.  ``ends`` = (pattern begin, pattern end, text begin, text end) free
+lengths selects ends-free alignment (see ``wfa_oracle.c``); the default
+(0, 0, 0, 0) is the global alignment.  Alignments are op strings over ``M X I D`` (I consumes text, D
 consumes pattern) or run-length words ``(len << 4) | code`` with codes
 M=0 X=1 I=2 D=3.
 """
@@ -75,22 +77,23 @@ def lib():
             vp = ctypes.c_void_p
             L.oracle_valid.argtypes = [cp, i64]
             L.oracle_valid.restype = ctypes.c_int
-            L.oracle_rescore.argtypes = [cp, i64, cp, i64, cp, i64, i64, i64, i64]
-            L.oracle_rescore.restype = i64
-            L.oracle_brute.argtypes = [cp, ctypes.c_int, cp, ctypes.c_int, i64, i64, i64, vp, vp, vp]
-            L.oracle_brute.restype = i64
-            L.oracle_gotoh.argtypes = [cp, i64, cp, i64, i64, i64, i64, vp, vp]
-            L.oracle_gotoh.restype = i64
-            L.oracle_wfa.argtypes = [cp, i64, cp, i64, i64, i64, i64, i64, ctypes.c_int,
-                                     vp, vp, i64, vp, vp]
-            L.oracle_wfa.restype = ctypes.c_int
+            L.oracle_rescore_ef.argtypes = [cp, i64, cp, i64, cp, i64, i64, i64, i64, i64, i64, i64, i64]
+            L.oracle_rescore_ef.restype = i64
+            L.oracle_brute_ef.argtypes = [cp, ctypes.c_int, cp, ctypes.c_int, i64, i64, i64, i64, i64, i64, i64,
+                                          vp, vp, vp]
+            L.oracle_brute_ef.restype = i64
+            L.oracle_gotoh_ef.argtypes = [cp, i64, cp, i64, i64, i64, i64, i64, i64, i64, i64, vp, vp]
+            L.oracle_gotoh_ef.restype = i64
+            L.oracle_wfa_ef.argtypes = [cp, i64, cp, i64, i64, i64, i64, i64, i64, i64, i64, i64, ctypes.c_int,
+                                        vp, vp, i64, vp, vp]
+            L.oracle_wfa_ef.restype = ctypes.c_int
             L.oracle_pack2bit.argtypes = [cp, i64, vp]
             L.oracle_pack2bit.restype = ctypes.c_int
             L.oracle_runs_encode.argtypes = [cp, i64, vp, i64]
             L.oracle_runs_encode.restype = i64
-            L.oracle_wfa_batch.argtypes = [i64, vp, vp, vp, vp, vp, vp, i64, i64, i64, i64,
-                                           vp, vp, vp, i64, vp, ctypes.c_int, vp]
-            L.oracle_wfa_batch.restype = ctypes.c_int
+            L.oracle_wfa_batch_ef.argtypes = [i64, vp, vp, vp, vp, vp, vp, i64, i64, i64, i64, i64, i64, i64,
+                                              i64, vp, vp, vp, i64, vp, ctypes.c_int, vp]
+            L.oracle_wfa_batch_ef.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -103,45 +106,48 @@ def _ptr(a: np.ndarray):
     return ctypes.c_void_p(a.ctypes.data)
 
 
-def rescore(p, t, ops: str, pen) -> int:
+GLOBAL = (0, 0, 0, 0)
+
+
+def rescore(p, t, ops: str, pen, ends=GLOBAL) -> int:
     """Cost of alignment ``ops`` of p and t, or -1 if it is not one."""
     p, t, o = _b(p), _b(t), ops.encode()
     x, go, ge = pen
-    return lib().oracle_rescore(p, len(p), t, len(t), o, len(o), x, go, ge)
+    return lib().oracle_rescore_ef(p, len(p), t, len(t), o, len(o), x, go, ge, *ends)
 
 
-def brute(p, t, pen):
+def brute(p, t, pen, ends=GLOBAL):
     """(minimum cost, canonical op string, number of alignments enumerated)."""
     p, t = _b(p), _b(t)
     x, go, ge = pen
     buf = ctypes.create_string_buffer(32)
     nops, npaths = ctypes.c_int64(), ctypes.c_int64()
-    c = lib().oracle_brute(p, len(p), t, len(t), x, go, ge, ctypes.cast(buf, ctypes.c_void_p),
-                           ctypes.byref(nops), ctypes.byref(npaths))
+    c = lib().oracle_brute_ef(p, len(p), t, len(t), x, go, ge, *ends, ctypes.cast(buf, ctypes.c_void_p),
+                              ctypes.byref(nops), ctypes.byref(npaths))
     if c < 0:
         raise ValueError("brute force takes lengths <= 12")
     return c, buf.raw[: nops.value].decode(), npaths.value
 
 
-def gotoh(p, t, pen, want_ops: bool = True):
+def gotoh(p, t, pen, want_ops: bool = True, ends=GLOBAL):
     """(score, op string or None) from the Gotoh DP and its walk-back."""
     p, t = _b(p), _b(t)
     x, go, ge = pen
     if want_ops:
         buf = ctypes.create_string_buffer(len(p) + len(t) + 1)
         nops = ctypes.c_int64()
-        s = lib().oracle_gotoh(p, len(p), t, len(t), x, go, ge,
-                               ctypes.cast(buf, ctypes.c_void_p), ctypes.byref(nops))
+        s = lib().oracle_gotoh_ef(p, len(p), t, len(t), x, go, ge, *ends,
+                                  ctypes.cast(buf, ctypes.c_void_p), ctypes.byref(nops))
         if s < 0:
             raise RuntimeError("oracle_gotoh failed (%d)" % s)
         return s, buf.raw[: nops.value].decode()
-    s = lib().oracle_gotoh(p, len(p), t, len(t), x, go, ge, None, None)
+    s = lib().oracle_gotoh_ef(p, len(p), t, len(t), x, go, ge, *ends, None, None)
     if s < 0:
         raise RuntimeError("oracle_gotoh failed (%d)" % s)
     return s, None
 
 
-def wfa(p, t, pen, max_score: int = 0, want_ops: bool = True, counts: Counts | None = None):
+def wfa(p, t, pen, max_score: int = 0, want_ops: bool = True, counts: Counts | None = None, ends=GLOBAL):
     """(status, score, op string or None) from the CPU wavefront algorithm."""
     p, t = _b(p), _b(t)
     x, go, ge = pen
@@ -149,9 +155,9 @@ def wfa(p, t, pen, max_score: int = 0, want_ops: bool = True, counts: Counts | N
     cap = len(p) + len(t) + 1
     buf = ctypes.create_string_buffer(cap)
     nops = ctypes.c_int64()
-    rc = lib().oracle_wfa(p, len(p), t, len(t), x, go, ge, max_score, int(want_ops),
-                          ctypes.byref(score), ctypes.cast(buf, ctypes.c_void_p), cap,
-                          ctypes.byref(nops), ctypes.byref(counts) if counts is not None else None)
+    rc = lib().oracle_wfa_ef(p, len(p), t, len(t), x, go, ge, *ends, max_score, int(want_ops),
+                             ctypes.byref(score), ctypes.cast(buf, ctypes.c_void_p), cap,
+                             ctypes.byref(nops), ctypes.byref(counts) if counts is not None else None)
     if rc < 0:
         raise RuntimeError("oracle_wfa failed (%d)" % rc)
     ops = buf.raw[: nops.value].decode() if (want_ops and rc == OK) else None
@@ -187,7 +193,8 @@ def runs_to_cigar(runs) -> str:
 
 
 def wfa_batch(batch, pen, max_score: int = 0, want_cigar: bool = True,
-              nthreads: int = 1, runs_per_pair: int | None = None, counts: Counts | None = None):
+              nthreads: int = 1, runs_per_pair: int | None = None, counts: Counts | None = None,
+              ends=GLOBAL):
     """Align every pair of ``batch`` (a ``synth.Batch``-like object with
     patterns/pattern_offsets/pattern_lengths/texts/text_offsets/text_lengths)
     with the CPU WFA.  Returns (scores int32, status int8, cigar words uint32,
@@ -212,10 +219,10 @@ def wfa_batch(batch, pen, max_score: int = 0, want_cigar: bool = True,
         runs_per_pair = 0
         runs = nruns = None
         rp = np_ = None
-    rc = lib().oracle_wfa_batch(n, _ptr(pat), _ptr(poff), _ptr(plen), _ptr(txt), _ptr(toff),
-                                _ptr(tlen), x, go, ge, max_score, _ptr(scores), _ptr(status),
-                                rp, runs_per_pair, np_, int(nthreads),
-                                ctypes.byref(counts) if counts is not None else None)
+    rc = lib().oracle_wfa_batch_ef(n, _ptr(pat), _ptr(poff), _ptr(plen), _ptr(txt), _ptr(toff),
+                                   _ptr(tlen), x, go, ge, *ends, max_score, _ptr(scores), _ptr(status),
+                                   rp, runs_per_pair, np_, int(nthreads),
+                                   ctypes.byref(counts) if counts is not None else None)
     if rc < 0:
         raise RuntimeError("oracle_wfa_batch failed (%d)" % rc)
     offsets = np.zeros(n + 1, dtype=np.int64)

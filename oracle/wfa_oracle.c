@@ -34,6 +34,18 @@
  *   'M' match, 'X' mismatch, 'I' (consumes text only), 'D' (consumes pattern
  *   only).  Run-length words are (len << 4) | op with op 0=M 1=X 2=I 3=D.
  *
+ * Ends-free alignment (the *_ef functions; not in the paper, which aligns
+ * reads end to end, Sec. I -- a variant of the cited method; the reading
+ * used here): up to pb leading and pe trailing pattern characters, and up to
+ * tb leading and te trailing text characters, may be left unaligned at no
+ * cost.  The alignment starts at (v, 0) with v <= pb or at (0, h) with
+ * h <= tb, and ends at (n, h) with h >= m - te or at (v, m) with
+ * v >= n - pe; a gap after the start or before the end is paid as usual.
+ * The op string still covers both sequences: the skipped characters are its
+ * leading / trailing D (pattern) or I (text) ops.  Among optimal end cells
+ * the one on the diagonal k = h - v closest to m - n is taken, the larger k
+ * on a tie.  All four lengths 0 is the global alignment above.
+ *
  * Status codes per pair: 0 ok, 1 score above max_score, 2 invalid character.
  */
 #include <limits.h>
@@ -105,6 +117,36 @@ int64_t oracle_rescore(const char *P, int64_t n, const char *T, int64_t m,
   return cost;
 }
 
+/* Cost of the alignment ops[0..nops) under the ends-free rules (pb, pe, tb,
+ * te; all 0 = oracle_rescore), or -1 if ops is not an alignment of P and T.
+ * The leading run of ops, if it is D (resp. I), has up to pb (resp. tb) of
+ * its characters free, the trailing run up to pe (resp. te); the free
+ * characters are taken at the sequence ends, and the rest of such a run is
+ * one gap.  Taking as many free characters as allowed is never worse, so
+ * that is the cost: the plain cost less what the free characters save (a
+ * whole free run saves o + L*e, a partly free one e per free character). */
+int64_t oracle_rescore_ef(const char *P, int64_t n, const char *T, int64_t m,
+                          const char *ops, int64_t nops, int64_t x, int64_t o,
+                          int64_t e, int64_t pb, int64_t pe, int64_t tb,
+                          int64_t te) {
+  int64_t cost = oracle_rescore(P, n, T, m, ops, nops, x, o, e);
+  if (cost < 0 || nops == 0) return cost;
+  int64_t l0 = 0, l1 = 0;
+  while (l0 < nops && ops[l0] == ops[0]) l0++;
+  while (l1 < nops && ops[nops - 1 - l1] == ops[nops - 1]) l1++;
+  int64_t fb = ops[0] == 'D' ? pb : ops[0] == 'I' ? tb : 0;
+  int64_t fe = ops[nops - 1] == 'D' ? pe : ops[nops - 1] == 'I' ? te : 0;
+  if (l0 == nops) {
+    /* one run: if a gap, both of its ends are free */
+    int64_t f = fb + fe < nops ? fb + fe : nops;
+    return f == nops ? 0 : cost - f * e;
+  }
+  int64_t f0 = l0 < fb ? l0 : fb, f1 = l1 < fe ? l1 : fe;
+  cost -= f0 == l0 ? o + l0 * e : f0 * e;
+  cost -= f1 == l1 ? o + l1 * e : f1 * e;
+  return cost;
+}
+
 /* ops string -> run-length words (len << 4) | code.  Returns the number of
  * runs, or -1 if cap is too small. */
 int64_t oracle_runs_encode(const char *ops, int64_t nops, uint32_t *runs,
@@ -153,6 +195,7 @@ typedef struct {
   const char *P, *T;
   int n, m;
   int64_t x, o, e;
+  int64_t pb, pe, tb, te;
   char path[32];
   int64_t best;
   char best_ops[32];
@@ -162,8 +205,8 @@ typedef struct {
 
 static void brute_rec(brute_t *b, int v, int h, int len) {
   if (v == b->n && h == b->m) {
-    int64_t c = oracle_rescore(b->P, b->n, b->T, b->m, b->path, len, b->x,
-                               b->o, b->e);
+    int64_t c = oracle_rescore_ef(b->P, b->n, b->T, b->m, b->path, len, b->x,
+                                  b->o, b->e, b->pb, b->pe, b->tb, b->te);
     b->count++;
     if (c < 0) return; /* cannot happen: diagonal steps are labelled M/X by
                           character equality */
@@ -190,23 +233,32 @@ static void brute_rec(brute_t *b, int v, int h, int len) {
   }
 }
 
-/* Minimum cost over every alignment of P and T (n, m <= 12), and the
- * alignment whose reversed op string is smallest under lex_rank among the
- * optimal ones.  Returns the cost, -1 on bad arguments.  *npaths receives the
- * number of alignments enumerated (a Delannoy number). */
-int64_t oracle_brute(const char *P, int n, const char *T, int m, int64_t x,
-                     int64_t o, int64_t e, char *ops, int64_t *nops,
-                     int64_t *npaths) {
+/* Minimum cost over every alignment of P and T (n, m <= 12) under the
+ * ends-free rules (oracle_rescore_ef), and the alignment whose reversed op
+ * string is smallest under lex_rank among the optimal ones.  Returns the
+ * cost, -1 on bad arguments.  *npaths receives the number of alignments
+ * enumerated (a Delannoy number). */
+int64_t oracle_brute_ef(const char *P, int n, const char *T, int m, int64_t x,
+                        int64_t o, int64_t e, int64_t pb, int64_t pe, int64_t tb,
+                        int64_t te, char *ops, int64_t *nops, int64_t *npaths) {
   if (n < 0 || m < 0 || n > 12 || m > 12) return -1;
   brute_t b;
   memset(&b, 0, sizeof b);
   b.P = P; b.T = T; b.n = n; b.m = m; b.x = x; b.o = o; b.e = e;
+  b.pb = pb; b.pe = pe; b.tb = tb; b.te = te;
   b.best = -1;
   brute_rec(&b, 0, 0, 0);
   if (ops) memcpy(ops, b.best_ops, (size_t)b.best_len);
   if (nops) *nops = b.best_len;
   if (npaths) *npaths = b.count;
   return b.best;
+}
+
+/* The global alignment: oracle_brute_ef with no free ends. */
+int64_t oracle_brute(const char *P, int n, const char *T, int m, int64_t x,
+                     int64_t o, int64_t e, char *ops, int64_t *nops,
+                     int64_t *npaths) {
+  return oracle_brute_ef(P, n, T, m, x, o, e, 0, 0, 0, 0, ops, nops, npaths);
 }
 
 /* ------------------------------------------------------------------ Gotoh */
@@ -221,14 +273,19 @@ static int64_t min2(int64_t a, int64_t b) { return a < b ? a : b; }
  *   D(v,h) = min(H(v-1,h) + o + e, D(v-1,h) + e)     pattern char consumed
  *   H(v,h) = min(H(v-1,h-1) + (P[v-1]==T[h-1] ? 0 : x), I(v,h), D(v,h))
  * out-of-range terms are +infinity; score = H(n,m).
+ * Ends-free (pb, pe, tb, te): H(v,0) = 0 for v <= pb and H(0,h) = 0 for
+ * h <= tb (free starts); the score is the least H over the end cells (n, h),
+ * h >= m - te, and (v, m), v >= n - pe.
  * If ops is not NULL the canonical alignment is recovered by walking back
- * from (n,m) with the project's tie-break (mismatch, then gap, then match at
- * each cell; inside a gap extend before open) and written forward into ops,
- * *nops receiving its length.  Returns the score, or -1 on allocation
- * failure.  Memory is 3 (n+1)(m+1) int64. */
-int64_t oracle_gotoh(const char *P, int64_t n, const char *T, int64_t m,
-                     int64_t x, int64_t o, int64_t e, char *ops,
-                     int64_t *nops) {
+ * from the chosen end cell (see the header) with the project's tie-break
+ * (mismatch, then gap, then match at each cell; inside a gap extend before
+ * open) down to a free start, and written forward into ops (the skipped
+ * characters as leading / trailing D or I ops), *nops receiving its length.
+ * Returns the score, or -1 on allocation failure.  Memory is 3 (n+1)(m+1)
+ * int64. */
+int64_t oracle_gotoh_ef(const char *P, int64_t n, const char *T, int64_t m,
+                        int64_t x, int64_t o, int64_t e, int64_t pb, int64_t pe,
+                        int64_t tb, int64_t te, char *ops, int64_t *nops) {
   int64_t W = m + 1;
   size_t cells = (size_t)(n + 1) * (size_t)(m + 1);
   int64_t *H = malloc(cells * sizeof(int64_t));
@@ -241,22 +298,44 @@ int64_t oracle_gotoh(const char *P, int64_t n, const char *T, int64_t m,
       int64_t iv = BIG, dv = BIG, hv = BIG;
       if (h > 0) iv = min2(AT(H, v, h - 1) + o + e, AT(I, v, h - 1) + e);
       if (v > 0) dv = min2(AT(H, v - 1, h) + o + e, AT(D, v - 1, h) + e);
-      if (v == 0 && h == 0) hv = 0;
+      if ((h == 0 && v <= pb) || (v == 0 && h <= tb)) hv = 0; /* a start */
       if (v > 0 && h > 0)
-        hv = AT(H, v - 1, h - 1) + (same(P, v - 1, T, h - 1) ? 0 : x);
+        hv = min2(hv, AT(H, v - 1, h - 1) + (same(P, v - 1, T, h - 1) ? 0 : x));
       hv = min2(hv, min2(iv, dv));
       AT(I, v, h) = iv;
       AT(D, v, h) = dv;
       AT(H, v, h) = hv;
     }
   }
-  int64_t score = AT(H, n, m);
+  /* the end cell: least H, then diagonal k = h - v nearest m - n (the
+   * larger k on a tie): d = 0, 1, ... tries k = kf + d (text end, (m - k,
+   * m)) before k = kf - d (pattern end, (n, n + k)) */
+  int64_t score = BIG, ev = n, eh = m;
+  int64_t dmax = pe > te ? pe : te;
+  for (int64_t d = 0; d <= dmax; d++) {
+    if (d <= pe && d <= n) {
+      int64_t v = n - d; /* (v, m) on k = kf + d */
+      if (AT(H, v, m) < score) { score = AT(H, v, m); ev = v; eh = m; }
+    }
+    if (d > 0 && d <= te && d <= m) {
+      int64_t h = m - d; /* (n, h) on k = kf - d */
+      if (AT(H, n, h) < score) { score = AT(H, n, h); ev = n; eh = h; }
+    }
+  }
   if (ops) {
     /* Walk back: state 0 = "M" (any op may come next), 1 = inside I, 2 =
      * inside D.  Ops are produced last-to-first, then reversed. */
-    int64_t v = n, h = m, s = score, k = 0;
+    int64_t v = ev, h = eh, s = score, k = 0;
+    for (int64_t i = 0; i < n - ev; i++) ops[k++] = 'D'; /* free pattern end */
+    for (int64_t i = 0; i < m - eh; i++) ops[k++] = 'I'; /* free text end */
     int state = 0;
-    while (v > 0 || h > 0 || state != 0) {
+    for (;;) {
+      if (state == 0 && s == 0 && ((h == 0 && v <= pb) || (v == 0 && h <= tb))) {
+        /* a free start: the skipped prefix */
+        for (int64_t i = 0; i < v; i++) ops[k++] = 'D';
+        for (int64_t i = 0; i < h; i++) ops[k++] = 'I';
+        break;
+      }
       if (state == 0) {
         if (v > 0 && h > 0 && !same(P, v - 1, T, h - 1) &&
             AT(H, v - 1, h - 1) + x == s) {
@@ -304,6 +383,13 @@ int64_t oracle_gotoh(const char *P, int64_t n, const char *T, int64_t m,
 #undef AT
   free(H); free(I); free(D);
   return score;
+}
+
+/* The global alignment: oracle_gotoh_ef with no free ends. */
+int64_t oracle_gotoh(const char *P, int64_t n, const char *T, int64_t m,
+                     int64_t x, int64_t o, int64_t e, char *ops,
+                     int64_t *nops) {
+  return oracle_gotoh_ef(P, n, T, m, x, o, e, 0, 0, 0, 0, ops, nops);
 }
 
 /* -------------------------------------------------------------------- WFA */
@@ -364,20 +450,27 @@ static void wf_free(wavefront *wf, int64_t count) {
  * lo_s/hi_s cover the sources that exist; a wavefront whose entries are all
  * missing does not exist.  s runs 0, 1, 2, ... and the result is the first
  * s with M_s[m-n] == m.
+ * Ends-free (pb, pe, tb, te): the free starts are the score-0 wavefront,
+ * M_0[k] = extend(max(k, 0)) on diagonals -min(pb, n) <= k <= min(tb, m);
+ * the result is the first s at which some diagonal reaches an end cell:
+ * M_s[k] == m for kf <= k <= kf + pe (text end), M_s[k] == n + k for
+ * kf - te <= k < kf (pattern end), kf = m - n; the nearest such k to kf
+ * ends the alignment (the larger on a tie).
  *
  * If max_score > 0 and no s <= max_score reaches the end, the status is
  * OR_SCORE_LIMIT.  If want_ops, the canonical alignment is written forward
  * into ops (capacity ops_cap) with its length in *nops; returns -3 if ops_cap
  * is too small, -2 on allocation failure, else the pair status. */
-int oracle_wfa(const char *P, int64_t n, const char *T, int64_t m, int64_t x,
-               int64_t o, int64_t e, int64_t max_score, int want_ops,
-               int64_t *score_out, char *ops, int64_t ops_cap, int64_t *nops,
-               oracle_counts *cnt) {
+int oracle_wfa_ef(const char *P, int64_t n, const char *T, int64_t m, int64_t x,
+                  int64_t o, int64_t e, int64_t pb, int64_t pe, int64_t tb,
+                  int64_t te, int64_t max_score, int want_ops,
+                  int64_t *score_out, char *ops, int64_t ops_cap, int64_t *nops,
+                  oracle_counts *cnt) {
   *score_out = -1;
   if (nops) *nops = 0;
   if (!oracle_valid(P, n) || !oracle_valid(T, m)) return OR_INVALID_CHAR;
   int64_t kf = m - n;
-  int64_t cap = 64, s_final = -1;
+  int64_t cap = 64, s_final = -1, k_end = kf, h_end = m;
   wavefront *wf = calloc((size_t)cap, sizeof(wavefront));
   if (!wf) return -2;
 
@@ -395,15 +488,20 @@ int oracle_wfa(const char *P, int64_t n, const char *T, int64_t m, int64_t x,
     }
     wavefront *w = &wf[s];
     if (s == 0) {
+      int64_t lo = -(pb < n ? pb : n), hi = tb < m ? tb : m;
       w->exists = 1;
-      w->lo = w->hi = 0;
-      w->M = malloc(sizeof(int64_t));
-      w->I = malloc(sizeof(int64_t));
-      w->D = malloc(sizeof(int64_t));
+      w->lo = lo;
+      w->hi = hi;
+      w->M = malloc((size_t)(hi - lo + 1) * sizeof(int64_t));
+      w->I = malloc((size_t)(hi - lo + 1) * sizeof(int64_t));
+      w->D = malloc((size_t)(hi - lo + 1) * sizeof(int64_t));
       if (!w->M || !w->I || !w->D) { wf_free(wf, cap); return -2; }
-      w->M[0] = extend(P, n, T, m, 0, 0, cnt);
-      w->I[0] = NUL;
-      w->D[0] = NUL;
+      for (int64_t k = lo; k <= hi; k++) {
+        /* start (0, k) for k >= 0, (-k, 0) for k < 0 */
+        w->M[k - lo] = extend(P, n, T, m, k, k > 0 ? k : 0, cnt);
+        w->I[k - lo] = NUL;
+        w->D[k - lo] = NUL;
+      }
     } else {
       int64_t sx = s - x, so = s - o - e, se = s - e;
       int ex_x = sx >= 0 && wf[sx].exists;
@@ -467,26 +565,43 @@ int oracle_wfa(const char *P, int64_t n, const char *T, int64_t m, int64_t x,
       cnt->cells += w->hi - w->lo + 1;
       cnt->wavefronts++;
     }
-    if (kf >= w->lo && kf <= w->hi && w->M[kf - w->lo] == m) {
-      s_final = s;
-      break;
+    /* end test, nearest diagonal to kf first (the larger k on a tie) */
+    int64_t dmax = pe > te ? pe : te;
+    for (int64_t d = 0; d <= dmax && s_final < 0; d++) {
+      if (d <= pe && wf_get(wf, s, kf + d, 'M') == m) {
+        s_final = s; k_end = kf + d; h_end = m;
+      } else if (d > 0 && d <= te && wf_get(wf, s, kf - d, 'M') == n + kf - d) {
+        s_final = s; k_end = kf - d; h_end = n + kf - d;
+      }
     }
+    if (s_final >= 0) break;
   }
 
   *score_out = s_final;
   int rc = OR_OK;
   if (want_ops) {
-    /* Backtrace from (M, s*, m-n, m).  Ops come out last-to-first. */
-    int64_t s = s_final, k = kf, h = m, len = 0;
+    /* Backtrace from (M, s*, k_end, h_end).  Ops come out last-to-first:
+     * first the free end (the pattern or text characters past the end
+     * cell). */
+    int64_t s = s_final, k = k_end, h = h_end, len = 0;
     char state = 'M';
+    for (int64_t i = 0; i < (n - (h_end - k_end)) + (m - h_end); i++) {
+      if (len >= ops_cap) { rc = -3; goto done; }
+      ops[len++] = k_end > kf ? 'D' : 'I';
+    }
     for (;;) {
       if (cnt) cnt->bt_steps++;
       if (state == 'M') {
         if (s == 0) {
-          /* k == 0 here: the remaining prefix is h matches */
-          for (int64_t i = 0; i < h; i++) {
+          /* a free start on diagonal k: (0, k) or (-k, 0), then matches */
+          int64_t h0 = k > 0 ? k : 0;
+          for (int64_t i = 0; i < h - h0; i++) {
             if (len >= ops_cap) { rc = -3; goto done; }
             ops[len++] = 'M';
+          }
+          for (int64_t i = 0; i < (k > 0 ? k : -k); i++) {
+            if (len >= ops_cap) { rc = -3; goto done; }
+            ops[len++] = k > 0 ? 'I' : 'D';
           }
           break;
         }
@@ -553,6 +668,15 @@ done:
   return rc;
 }
 
+/* The global alignment: oracle_wfa_ef with no free ends. */
+int oracle_wfa(const char *P, int64_t n, const char *T, int64_t m, int64_t x,
+               int64_t o, int64_t e, int64_t max_score, int want_ops,
+               int64_t *score_out, char *ops, int64_t ops_cap, int64_t *nops,
+               oracle_counts *cnt) {
+  return oracle_wfa_ef(P, n, T, m, x, o, e, 0, 0, 0, 0, max_score, want_ops, score_out, ops, ops_cap, nops,
+                       cnt);
+}
+
 /* --------------------------------------------------------------- pack2bit */
 
 /* The packed sequence format: code A=0 C=1 G=2 T=3 (either case), 32 bases
@@ -578,6 +702,7 @@ typedef struct {
   const char *pat; const int64_t *poff; const int32_t *plen;
   const char *txt; const int64_t *toff; const int32_t *tlen;
   int64_t x, o, e, max_score;
+  int64_t pb, pe, tb, te;
   int want_ops;
   int32_t *scores; int8_t *status;
   uint32_t *runs; int64_t runs_per_pair; int32_t *nruns;
@@ -600,8 +725,9 @@ static void *batch_worker(void *arg) {
       if (!ops) { j->err = -2; return NULL; }
     }
     int64_t score, nops = 0;
-    int rc = oracle_wfa(P, n, T, m, j->x, j->o, j->e, j->max_score,
-                        j->want_ops, &score, ops, ops_cap, &nops, &j->counts);
+    int rc = oracle_wfa_ef(P, n, T, m, j->x, j->o, j->e, j->pb, j->pe, j->tb,
+                           j->te, j->max_score, j->want_ops, &score, ops,
+                           ops_cap, &nops, &j->counts);
     if (rc < 0) { j->err = rc; free(ops); return NULL; }
     j->status[i] = (int8_t)rc;
     j->scores[i] = rc == OR_OK ? (int32_t)score : -1;
@@ -617,19 +743,21 @@ static void *batch_worker(void *arg) {
   return NULL;
 }
 
-/* Align pairs [0, n_pairs) with oracle_wfa on nthreads POSIX threads (static
- * contiguous chunks).  Pair i is pat[poff[i] .. +plen[i]) against
- * txt[toff[i] .. +tlen[i]).  If runs != NULL the canonical alignment of pair
- * i is written as run-length words to runs[i*runs_per_pair ...] with the
- * count in nruns[i].  counts_out (may be NULL) receives the summed work
- * counters.  Returns 0, or a negative error (-2 memory, -3 runs_per_pair too
- * small). */
-int oracle_wfa_batch(int64_t n_pairs, const char *pat, const int64_t *poff,
-                     const int32_t *plen, const char *txt, const int64_t *toff,
-                     const int32_t *tlen, int64_t x, int64_t o, int64_t e,
-                     int64_t max_score, int32_t *scores, int8_t *status,
-                     uint32_t *runs, int64_t runs_per_pair, int32_t *nruns,
-                     int nthreads, oracle_counts *counts_out) {
+/* Align pairs [0, n_pairs) with oracle_wfa_ef (free ends pb, pe, tb, te; all
+ * 0 = global) on nthreads POSIX threads (static contiguous chunks).  Pair i
+ * is pat[poff[i] .. +plen[i]) against txt[toff[i] .. +tlen[i]).  If runs !=
+ * NULL the canonical alignment of pair i is written as run-length words to
+ * runs[i*runs_per_pair ...] with the count in nruns[i].  counts_out (may be
+ * NULL) receives the summed work counters.  Returns 0, or a negative error
+ * (-2 memory, -3 runs_per_pair too small). */
+int oracle_wfa_batch_ef(int64_t n_pairs, const char *pat, const int64_t *poff,
+                        const int32_t *plen, const char *txt,
+                        const int64_t *toff, const int32_t *tlen, int64_t x,
+                        int64_t o, int64_t e, int64_t pb, int64_t pe,
+                        int64_t tb, int64_t te, int64_t max_score,
+                        int32_t *scores, int8_t *status, uint32_t *runs,
+                        int64_t runs_per_pair, int32_t *nruns, int nthreads,
+                        oracle_counts *counts_out) {
   if (nthreads < 1) nthreads = 1;
   if (nthreads > 1024) nthreads = 1024;
   batch_job *jobs = calloc((size_t)nthreads, sizeof(batch_job));
@@ -643,6 +771,7 @@ int oracle_wfa_batch(int64_t n_pairs, const char *pat, const int64_t *poff,
     j->pat = pat; j->poff = poff; j->plen = plen;
     j->txt = txt; j->toff = toff; j->tlen = tlen;
     j->x = x; j->o = o; j->e = e; j->max_score = max_score;
+    j->pb = pb; j->pe = pe; j->tb = tb; j->te = te;
     j->want_ops = runs != NULL;
     j->scores = scores; j->status = status;
     j->runs = runs; j->runs_per_pair = runs_per_pair; j->nruns = nruns;
@@ -669,4 +798,16 @@ int oracle_wfa_batch(int64_t n_pairs, const char *pat, const int64_t *poff,
   free(jobs);
   free(th);
   return err;
+}
+
+/* The global alignment of every pair: oracle_wfa_batch_ef with no free ends. */
+int oracle_wfa_batch(int64_t n_pairs, const char *pat, const int64_t *poff,
+                     const int32_t *plen, const char *txt, const int64_t *toff,
+                     const int32_t *tlen, int64_t x, int64_t o, int64_t e,
+                     int64_t max_score, int32_t *scores, int8_t *status,
+                     uint32_t *runs, int64_t runs_per_pair, int32_t *nruns,
+                     int nthreads, oracle_counts *counts_out) {
+  return oracle_wfa_batch_ef(n_pairs, pat, poff, plen, txt, toff, tlen, x, o, e,
+                             0, 0, 0, 0, max_score, scores, status, runs,
+                             runs_per_pair, nruns, nthreads, counts_out);
 }

@@ -302,3 +302,106 @@ def test_batch_matches_single(oracle_mod):
     s1, st1, w1, o1 = oracle_mod.wfa_batch(b, pen, nthreads=1)
     assert np.array_equal(s, s1) and np.array_equal(st, st1)
     assert np.array_equal(words, w1) and np.array_equal(off, o1)
+
+
+# ------------------------------------------------------------ ends-free
+
+ENDS_PENALTIES = [(4, 6, 2), (1, 0, 1), (2, 3, 1), (3, 0, 2)]
+
+
+def check_ends(oracle, p, t, pen, ends):
+    bs, _, _ = oracle.brute(p, t, pen, ends=ends)
+    gs, gops = oracle.gotoh(p, t, pen, ends=ends)
+    st, ws, wops = oracle.wfa(p, t, pen, ends=ends)
+    assert st == oracle.OK
+    assert bs == gs == ws, (p, t, pen, ends, bs, gs, ws)
+    assert wops == gops, (p, t, pen, ends, gops, wops)
+    assert oracle.rescore(p, t, wops, pen, ends=ends) == ws
+    return ws, wops
+
+
+@pytest.mark.parametrize("pen", ENDS_PENALTIES)
+def test_ends_free_brute_force(oracle_mod, pen):
+    """Free leading / trailing pattern and text characters: brute force over
+    every alignment (scored with the free ends), Gotoh with free start and
+    end cells, and WFA with a widened first wavefront and an end test over
+    the free diagonals agree on the score; the two walk-backs give the same
+    alignment, which rescores to that score."""
+    rng = random.Random(sum(pen) * 31 + 7)
+    for _ in range(700):
+        p = "".join(rng.choice("ACGT") for _ in range(rng.randint(0, 6)))
+        t = "".join(rng.choice("ACGT") for _ in range(rng.randint(0, 6)))
+        ends = tuple(rng.randint(0, 4) for _ in range(4))
+        check_ends(oracle_mod, p, t, pen, ends)
+    for _ in range(300):  # repeats: many ties
+        p = "".join(rng.choice("AC") for _ in range(rng.randint(0, 6)))
+        t = "".join(rng.choice("AC") for _ in range(rng.randint(0, 6)))
+        ends = tuple(rng.randint(0, 3) for _ in range(4))
+        check_ends(oracle_mod, p, t, pen, ends)
+
+
+def test_ends_free_zero_is_global(oracle_mod):
+    rng = random.Random(3)
+    for _ in range(300):
+        p = "".join(rng.choice("ACGT") for _ in range(rng.randint(0, 12)))
+        t = "".join(rng.choice("ACGT") for _ in range(rng.randint(0, 12)))
+        for pen in PENALTY_SETS:
+            assert oracle_mod.wfa(p, t, pen, ends=(0, 0, 0, 0)) == oracle_mod.wfa(p, t, pen)
+
+
+def test_ends_free_everything_free(oracle_mod):
+    """Every character may be skipped: the score is 0."""
+    rng = random.Random(4)
+    for _ in range(200):
+        p = "".join(rng.choice("ACGT") for _ in range(rng.randint(0, 20)))
+        t = "".join(rng.choice("ACGT") for _ in range(rng.randint(0, 20)))
+        ends = (len(p), len(p), len(t), len(t))
+        assert oracle_mod.wfa(p, t, (4, 6, 2), ends=ends)[1] == 0
+        assert oracle_mod.gotoh(p, t, (4, 6, 2), want_ops=False, ends=ends)[0] == 0
+
+
+def test_ends_free_semi_global_is_sellers(oracle_mod):
+    """Text ends free, pattern global, unit costs: the score is the least edit
+    distance between the pattern and any substring of the text (Sellers'
+    textbook DP, written here)."""
+
+    def sellers(a, b):
+        prev = [0] * (len(b) + 1)  # any text prefix may be skipped
+        for i in range(1, len(a) + 1):
+            cur = [i] + [0] * len(b)
+            for j in range(1, len(b) + 1):
+                cur[j] = min(prev[j] + 1, cur[j - 1] + 1, prev[j - 1] + (a[i - 1] != b[j - 1]))
+            prev = cur
+        return min(prev)  # any text suffix may be skipped
+
+    rng = random.Random(5)
+    for _ in range(400):
+        p = "".join(rng.choice("ACGT") for _ in range(rng.randint(0, 10)))
+        t = "".join(rng.choice("ACGT") for _ in range(rng.randint(0, 30)))
+        ends = (0, 0, len(t), len(t))
+        st, s, ops = oracle_mod.wfa(p, t, (1, 0, 1), ends=ends)
+        assert s == sellers(p, t), (p, t)
+        assert oracle_mod.gotoh(p, t, (1, 0, 1), want_ops=False, ends=ends)[0] == s
+        assert oracle_mod.rescore(p, t, ops, (1, 0, 1), ends=ends) == s
+
+
+def test_ends_free_swap_symmetry(oracle_mod):
+    """Swapping pattern and text (and their free lengths) keeps the score."""
+    rng = random.Random(6)
+    for _ in range(300):
+        p = "".join(rng.choice("ACGT") for _ in range(rng.randint(0, 15)))
+        t = "".join(rng.choice("ACGT") for _ in range(rng.randint(0, 15)))
+        pb, pe, tb, te = (rng.randint(0, 5) for _ in range(4))
+        a = oracle_mod.wfa(p, t, (4, 6, 2), ends=(pb, pe, tb, te))[1]
+        b = oracle_mod.wfa(t, p, (4, 6, 2), ends=(tb, te, pb, pe))[1]
+        assert a == b
+
+
+def test_ends_free_worked_examples(oracle_mod):
+    """Hand-derived: a pattern that occurs inside the text aligns at cost 0
+    with the flanks as free I runs; a pattern with a 3-base junk prefix and 2
+    free pattern-begin characters pays one 1-base deletion (o + e)."""
+    st, s, ops = oracle_mod.wfa("GATTA", "CCGATTACC", (4, 6, 2), ends=(0, 0, 9, 9))
+    assert s == 0 and ops == "II" + "M" * 5 + "II"
+    st, s, ops = oracle_mod.wfa("TTTGATTACA", "GATTACA", (4, 6, 2), ends=(2, 0, 0, 0))
+    assert s == 8 and ops == "DDD" + "M" * 7
