@@ -120,6 +120,25 @@ int wfa_gpu_create(wfa_gpu_ctx **out, int device, size_t scratch_bytes);
  * stream and must keep it alive while the context uses it. */
 int wfa_gpu_set_stream(wfa_gpu_ctx *ctx, void *stream);
 
+/* Ends-free alignment for the context's later wfa_gpu_align_batch calls
+ * (the paper aligns reads end to end, Sec. I; this is a variant of the
+ * method it cites): up to pattern_begin_free leading and pattern_end_free
+ * trailing pattern characters, and up to text_begin_free leading and
+ * text_end_free trailing text characters, may stay unaligned at no cost.
+ * The alignment starts at (v, 0), v <= pattern_begin_free, or (0, h),
+ * h <= text_begin_free, and ends at (n, h), h >= m - text_end_free, or
+ * (v, m), v >= n - pattern_end_free; a gap after the start or before the
+ * end is paid as usual.  The CIGAR still covers both sequences: skipped
+ * characters are its leading / trailing D (pattern) or I (text) runs.  Of
+ * the optimal end cells, the one on the diagonal k = h - v nearest m - n is
+ * taken, the larger k on a tie.  Example: pattern_* = 0 and text_* >= m
+ * aligns the whole pattern to its best-matching stretch of the text.
+ * All four 0 (the default) is the global alignment.  A CIGAR may take two
+ * runs more than wfa_gpu_cigar_bound() states.  Returns OK, or EINVAL (ctx
+ * NULL, a length negative or above WFA_GPU_MAX_SEQ_LEN).  Host-only. */
+int wfa_gpu_set_ends_free(wfa_gpu_ctx *ctx, int32_t pattern_begin_free, int32_t pattern_end_free,
+                          int32_t text_begin_free, int32_t text_end_free);
+
 /* Align n_pairs independent pairs (paper Sec. I: many read pairs aligned
  * independently, each producing its result; Sec. II workload: 100 bp reads).
  *

@@ -47,6 +47,7 @@ EXPORTS = (
     "wfa_gpu_request_bytes",
     "wfa_gpu_server_destroy",
     "wfa_gpu_short_variant_name",
+    "wfa_gpu_set_ends_free",
 )
 WFA_GPU_NOALLOC_SCRATCH_BYTES = 4 << 20
 WFA_GPU_NOALLOC_MAX_PAIRS = 32768
@@ -141,6 +142,8 @@ def load(path: str = LIB_PATH):
     L.wfa_gpu_destroy.restype = None
     L.wfa_gpu_short_variant_name.argtypes = [vp, ctypes.c_int]
     L.wfa_gpu_short_variant_name.restype = ctypes.c_char_p
+    L.wfa_gpu_set_ends_free.argtypes = [vp, i32, i32, i32, i32]
+    L.wfa_gpu_set_ends_free.restype = ctypes.c_int
     L.wfa_gpu_align_short_noalloc.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, Penalties, i32, vp, vp, vp, i64, vp]
     L.wfa_gpu_align_short_noalloc.restype = ctypes.c_int
     L.wfa_gpu_server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_size_t]
@@ -282,6 +285,13 @@ class Aligner:
 
     def timing(self) -> dict:
         return wfa_gpu_last_timing(self.ctx).as_dict()
+
+    def set_ends_free(self, pattern_begin: int = 0, pattern_end: int = 0, text_begin: int = 0,
+                      text_end: int = 0) -> None:
+        """Ends-free alignment for later calls (all 0: global)."""
+        rc = load().wfa_gpu_set_ends_free(self.ctx, pattern_begin, pattern_end, text_begin, text_end)
+        if rc != WFA_GPU_OK:
+            raise WfaGpuError(rc, "wfa_gpu_set_ends_free")
 
     def variant_name(self, index: int) -> str | None:
         """Name of short-kernel variant `index` (as timing()["short_variant"])."""

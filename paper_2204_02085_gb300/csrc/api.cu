@@ -95,6 +95,8 @@ struct wfa_gpu_ctx {
   // their total is known (merged server calls size their staging with it)
   wfa::CigarSink cig_sink = nullptr;
   void* cig_sink_user = nullptr;
+  // ends-free alignment: free pattern begin / end, text begin / end lengths
+  int32_t ends_free[4] = {0, 0, 0, 0};
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;
   int32_t* arena = nullptr;
@@ -412,7 +414,7 @@ int autotune_short(wfa_gpu_ctx* c, Call& k, const wfa::AlignArgs& a_in, int64_t 
   int s_store[3];
   for (int j = 0; j < 3; ++j) {
     const wfa::ShortVariant& v = c->plan.v[small[j]];
-    s_store[j] = wfa::build_ugeo(tab, v.scap, v.cells, pen);
+    s_store[j] = wfa::build_ugeo(tab, v.scap, v.cells, pen, -std::min(a_in.pb, v.max_len), std::min(a_in.tb, v.max_len));
   }
   const int64_t m = std::min(n, kTuneSample);
   cudaStream_t st = c->stream;
@@ -598,6 +600,10 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
   a.oes = (pen.o + pen.e) / g;
   a.s_cap = max_score > 0 ? max_score / g : INT_MAX;
   a.score_only = score_only ? 1 : 0;
+  a.pb = ctx->ends_free[0];
+  a.pe = ctx->ends_free[1];
+  a.tb = ctx->ends_free[2];
+  a.te = ctx->ends_free[3];
   a.host_seqs = host_seqs ? 1 : 0;
   a.score = d_score;
   a.status = d_status;
@@ -719,6 +725,10 @@ wfa::AlignArgs device_args(wfa_gpu_ctx* c, int64_t n, const char* pat, const int
   a.oes = (pen.o + pen.e) / g;
   a.s_cap = max_score > 0 ? max_score / g : INT_MAX;
   a.score_only = score_only ? 1 : 0;
+  a.pb = c->ends_free[0];
+  a.pe = c->ends_free[1];
+  a.tb = c->ends_free[2];
+  a.te = c->ends_free[3];
   a.score = out_scores;
   a.status = out_status;
   a.nruns = c->nruns.p;
@@ -802,6 +812,8 @@ int graph_key(wfa_gpu_ctx* c, uint64_t* key, int64_t n, const void* const* ptrs,
   for (const void* b : bufs) key[l++] = (uint64_t)(uintptr_t)b;
   key[l++] = c->pool.cap;
   key[l++] = ((uint64_t)(uint32_t)c->teams_medium << 32) | (uint32_t)c->teams_long;
+  key[l++] = ((uint64_t)(uint32_t)c->ends_free[0] << 32) | (uint32_t)c->ends_free[1];
+  key[l++] = ((uint64_t)(uint32_t)c->ends_free[2] << 32) | (uint32_t)c->ends_free[3];
   return l;
 }
 
@@ -915,6 +927,16 @@ int wfa_gpu_align_batch(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const
                        max_score, flags, out_scores, out_status, out_cigars, cap, out_cigar_offsets);
   return align_eager(ctx, n, patterns, pattern_offsets, pattern_lengths, texts, text_offsets, text_lengths, pen,
                      max_score, flags, out_scores, out_status, out_cigars, cap, out_cigar_offsets);
+}
+
+int wfa_gpu_set_ends_free(wfa_gpu_ctx* ctx, int32_t pattern_begin_free, int32_t pattern_end_free,
+                          int32_t text_begin_free, int32_t text_end_free) {
+  if (!ctx) return WFA_GPU_EINVAL;
+  const int32_t v[4] = {pattern_begin_free, pattern_end_free, text_begin_free, text_end_free};
+  for (int32_t x : v)
+    if (x < 0 || x > WFA_GPU_MAX_SEQ_LEN) return WFA_GPU_EINVAL;
+  std::memcpy(ctx->ends_free, v, sizeof v);
+  return WFA_GPU_OK;
 }
 
 const char* wfa_gpu_short_variant_name(const wfa_gpu_ctx* ctx, int index) {

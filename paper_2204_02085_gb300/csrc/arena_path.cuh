@@ -168,19 +168,43 @@ __device__ __forceinline__ Src<typename V::Off> src_of(const V& view, const Geo&
 // are 32-bit words (16 bases).
 template <int WPP, class V>
 __device__ int team_forward(V& view, const uint32_t* pw, const uint32_t* tw, int n, int m, ScaledPen p, int s_cap,
-                            int* flags, int& round, int* s_out) {
+                            const AlignArgs& a, int* flags, int& round, int* s_out, int* k_out, int* h_out) {
   using Off = typename V::Off;
   using T = Team<WPP>;
   constexpr int NUL = NullOf<Off>::value;
   const int r = T::rank();
   const bool leader = (threadIdx.x & 31) == 0;
   const int kf = m - n;
+  // End test of a score on diagonals [lo, lo + w) at block b (every member,
+  // the same answer): the diagonal nearest kf reaching an end cell -- text
+  // end (M == m) on kf .. kf + pe, pattern end (M == n + k) on kf - te ..
+  // kf - 1 -- the larger k on a tie; kf alone for a global alignment.
+  auto reaches_end = [&](int lo, int w, int b) -> bool {
+    const int dmax = max(a.pe, a.te);
+    for (int d = 0; d <= dmax; ++d) {
+      if (d <= a.pe && kf + d >= lo && kf + d < lo + w && view.getM(Geo{lo, w, b}, kf + d - lo) == m) {
+        *k_out = kf + d;
+        *h_out = m;
+        return true;
+      }
+      if (d > 0 && d <= a.te && kf - d >= lo && kf - d < lo + w && view.getM(Geo{lo, w, b}, kf - d - lo) == m - d) {
+        *k_out = kf - d;
+        *h_out = m - d;
+        return true;
+      }
+    }
+    return false;
+  };
+  // score 0: the free starts, diagonals -min(pb, n) .. min(tb, m) (0 alone
+  // for a global alignment), M_0[k] = extend(max(k, 0))
+  const int lo0 = -min(a.pb, n), hi0 = min(a.tb, m), w0 = hi0 - lo0 + 1;
   int top = 0, b0 = 0;
-  if (!view.alloc(0, 1, top, b0)) return kFwdOverflow;
-  if (r == 0) view.put(b0, 1, 0, extend_diag32(pw, tw, n, m, 0, 0, 1), NUL, NUL);
-  if (leader) view.set_meta(0, 0, 0, b0, 1);
+  if (!view.alloc(0, w0, top, b0)) return kFwdOverflow;
+  for (int k = lo0 + r; k <= hi0; k += T::kSize)
+    view.put(b0, w0, k - lo0, extend_diag32(pw, tw, n, m, k, k > 0 ? k : 0, 1), NUL, NUL);
+  if (leader) view.set_meta(0, lo0, hi0, b0, 1);
   T::sync();
-  if (kf == 0 && view.getM(Geo{0, 1, b0}, 0) == m) {
+  if (reaches_end(lo0, w0, b0)) {
     *s_out = 0;
     return kFwdOk;
   }
@@ -235,7 +259,7 @@ __device__ int team_forward(V& view, const uint32_t* pw, const uint32_t* tw, int
     if (exbits == 0) view.release(b, top);
     if (leader) view.set_meta(s, lo, hi, b, exbits);
     __syncwarp();
-    if ((exbits & 1) && kf >= lo && kf <= hi && view.getM(Geo{lo, w, b}, kf - lo) == m) {
+    if ((exbits & 1) && reaches_end(lo, w, b)) {
       *s_out = s;
       return kFwdOk;
     }
@@ -283,7 +307,7 @@ __device__ __forceinline__ void overflow_pair_to(const AlignArgs& a, int64_t pai
 // score its CIGAR, backtraced into a reservation of the run pool.
 template <class V>
 __device__ void finish_cigar(const AlignArgs& a, const V& view, int64_t pair, int n, int m, ScaledPen pen, int res,
-                             int s, int32_t* overflow_count) {
+                             int s, int k_end, int h_end, int32_t* overflow_count) {
   if (res == kFwdOverflow) {
     overflow_pair_to(a, pair, overflow_count);
     return;
@@ -301,7 +325,7 @@ __device__ void finish_cigar(const AlignArgs& a, const V& view, int64_t pair, in
     return;
   }
   const int64_t src = -(int64_t)pos - 1;  // negative: an index into the pool
-  const int nr = wfa_backtrace(view, n, m, pen, s, a.pool + pos, (int)bound);
+  const int nr = wfa_backtrace(view, n, m, pen, s, k_end, h_end, a.pool + pos, (int)bound);
   if (nr < 0) {
     atomicExch(&a.ctrl->internal_error, 1);
     write_result(a, pair, 0, s * a.g, 0, src);
@@ -364,7 +388,7 @@ __device__ void arena_body(const AlignArgs& a, const int32_t* list, const int32_
       continue;
     }
     unsigned char* wf = slot + seq_bytes;
-    int s = 0, res;
+    int s = 0, res, k_end = m - n, h_end = m;
     const bool small = n < 32000 && m < 32000;
     if (a.score_only) {
       const int R = max(pen.x, max(pen.oe, pen.e)) + 1;
@@ -374,10 +398,10 @@ __device__ void arena_body(const AlignArgs& a, const int32_t* list, const int32_
         res = kFwdOverflow;
       } else if (small) {
         RingView<int16_t> v{reinterpret_cast<int32_t*>(wf), reinterpret_cast<int16_t*>(wf + 16L * R), R, W};
-        res = team_forward<WPP>(v, pw, tw, n, m, pen, a.s_cap, ts->flags, round, &s);
+        res = team_forward<WPP>(v, pw, tw, n, m, pen, a.s_cap, a, ts->flags, round, &s, &k_end, &h_end);
       } else {
         RingView<int32_t> v{reinterpret_cast<int32_t*>(wf), reinterpret_cast<int32_t*>(wf + 16L * R), R, W};
-        res = team_forward<WPP>(v, pw, tw, n, m, pen, a.s_cap, ts->flags, round, &s);
+        res = team_forward<WPP>(v, pw, tw, n, m, pen, a.s_cap, a, ts->flags, round, &s, &k_end, &h_end);
       }
       if (r == 0) {
         if (res == kFwdOverflow) overflow_pair_to(a, pair, overflow_count);
@@ -388,12 +412,12 @@ __device__ void arena_body(const AlignArgs& a, const int32_t* list, const int32_
       const long cap = room & ~15L;
       if (small) {
         ArenaViewT<int16_t> v{reinterpret_cast<int32_t*>(wf), reinterpret_cast<int16_t*>(wf + cap), cap};
-        res = team_forward<WPP>(v, pw, tw, n, m, pen, a.s_cap, ts->flags, round, &s);
-        if (r == 0) finish_cigar(a, v, pair, n, m, pen, res, s, overflow_count);
+        res = team_forward<WPP>(v, pw, tw, n, m, pen, a.s_cap, a, ts->flags, round, &s, &k_end, &h_end);
+        if (r == 0) finish_cigar(a, v, pair, n, m, pen, res, s, k_end, h_end, overflow_count);
       } else {
         ArenaViewT<int32_t> v{reinterpret_cast<int32_t*>(wf), reinterpret_cast<int32_t*>(wf + cap), cap};
-        res = team_forward<WPP>(v, pw, tw, n, m, pen, a.s_cap, ts->flags, round, &s);
-        if (r == 0) finish_cigar(a, v, pair, n, m, pen, res, s, overflow_count);
+        res = team_forward<WPP>(v, pw, tw, n, m, pen, a.s_cap, a, ts->flags, round, &s, &k_end, &h_end);
+        if (r == 0) finish_cigar(a, v, pair, n, m, pen, res, s, k_end, h_end, overflow_count);
       }
     }
     T::sync();

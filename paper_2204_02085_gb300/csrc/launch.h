@@ -41,6 +41,9 @@ struct AlignArgs {
   int s_cap;        // largest scaled score reported (INT_MAX: none)
   int score_only;
   int host_seqs;  // sequences read in place from page-locked host memory
+  // ends-free alignment: free leading / trailing pattern (pb, pe) and text
+  // (tb, te) characters; all 0 for a global alignment
+  int pb, pe, tb, te;
   int32_t* score;
   int8_t* status;
   int32_t* nruns;

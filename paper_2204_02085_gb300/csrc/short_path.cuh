@@ -155,9 +155,12 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
   const int lane = lane32 & (G - 1), q = lane32 / G;
   auto* W = reinterpret_cast<typename C::WarpShm*>(smem + C::kTabBytes + warp * C::kWarpBytes);
   const ScaledPen pen{a.xs, a.oes, a.es};
-  if (threadIdx.x == 0) s_last = build_ugeo(tab, SCAP, CELLS, pen);
+  // the first wavefront spans the free starts (diagonal 0 alone for a
+  // global alignment)
+  const int lo0 = -min(a.pb, LMAX), hi0 = min(a.tb, LMAX);
+  if (threadIdx.x == 0) s_last = build_ugeo(tab, SCAP, CELLS, pen, lo0, hi0);
   __syncthreads();
-  const int s_store = s_last;
+  const int s_store = s_last;  // -1: the first wavefront does not fit
   const int s_hi = min(s_store, a.s_cap);
   const unsigned gmask = group_mask(G);
   UView<Off, P> view{tab, W->M, W->I, W->D, q};
@@ -173,7 +176,7 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
     if (active) {
       n = a.plen[pair];
       m = a.tlen[pair];
-      if (n > LMAX || m > LMAX) {
+      if (n > LMAX || m > LMAX || s_store < 0) {
         if (lane == 0) defer_pair(a, pair);
         active = false;
       }
@@ -196,17 +199,29 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
     }
     __syncwarp();
     const int kf = m - n;
-    int s_fin = -1;
-    if (active && lane == 0) {
-      const int h0 = extend_diag32(pw, tw, n, m, 0, 0, PS);
-      if constexpr (LIN) W->M[q] = (Off)h0;  // no I/D store under the gap-linear model
-      else view.put(0, 0, h0, NUL, NUL);
-    }
-    __syncwarp();
-    if (active && kf == 0 && view.getM(Geo{0, 1, 0}, 0) == m) {
-      s_fin = 0;
-      active = false;
-    }
+    int s_fin = -1, k_end = kf, h_end = m;
+    // End test of a score (every lane of the pair, the same answer): the
+    // diagonal nearest kf whose offset reaches an end cell -- the text end
+    // (M == m) on kf .. kf + pe, the pattern end (M == n + k) on kf - te ..
+    // kf - 1 -- the larger k on a tie; kf alone for a global alignment.
+    auto reaches_end = [&](const UGeo& g) -> bool {
+      const int dmax = max(a.pe, a.te);
+      for (int d = 0; d <= dmax; ++d) {
+        if (d <= a.pe && kf + d >= g.lo && kf + d < g.lo + g.w &&
+            view.getM(Geo{g.lo, g.w, g.base}, kf + d - g.lo) == m) {
+          k_end = kf + d;
+          h_end = m;
+          return true;
+        }
+        if (d > 0 && d <= a.te && kf - d >= g.lo && kf - d < g.lo + g.w &&
+            view.getM(Geo{g.lo, g.w, g.base}, kf - d - g.lo) == m - d) {
+          k_end = kf - d;
+          h_end = m - d;
+          return true;
+        }
+      }
+      return false;
+    };
     // The running pairs share the warp's lanes: at each score the cells of
     // all of them are spread over the 32 lanes, pair index fastest (cell
     // (i, j) of the j-th running pair is item i * na + j), so a pair that has
@@ -220,6 +235,36 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
       __syncwarp();
     };
     relist();
+    {
+      // score 0: M_0[k] = extend(max(k, 0)) on the first wavefront's
+      // diagonals that start inside both sequences
+      const UGeo g0 = tab[0];
+      const int items = na * g0.w;
+      for (int f = lane32; f < items; f += 32) {
+        const int i = na > 1 ? (int)__umulhi((unsigned)f, inv_na) : f;
+        const int r = W->act[f - i * na];
+        const int rn = W->nl[r], rm = W->ml[r], k = g0.lo + i;
+        int h = NUL;
+        if (k <= rm && -k <= rn) h = extend_diag32(W->pw + r, W->tw + r, rn, rm, k, k > 0 ? k : 0, PS);
+        const int c = (g0.base + i) * P + r;
+        W->M[c] = (Off)h;
+        if constexpr (!LIN) {
+          W->I[c] = (Off)NUL;
+          W->D[c] = (Off)NUL;
+        }
+      }
+      __syncwarp();
+      if (active && reaches_end(g0)) {
+        s_fin = 0;
+        active = false;
+      }
+      const unsigned now = __ballot_sync(FULL, active && lane == 0);
+      if (now != amask) {
+        amask = now;
+        na = __popc(amask);
+        relist();
+      }
+    }
     for (int s = 1; s <= s_hi && na > 0; ++s) {
       const UGeo g = tab[s];
       if (!g.ex) continue;
@@ -234,7 +279,7 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
         c.store(W->M, W->I, W->D, g);
       }
       __syncwarp();
-      if (active && kf >= g.lo && kf < g.lo + g.w && view.getM(Geo{g.lo, g.w, g.base}, kf - g.lo) == m) {
+      if (active && reaches_end(g)) {
         s_fin = s;
         active = false;
       }
@@ -259,9 +304,9 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
           int nr;
           if constexpr (LIN) {
             LinUView<Off, P> lv{view, n, m, pen.e};
-            nr = wfa_backtrace(lv, n, m, pen, s_fin, a.runs + src, kSlot);
+            nr = wfa_backtrace(lv, n, m, pen, s_fin, k_end, h_end, a.runs + src, kSlot);
           } else {
-            nr = wfa_backtrace(view, n, m, pen, s_fin, a.runs + src, kSlot);
+            nr = wfa_backtrace(view, n, m, pen, s_fin, k_end, h_end, a.runs + src, kSlot);
           }
           if (nr == -1) {
             defer_pair(a, pair);  // more runs than a slot holds

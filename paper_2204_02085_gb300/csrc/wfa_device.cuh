@@ -443,17 +443,20 @@ struct UGeo {
   uint8_t ex, pad;
 };
 
-// Fill tab[0..scap] for penalties p; wavefronts whose cells would pass
-// cellcap are marked absent and the last storable score is returned.
-__host__ __device__ inline int build_ugeo(UGeo* tab, int scap, int cellcap, ScaledPen p) {
+// Fill tab[0..scap] for penalties p and a first wavefront on diagonals
+// lo0 .. hi0; wavefronts whose cells would pass cellcap are marked absent
+// and the last storable score is returned (-1: not even the first).
+__host__ __device__ inline int build_ugeo(UGeo* tab, int scap, int cellcap, ScaledPen p, int lo0 = 0,
+                                          int hi0 = 0) {
   int top = 0, last = scap;
   for (int s = 0; s <= scap; ++s) {
     UGeo g{0, 0, 0, 0, 0};
     int lo = 1 << 14, hi = -(1 << 14);
     bool exM = false, exG = false;
     if (s == 0) {
-      exM = true;
-      lo = hi = 0;
+      exM = true;  // diagonals lo0 .. hi0: the free starts (0 .. 0: global)
+      lo = lo0;
+      hi = hi0;
     } else {
       const bool eX = s - p.x >= 0 && (tab[s - p.x].ex & 1);
       const bool eO = s - p.oe >= 0 && (tab[s - p.oe].ex & 1);
@@ -619,15 +622,21 @@ __device__ __forceinline__ int bt_D(const V& view, int s, int k) {
   return get_off<V, 2>(view, geo_of(view, s, 4), k, NullOf<typename V::Off>::value);
 }
 
-// Walk back from (M, s_final, m-n, m) and write run-length CIGAR words into
-// runs[0 ..), LAST run first.  Returns the number of runs, -1 if more than
-// cap runs are needed, -2 if the stored wavefronts are inconsistent (which
-// the forward pass never produces).  Single lane.
+// Walk back from the end cell (M, s_final, k_end, h_end) -- (m-n, m) for a
+// global alignment -- and write run-length CIGAR words into runs[0 ..), LAST
+// run first.  Under ends-free alignment the characters past the end cell
+// come out first (D run if k_end > m-n, I run if k_end < m-n), and the walk
+// stops at score 0 on any diagonal k of the first wavefront: matches back to
+// the free start (0, k) or (-k, 0), then its skipped prefix (I or D run).
+// Returns the number of runs, -1 if more than cap runs are needed, -2 if the
+// stored wavefronts are inconsistent (which the forward pass never
+// produces).  Single lane.
 template <class V>
-__device__ int wfa_backtrace(const V& view, int n, int m, ScaledPen p, int s_final, uint32_t* runs, int cap) {
+__device__ int wfa_backtrace(const V& view, int n, int m, ScaledPen p, int s_final, int k_end, int h_end,
+                             uint32_t* runs, int cap) {
   using Off = typename V::Off;
   constexpr int NUL = NullOf<Off>::value;
-  int s = s_final, k = m - n, h = m, state = kOpM;
+  int s = s_final, k = k_end, h = h_end, state = kOpM;
   uint32_t cur_op = 0xF, cur_len = 0;
   int nr = 0;
   long guard = 2L * ((long)n + (long)m) + 4;
@@ -645,12 +654,19 @@ __device__ int wfa_backtrace(const V& view, int n, int m, ScaledPen p, int s_fin
     cur_op = op;
     cur_len = len;
   };
+  // free end: the characters past the end cell
+  if (k_end > m - n) emit(kOpD, (uint32_t)(k_end - (m - n)));
+  if (k_end < m - n) emit(kOpI, (uint32_t)((m - n) - k_end));
   while (guard-- > 0) {
     if (s < 0) return -2;
     if (state == kOpM) {
       if (s == 0) {
-        if (k != 0) return -2;
-        emit(kOpM, (uint32_t)h);
+        // a start on diagonal k: (0, k) or (-k, 0), then matches to h
+        const int h0 = k > 0 ? k : 0;
+        if (h < h0 || k > m || -k > n) return -2;
+        emit(kOpM, (uint32_t)(h - h0));
+        if (k > 0) emit(kOpI, (uint32_t)k);
+        if (k < 0) emit(kOpD, (uint32_t)(-k));
         break;
       }
       int xv = get_off<V, 0>(view, geo_of(view, s - p.x, 1), k, NUL);
@@ -714,7 +730,7 @@ __device__ int wfa_backtrace(const V& view, int n, int m, ScaledPen p, int s_fin
 // largest number of CIGAR runs of an alignment of scaled score s
 __host__ __device__ __forceinline__ long runs_bound_scaled(long s, int x, int oe) {
   const int mn = x < oe ? x : oe;
-  return 2L * (s / mn) + 1;
+  return 2L * (s / mn) + 1 + 2;  // + the free end runs of an ends-free alignment
 }
 
 }  // namespace wfa
