@@ -89,7 +89,7 @@ def parse():
     ap.add_argument("--requests", type=int, default=2000, help="requests in the serving trace (config 5)")
     ap.add_argument("--workers", type=int, default=2, help="server slots (config 5)")
     ap.add_argument("--baselines", type=int, default=1, help="config 5: also replay the one-at-a-time baselines")
-    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5],
+    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5, 6],
                     help="2: the paper's 5M x 100 bp workload (default); 3: 1M mixed-length pairs (100-2,000 bp, "
                          "0-10%% edits, tandem repeats); 4: 20k long-read pairs (10 kbp, 1-5%% edits); 5: serving, "
                          "a Poisson stream of requests")
@@ -314,6 +314,84 @@ def run_config(args):
     return 0
 
 
+def run_models(args):
+    """Configuration 6: the other penalty models and ends-free alignment
+    (rank 0 only), device-resident inputs, score + CIGAR: 5M x 100 bp pairs
+    at E=4% (seed 1) under gap-affine 4/6/2, edit distance (1/0/1: the
+    M-only short kernel) and gap-linear 3/0/2; 1M 100 bp reads (3 edits)
+    against reference windows of 100-300 bp (seed 6), global and with the
+    text ends free (semi-global)."""
+    import torch
+
+    import paper_2204_02085_gb300 as pkg
+    from paper_2204_02085_gb300 import build as gpu_build
+    from paper_2204_02085_gb300 import synth
+
+    gpu_build.build()
+    dev = torch.device("cuda:0")
+    n_short = args.pairs if args.pairs != N_PAIRS else N_PAIRS
+    n_win = max(1, n_short // 5)
+    work = {"reads_100bp_E4": synth.uniform_reads(n_short, LENGTH, 4, seed=SEED),
+            "reads_in_windows": synth.reads_in_windows(n_win, 100, 100, 3, seed=6)}
+    runs = [("reads_100bp_E4", "gap_affine_4_6_2", (4, 6, 2), (0, 0, 0, 0)),
+            ("reads_100bp_E4", "edit_distance_1_0_1", (1, 0, 1), (0, 0, 0, 0)),
+            ("reads_100bp_E4", "gap_linear_3_0_2", (3, 0, 2), (0, 0, 0, 0)),
+            ("reads_in_windows", "global_4_6_2", (4, 6, 2), (0, 0, 0, 0)),
+            ("reads_in_windows", "text_ends_free_4_6_2", (4, 6, 2), (0, 0, 300, 300))]
+    stream = torch.cuda.Stream(dev)
+    res = {}
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    with pkg.Aligner(0, scratch_bytes=8 << 30) as al:
+        al.set_stream(stream)
+        for wname, label, pen, ends in runs:
+            b = work[wname]
+            n = b.n
+            d = dict(pat=t(b.patterns), plen=t(b.pattern_lengths), txt=t(b.texts), tlen=t(b.text_lengths),
+                     s=torch.empty(n, dtype=torch.int32, device=dev), st=torch.empty(n, dtype=torch.int8, device=dev),
+                     off=torch.empty(n + 1, dtype=torch.int64, device=dev))
+            al.set_ends_free(*ends)
+            w = torch.empty(1, dtype=torch.int32, device=dev)
+            al.align_device(d["pat"], None, d["plen"], d["txt"], None, d["tlen"], d["s"], d["st"], w, d["off"],
+                            pen=pen)
+            w = torch.empty(int(d["off"][-1]) + 1, dtype=torch.int32, device=dev)
+
+            def call():
+                rc = al.align_device(d["pat"], None, d["plen"], d["txt"], None, d["tlen"], d["s"], d["st"], w,
+                                     d["off"], pen=pen, timing=True)
+                assert rc == pkg.WFA_GPU_OK
+                return al.timing()
+
+            for _ in range(args.warmup):
+                call()
+            torch.cuda.synchronize(dev)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ts = []
+            ev0.record(stream)
+            for _ in range(args.steps):
+                ts.append(call())
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = ev0.elapsed_time(ev1) / args.steps
+            res[label] = {"workload": wname, "pairs": n, "pairs_per_s": n / (ms / 1000.0), "ms_per_call": ms,
+                          "ends_free": ends,
+                          "short_kernel_ms": round(float(np.mean([x["align_ms"] for x in ts])), 3),
+                          "arena_ms": round(float(np.mean([x["general_ms"] for x in ts])), 3),
+                          "short_variant": al.variant_name(int(ts[-1]["short_variant"])),
+                          "deferred_pairs": int(ts[-1]["deferred_pairs"]),
+                          "mean_score": float(d["s"].float().mean().item())}
+            del d
+    main = res["edit_distance_1_0_1"]
+    line = {"metric": "pairs/s (config 6: penalty models, ends-free)", "value": main["pairs_per_s"],
+            "unit": "pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": main["ms_per_call"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "%d x 100 bp pairs at E=4%% under three penalty models; %d 100 bp reads "
+                                   "against 100-300 bp windows, global and text-ends-free" % (n_short, n_win)},
+            "modes": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serving(args):
     """Configuration 5: a Poisson stream of requests (2,000 per second;
     batch sizes log-uniform 1-4,096 pairs; lengths log-uniform 100-5,000 bp;
@@ -437,6 +515,8 @@ def main():
         return run_reference(args)
     if args.config == 5:
         return run_serving(args)
+    if args.config == 6:
+        return run_models(args)
     if args.config != 2:
         return run_config(args)
 

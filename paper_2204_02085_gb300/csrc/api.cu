@@ -112,6 +112,9 @@ struct wfa_gpu_ctx {
   int variants_small[2][3] = {{7, 4, 1}, {8, 9, 9}};
   int variant_big[2] = {1, 9};
   int variant_mid[2] = {6, 10};
+  // ends-free calls, per model: <= 127 bases and <= 255 bases
+  int variant_ef[2] = {11, 13};
+  int variant_ef_mid[2] = {12, 14};
   int variant_forced = -1;  // tuning override (WFA_GPU_SHORT_VARIANT)
   int last_variant = -1;
   wfa::Ctrl* ctrl = nullptr;    // device
@@ -133,6 +136,7 @@ struct wfa_gpu_ctx {
   HostBuf<unsigned char> h_score, h_status, h_off, h_cig;
   // internal
   DevBuf<int32_t> nruns, defer, defer_long, overflow;
+  DevBuf<int32_t> sorted, sorted_long, sort_aux;  // longest-first work lists (batched path)
   DevBuf<int64_t> run_src, scan_tmp;
   DevBuf<uint32_t> runs, pool;
   int64_t pool_words = kPoolInitWords;  // CIGAR words the arena pool holds
@@ -148,6 +152,7 @@ struct wfa_gpu_ctx {
     uint64_t key[40] = {};
     int key_len = 0;
     int variant = -1;
+    int launches = 0;  // kernels captured
   };
   static constexpr int kGraphs = 4;
   Graph graphs[kGraphs];
@@ -326,20 +331,36 @@ int run_retries(wfa_gpu_ctx* c, Call& k, wfa::AlignArgs& a);
 // on one-warp teams, long ones on one-CTA teams), then retries of the pairs
 // that did not fit: fewer, larger arena slices on one-CTA teams, or a larger
 // CIGAR pool.  A pair that does not fit the whole arena gives ENOMEM.
-int run_arena(wfa_gpu_ctx* c, Call& k, wfa::AlignArgs& a) {
+int run_arena(wfa_gpu_ctx* c, Call& k, wfa::AlignArgs& a, bool longest_first) {
   cudaStream_t st = c->stream;
   wfa::Ctrl* hc = c->h_ctrl;
   wfa::Ctrl* dc = c->ctrl;
   const long arena = (long)c->arena_bytes;
+  // batched path: the longest pairs first, so that the last pairs a team
+  // takes are short ones (a shorter tail)
+  const int32_t* medium = a.defer_list;
+  const int32_t* lng = a.defer_long_list;
+  if (longest_first && hc->defer_count > 1) {
+    if (!k.launched(wfa::launch_sort_longest_first(a, a.defer_list, &dc->defer_count, hc->defer_count,
+                                                   c->sort_aux.p, c->sorted.p, st), 3))
+      return WFA_GPU_ECUDA;
+    medium = c->sorted.p;
+  }
+  if (longest_first && hc->defer_long_count > 1) {
+    if (!k.launched(wfa::launch_sort_longest_first(a, a.defer_long_list, &dc->defer_long_count,
+                                                   hc->defer_long_count, c->sort_aux.p, c->sorted_long.p, st), 3))
+      return WFA_GPU_ECUDA;
+    lng = c->sorted_long.p;
+  }
   // no more teams than pairs: small batches leave the GPU to concurrent work
   // and get larger arena slices
   const int tm = std::min<int>(c->teams_medium, hc->defer_count);
   const int tl = std::min<int>(c->teams_long, hc->defer_long_count);
-  if (tm > 0 && !k.launched(wfa::launch_arena(false, a, a.defer_list, &dc->defer_count, &dc->next_medium,
+  if (tm > 0 && !k.launched(wfa::launch_arena(false, a, medium, &dc->defer_count, &dc->next_medium,
                                               &dc->overflow_count, reinterpret_cast<unsigned char*>(c->arena),
                                               (arena / tm) & ~255L, tm, st)))
     return WFA_GPU_ECUDA;
-  if (tl > 0 && !k.launched(wfa::launch_arena(true, a, a.defer_long_list, &dc->defer_long_count, &dc->next_long,
+  if (tl > 0 && !k.launched(wfa::launch_arena(true, a, lng, &dc->defer_long_count, &dc->next_long,
                                               &dc->overflow_count, reinterpret_cast<unsigned char*>(c->arena),
                                               (arena / tl) & ~255L, tl, st)))
     return WFA_GPU_ECUDA;
@@ -406,7 +427,10 @@ constexpr int64_t kTuneSample = 8192;
 // variant index, or -1 on a CUDA error.
 int autotune_short(wfa_gpu_ctx* c, Call& k, const wfa::AlignArgs& a_in, int64_t n) {
   const int model = a_in.oes == a_in.es ? 1 : 0;  // o = 0: gap-linear
-  if (c->variant_forced >= 0 && c->plan.v[c->variant_forced].linear == model) return c->variant_forced;
+  if ((a_in.pb | a_in.pe | a_in.tb | a_in.te) != 0) return c->variant_ef[model];  // ends-free: one variant
+  if (c->variant_forced >= 0 && c->plan.v[c->variant_forced].linear == model &&
+      !c->plan.v[c->variant_forced].ends_free)
+    return c->variant_forced;
   const int* small = c->variants_small[model];
   const int big = c->variant_big[model];
   wfa::UGeo tab[64];
@@ -586,7 +610,9 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
   }
   const int64_t slot_words = score_only ? 1 : n * (int64_t)wfa::kSlot;
   if ((e = ctx->nruns.ensure(n)) || (e = ctx->run_src.ensure(n)) || (e = ctx->defer.ensure(n)) ||
-      (e = ctx->defer_long.ensure(n)) || (e = ctx->overflow.ensure(n)) || (e = ctx->runs.ensure(slot_words)) ||
+      (e = ctx->defer_long.ensure(n)) || (e = ctx->overflow.ensure(n)) || (e = ctx->sorted.ensure(n)) ||
+      (e = ctx->sorted_long.ensure(n)) || (e = ctx->sort_aux.ensure(2 * wfa::kSortBuckets)) ||
+      (e = ctx->runs.ensure(slot_words)) ||
       (e = ctx->pool.ensure(score_only ? 1 : ctx->pool_words)))
     return map_alloc(e);
 
@@ -620,7 +646,8 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
   if (plain) {
     if (!k.launched(wfa::launch_route_all(a, st))) return fail_cuda(k);
   } else {
-    int vi = ctx->variant_mid[pen.o == 0 ? 1 : 0];
+    const bool ef = (a.pb | a.pe | a.tb | a.te) != 0;
+    int vi = ef ? ctx->variant_ef_mid[pen.o == 0 ? 1 : 0] : ctx->variant_mid[pen.o == 0 ? 1 : 0];
     if (ctx->h_ctrl->max_len <= 127) {
       vi = autotune_short(ctx, k, a, n);
       if (vi < 0) return fail_cuda(k);
@@ -633,7 +660,7 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
     return fail_cuda(k);
   ctx->last.deferred_pairs = (int64_t)ctx->h_ctrl->defer_count + ctx->h_ctrl->defer_long_count;
   if (ctx->last.deferred_pairs > 0) {
-    rc = run_arena(ctx, k, a);
+    rc = run_arena(ctx, k, a, !plain);
     if (rc) return rc;
   }
   if (ctx->h_ctrl->internal_error) return WFA_GPU_ECUDA;
@@ -749,7 +776,8 @@ wfa::AlignArgs device_args(wfa_gpu_ctx* c, int64_t n, const char* pat, const int
 int enqueue_device_work(wfa_gpu_ctx* c, Call& k, int64_t n, const char* pat, const int64_t* poff,
                         const int32_t* plen, const char* txt, const int64_t* toff, const int32_t* tlen,
                         wfa_gpu_penalties pen, int32_t max_score, uint32_t flags, int32_t* out_scores,
-                        int8_t* out_status, uint32_t* out_cigars, int64_t cap, int64_t* out_off) {
+                        int8_t* out_status, uint32_t* out_cigars, int64_t cap, int64_t* out_off,
+                        bool longest_first) {
   cudaStream_t st = c->stream;
   const bool score_only = flags & WFA_GPU_SCORE_ONLY;
   // external event records become graph nodes: replays time their phases
@@ -779,9 +807,20 @@ int enqueue_device_work(wfa_gpu_ctx* c, Call& k, int64_t n, const char* pat, con
   const long arena = (long)c->arena_bytes;
   unsigned char* ab = reinterpret_cast<unsigned char*>(c->arena);
   wfa::Ctrl* dc = c->ctrl;
-  if (!k.launched(wfa::launch_arena(false, a, a.defer_list, &dc->defer_count, &dc->next_medium, &dc->overflow_count,
+  const int32_t* medium = a.defer_list;
+  const int32_t* lng = a.defer_long_list;
+  if (longest_first) {  // batched path with many deferred pairs: longest first
+    if (!k.launched(wfa::launch_sort_longest_first(a, a.defer_list, &dc->defer_count, n, c->sort_aux.p,
+                                                   c->sorted.p, st), 3) ||
+        !k.launched(wfa::launch_sort_longest_first(a, a.defer_long_list, &dc->defer_long_count, n, c->sort_aux.p,
+                                                   c->sorted_long.p, st), 3))
+      return WFA_GPU_ECUDA;
+    medium = c->sorted.p;
+    lng = c->sorted_long.p;
+  }
+  if (!k.launched(wfa::launch_arena(false, a, medium, &dc->defer_count, &dc->next_medium, &dc->overflow_count,
                                     ab, (arena / c->teams_medium) & ~255L, c->teams_medium, st)) ||
-      !k.launched(wfa::launch_arena(true, a, a.defer_long_list, &dc->defer_long_count, &dc->next_long,
+      !k.launched(wfa::launch_arena(true, a, lng, &dc->defer_long_count, &dc->next_long,
                                     &dc->overflow_count, ab, (arena / c->teams_long) & ~255L, c->teams_long, st)))
     return WFA_GPU_ECUDA;
   if (!k.ok(cudaEventRecordWithFlags(c->ev[3], st, cudaEventRecordExternal))) return WFA_GPU_ECUDA;
@@ -808,7 +847,8 @@ int graph_key(wfa_gpu_ctx* c, uint64_t* key, int64_t n, const void* const* ptrs,
   key[l++] = (uint64_t)cap;
   key[l++] = (uint64_t)(uintptr_t)c->stream;
   const void* bufs[] = {c->ctrl, c->poff.p, c->toff.p, c->scan_tmp.p, c->nruns.p, c->run_src.p, c->runs.p,
-                        c->pool.p, c->defer.p, c->defer_long.p, c->overflow.p, c->arena};
+                        c->pool.p, c->defer.p, c->defer_long.p, c->overflow.p, c->arena,
+                        c->sorted.p, c->sorted_long.p, c->sort_aux.p};
   for (const void* b : bufs) key[l++] = (uint64_t)(uintptr_t)b;
   key[l++] = c->pool.cap;
   key[l++] = ((uint64_t)(uint32_t)c->teams_medium << 32) | (uint32_t)c->teams_long;
@@ -849,8 +889,11 @@ int align_graph(wfa_gpu_ctx* ctx, int64_t n, const char* pat, const int64_t* pof
     Call k{ctx, false};
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return WFA_GPU_ECUDA;
+    // the longest-first sorts only when the eager run deferred many pairs
+    // (a pure scheduling choice: replays stay correct either way)
+    const bool longest_first = !(flags & WFA_GPU_PLAIN) && eager_timing.deferred_pairs > 1024;
     const int erc = enqueue_device_work(ctx, k, n, pat, poff, plen, txt, toff, tlen, pen, max_score, base,
-                                        out_scores, out_status, out_cigars, cap, out_off);
+                                        out_scores, out_status, out_cigars, cap, out_off, longest_first);
     const cudaError_t ee = cudaStreamEndCapture(st, &g);
     if (erc || ee != cudaSuccess || !g) {
       if (g) cudaGraphDestroy(g);
@@ -863,6 +906,7 @@ int align_graph(wfa_gpu_ctx* ctx, int64_t n, const char* pat, const int64_t* pof
     if (ie != cudaSuccess) return WFA_GPU_ECUDA;
     slot.exec = exec;
     slot.variant = ctx->last_variant;
+    slot.launches = k.launches;
     kl = graph_key(ctx, key, n, ptrs, 10, pen, max_score, flags, cap);
     std::memcpy(slot.key, key, kl * sizeof(uint64_t));
     slot.key_len = kl;
@@ -875,7 +919,7 @@ int align_graph(wfa_gpu_ctx* ctx, int64_t n, const char* pat, const int64_t* pof
   cudaStream_t st = ctx->stream;
   Call k{ctx, (flags & WFA_GPU_TIMING) != 0};
   if (!k.ok(cudaGraphLaunch(hit->exec, st))) return WFA_GPU_ECUDA;
-  k.launches += score_only ? 10 : 14;
+  k.launches += hit->launches;  // the kernels the graph holds
   int64_t total = 0;
   if (!k.ok(d2h(ctx->h_ctrl, ctx->ctrl, sizeof(wfa::Ctrl), st))) return WFA_GPU_ECUDA;
   if (!score_only && !k.ok(d2h(ctx->h_total, out_off + n, sizeof(int64_t), st))) return WFA_GPU_ECUDA;
@@ -1062,6 +1106,7 @@ void wfa_gpu_destroy(wfa_gpu_ctx* c) {
   c->poff.release(); c->toff.release(); c->score.release(); c->status.release();
   c->cig_off.release(); c->cig.release(); c->nruns.release(); c->defer.release();
   c->overflow.release(); c->run_src.release(); c->scan_tmp.release(); c->runs.release();
+  c->sorted.release(); c->sorted_long.release(); c->sort_aux.release();
   c->defer_long.release(); c->pool.release();
   c->h_score.release(); c->h_status.release(); c->h_off.release(); c->h_cig.release();
   if (c->arena) cudaFree(c->arena);

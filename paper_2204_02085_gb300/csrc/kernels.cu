@@ -22,11 +22,11 @@ namespace {
 
 // ------------------------------------------------------------ short kernel
 
-template <int G, int LMAX, int CELLS, int SCAP, typename Off, bool LIN>
+template <int G, int LMAX, int CELLS, int SCAP, typename Off, bool LIN, bool EF>
 __global__ void __launch_bounds__(kShortBlock, 8) short_kernel(const AlignArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_last;
-  short_body<G, LMAX, CELLS, SCAP, Off, LIN>(a, smem, &s_last);
+  short_body<G, LMAX, CELLS, SCAP, Off, LIN, EF>(a, smem, &s_last);
 }
 
 // ----------------------------------------------------------- arena kernels
@@ -199,6 +199,45 @@ __global__ void __launch_bounds__(kAuxBlock) pack_kernel(int64_t n, const char* 
   }
 }
 
+// ------------------------------------------------ longest-first work order
+
+__device__ __forceinline__ int len_bucket(const AlignArgs& a, int32_t pair, int max_len) {
+  const int L = max(a.plen[pair], a.tlen[pair]);
+  const int b = (int)(((long long)L * kSortBuckets) / ((long long)max_len + 1));
+  return b < kSortBuckets ? b : kSortBuckets - 1;
+}
+
+__global__ void sort_hist_kernel(const AlignArgs a, const int32_t* list, const int32_t* count, int32_t* hist) {
+  __shared__ int h[kSortBuckets];
+  for (int i = threadIdx.x; i < kSortBuckets; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  const int n = *count, ml = a.ctrl->max_len;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    atomicAdd(&h[len_bucket(a, list[i], ml)], 1);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kSortBuckets; i += blockDim.x)
+    if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// bucket starts, longest bucket first (one thread: 64 buckets)
+__global__ void sort_scan_kernel(const int32_t* hist, int32_t* cursor) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int at = 0;
+  for (int b = kSortBuckets - 1; b >= 0; --b) {
+    cursor[b] = at;
+    at += hist[b];
+  }
+}
+
+__global__ void sort_scatter_kernel(const AlignArgs a, const int32_t* list, const int32_t* count, int32_t* cursor,
+                                    int32_t* out) {
+  const int n = *count, ml = a.ctrl->max_len;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int32_t p = list[i];
+    out[atomicAdd(&cursor[len_bucket(a, p, ml)], 1)] = p;
+  }
+}
+
 int sm_count(int device) {
   int v = 0;
   cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
@@ -223,10 +262,10 @@ int current_device() {
 
 namespace {
 
-template <int G, int LMAX, int CELLS, int SCAP, typename Off, bool LIN = false>
+template <int G, int LMAX, int CELLS, int SCAP, typename Off, bool LIN = false, bool EF = false>
 cudaError_t plan_one(int device, ShortVariant* v, const char* name) {
   using C = ShortCfg<G, LMAX, CELLS, SCAP, Off, LIN>;
-  auto k = short_kernel<G, LMAX, CELLS, SCAP, Off, LIN>;
+  auto k = short_kernel<G, LMAX, CELLS, SCAP, Off, LIN, EF>;
   const int warps = kShortBlock / 32;
   const size_t smem = C::smem_bytes(warps);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -245,6 +284,7 @@ cudaError_t plan_one(int device, ShortVariant* v, const char* name) {
   v->cells = CELLS;
   v->scap = SCAP;
   v->linear = LIN ? 1 : 0;
+  v->ends_free = EF ? 1 : 0;
   return cudaSuccess;
 }
 
@@ -267,6 +307,14 @@ cudaError_t short_plan(int device, ShortPlan* plan) {
   if ((e = plan_one<1, 127, 64, 15, int8_t, true>(device, &plan->v[i++], "g1_l127_c64_lin"))) return e;
   if ((e = plan_one<2, 127, 256, 31, int8_t, true>(device, &plan->v[i++], "g2_l127_c256_lin"))) return e;
   if ((e = plan_one<2, 255, 256, 31, int16_t, true>(device, &plan->v[i++], "g2_l255_c256_lin_i16"))) return e;
+  // ends-free calls (first wavefront over the free starts, end test over the
+  // free diagonals)
+  if ((e = plan_one<2, 127, 208, 31, int8_t, false, true>(device, &plan->v[i++], "g2_l127_c208_i8_ef"))) return e;
+  if ((e = plan_one<4, 255, 208, 31, int16_t, false, true>(device, &plan->v[i++], "g4_l255_c208_i16_ef")))
+    return e;
+  if ((e = plan_one<2, 127, 256, 31, int8_t, true, true>(device, &plan->v[i++], "g2_l127_c256_lin_ef"))) return e;
+  if ((e = plan_one<2, 255, 256, 31, int16_t, true, true>(device, &plan->v[i++], "g2_l255_c256_lin_i16_ef")))
+    return e;
   plan->count = i;
   // the one-CTA arena kernel keeps two sequences of up to 32,768 bases in
   // shared memory
@@ -325,6 +373,18 @@ cudaError_t launch_arena(bool long_team, const AlignArgs& a, const int32_t* list
     arena_kernel<8><<<nteams, 256, smem, st>>>(a, list, count, next, overflow_count, arena, slot_bytes, nteams,
                                               seq_words);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort_longest_first(const AlignArgs& a, const int32_t* list, const int32_t* count, int64_t n_cap,
+                                      int32_t* aux, int32_t* out, cudaStream_t st) {
+  if (n_cap <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(aux, 0, kSortBuckets * sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(aux_grid(n_cap, current_device()), 2 * sm_count(current_device()));
+  sort_hist_kernel<<<grid, kAuxBlock, 0, st>>>(a, list, count, aux);
+  sort_scan_kernel<<<1, 32, 0, st>>>(aux, aux + kSortBuckets);
+  sort_scatter_kernel<<<grid, kAuxBlock, 0, st>>>(a, list, count, aux + kSortBuckets, out);
   return cudaGetLastError();
 }
 

@@ -75,9 +75,10 @@ struct ShortVariant {
   int cells;    // wavefront cells stored per pair
   int scap;     // largest score index of the geometry table
   int linear;   // 1: gap-linear model only (o = 0; M stored, I and D derived)
+  int ends_free;  // 1: for ends-free calls only
 };
 struct ShortPlan {
-  ShortVariant v[12];
+  ShortVariant v[16];
   int count;
 };
 cudaError_t short_plan(int device, ShortPlan* plan);
@@ -95,6 +96,16 @@ cudaError_t arena_occupancy(bool long_team, int* teams_per_sm);
 cudaError_t launch_arena(bool long_team, const AlignArgs& a, const int32_t* list, const int32_t* count,
                          int32_t* next, int32_t* overflow_count, unsigned char* arena, long slot_bytes, int nteams,
                          cudaStream_t st);
+
+// Longest-first order of a work list (batched path): list[0 .. *count) ->
+// out, by the longer sequence of each pair in kSortBuckets equal-width
+// buckets over [0, ctrl->max_len], longest bucket first (order inside a
+// bucket unspecified).  aux: 2 * kSortBuckets ints of scratch.  n_cap bounds
+// *count (sizes the grid).  Reads the count on the device, so it can be
+// captured into a graph.
+constexpr int kSortBuckets = 64;
+cudaError_t launch_sort_longest_first(const AlignArgs& a, const int32_t* list, const int32_t* count, int64_t n_cap,
+                                      int32_t* aux, int32_t* out, cudaStream_t st);
 
 // Validate lengths / offsets, record max(offset + length) extents.
 cudaError_t launch_validate(int64_t n, const int64_t* poff, const int32_t* plen, const int64_t* toff,

@@ -140,8 +140,10 @@ __device__ __forceinline__ int bt_D(const LinUView<Off, P>& v, int s, int k) {
 // CIGAR runs (last first) into the pair's slot.  Pairs longer than LMAX, or
 // whose score passes the last storable wavefront (but not the caller's
 // max_score), are deferred to the arena kernel.  LIN: the gap-linear model
-// (o = 0, the edit distance at x = e = 1), only M stored.
-template <int G, int LMAX, int CELLS, int SCAP, typename Off, bool LIN = false>
+// (o = 0, the edit distance at x = e = 1), only M stored.  EF: ends-free
+// calls (free pattern / text ends; the first wavefront spans the free
+// starts, the end test scans the free diagonals).
+template <int G, int LMAX, int CELLS, int SCAP, typename Off, bool LIN = false, bool EF = false>
 __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* smem, int* s_last_shared) {
   using C = ShortCfg<G, LMAX, CELLS, SCAP, Off, LIN>;
   constexpr int P = C::P;
@@ -157,10 +159,13 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
   const ScaledPen pen{a.xs, a.oes, a.es};
   // the first wavefront spans the free starts (diagonal 0 alone for a
   // global alignment)
-  const int lo0 = -min(a.pb, LMAX), hi0 = min(a.tb, LMAX);
+  const int lo0 = EF ? -min(a.pb, LMAX) : 0, hi0 = EF ? min(a.tb, LMAX) : 0;
+  constexpr bool ends_free = EF;  // the variant for ends-free calls
   if (threadIdx.x == 0) s_last = build_ugeo(tab, SCAP, CELLS, pen, lo0, hi0);
   __syncthreads();
-  const int s_store = s_last;  // -1: the first wavefront does not fit
+  // -1: the first wavefront does not fit; also when a global variant is
+  // handed an ends-free call (then the arena kernels take every pair)
+  const int s_store = (!EF && (a.pb | a.pe | a.tb | a.te) != 0) ? -1 : s_last;
   const int s_hi = min(s_store, a.s_cap);
   const unsigned gmask = group_mask(G);
   UView<Off, P> view{tab, W->M, W->I, W->D, q};
@@ -234,8 +239,23 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
       inv_na = na > 1 ? 0xffffffffu / (unsigned)na + 1u : 0u;
       __syncwarp();
     };
-    relist();
-    {
+    if constexpr (!ends_free) {
+      // global alignment: score 0 is diagonal 0 alone, one lane per pair
+      if (active && lane == 0) {
+        const int h0 = extend_diag32(pw, tw, n, m, 0, 0, PS);
+        if constexpr (LIN) W->M[q] = (Off)h0;
+        else view.put(0, 0, h0, NUL, NUL);
+      }
+      __syncwarp();
+      if (active && kf == 0 && view.getM(Geo{0, 1, 0}, 0) == m) {
+        s_fin = 0;
+        active = false;
+      }
+      amask = __ballot_sync(FULL, active && lane == 0);
+      na = __popc(amask);
+      relist();
+    } else {
+      relist();
       // score 0: M_0[k] = extend(max(k, 0)) on the first wavefront's
       // diagonals that start inside both sequences
       const UGeo g0 = tab[0];
@@ -279,7 +299,10 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
         c.store(W->M, W->I, W->D, g);
       }
       __syncwarp();
-      if (active && reaches_end(g)) {
+      bool done;
+      if constexpr (ends_free) done = active && reaches_end(g);
+      else done = active && kf >= g.lo && kf < g.lo + g.w && view.getM(Geo{g.lo, g.w, g.base}, kf - g.lo) == m;
+      if (done) {
         s_fin = s;
         active = false;
       }

@@ -264,3 +264,39 @@ def from_pairs(pairs) -> Batch:
         np.cumsum(pl[:-1], out=poff[1:])
         np.cumsum(tl[:-1], out=toff[1:])
     return Batch(pat, poff, pl, txt, toff, tl)
+
+
+def reads_in_windows(n_pairs: int, read_len: int = 100, flank: int = 100, n_edits: int = 3,
+                     seed: int = 6) -> Batch:
+    """Reads against reference windows (the shape of ends-free / semi-global
+    alignment): pattern = `read_len` uniform bases; text = a uniform left
+    flank of U{0..flank} bases + the read after `n_edits` sequential edits
+    (the generator of uniform_reads) + a uniform right flank of U{0..flank}
+    bases.  Draws: the uniform_reads batch (seed), then from PCG64(seed + 1)
+    the left flank lengths, the right flank lengths, the left flank bases and
+    the right flank bases, each as one array."""
+    core = uniform_reads(n_pairs, read_len, n_edits, seed=seed)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    left = rng.integers(0, flank + 1, size=n_pairs).astype(np.int64)
+    right = rng.integers(0, flank + 1, size=n_pairs).astype(np.int64)
+    lb = ALPHABET[rng.integers(0, 4, size=int(left.sum()))]
+    rb = ALPHABET[rng.integers(0, 4, size=int(right.sum()))]
+    el = core.pattern_lengths.astype(np.int64)  # the edited read (uniform_reads' pattern)
+    tl = left + el + right
+    toff = np.zeros(n_pairs, dtype=np.int64)
+    if n_pairs > 1:
+        np.cumsum(tl[:-1], out=toff[1:])
+    txt = np.empty(int(tl.sum()), dtype=np.uint8)
+
+    def place(dst_start, src, lengths):
+        src_off = np.zeros(n_pairs, dtype=np.int64)
+        if n_pairs > 1:
+            np.cumsum(lengths[:-1], out=src_off[1:])
+        pos = np.repeat(dst_start - src_off, lengths) + np.arange(int(lengths.sum()), dtype=np.int64)
+        txt[pos] = src
+
+    place(toff, lb, left)
+    place(toff + left, core.patterns, el)
+    place(toff + left + el, rb, right)
+    return Batch(np.ascontiguousarray(core.texts), core.text_offsets.copy(), core.text_lengths.copy(), txt, toff,
+                 tl.astype(np.int32))

@@ -54,3 +54,17 @@ def test_from_pairs_and_subset():
     assert [b.pair(i) for i in range(3)] == pairs
     s = b.subset([2, 0])
     assert [s.pair(i) for i in range(2)] == [pairs[2], pairs[0]]
+
+
+def test_reads_in_windows_shape_and_determinism():
+    from paper_2204_02085_gb300 import synth
+
+    a = synth.reads_in_windows(300, 100, 50, 3, seed=11)
+    b = synth.reads_in_windows(300, 100, 50, 3, seed=11)
+    assert a.sha256() == b.sha256()
+    core = synth.uniform_reads(300, 100, 3, seed=11)
+    for i in range(a.n):
+        read, window = a.pair(i)
+        edited, original = core.pair(i)
+        assert read == original and len(read) == 100
+        assert edited in window and len(edited) <= len(window) <= len(edited) + 100
