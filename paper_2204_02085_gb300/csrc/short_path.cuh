@@ -47,8 +47,8 @@ struct ShortCfg {
     Off M[CELLS * P];
     Off I[LIN ? 4 : CELLS * P];  // gap-linear model: I and D follow from M
     Off D[LIN ? 4 : CELLS * P];
-    int16_t nl[P], ml[P];  // pair lengths, readable by every lane
-    uint8_t act[P];        // slots of the pairs still running, ascending
+    // the pairs still running, ascending slot: slot | n << 8 | m << 20
+    uint32_t act[P];
   };
   // the packer's span scratch (the raw bytes of up to P back-to-back
   // sequences, 16-byte chunks) borrows the cell arrays, unused while
@@ -63,33 +63,47 @@ struct ShortCfg {
   static constexpr size_t smem_bytes(int warps) { return kTabBytes + (size_t)warps * kWarpBytes; }
 };
 
-// One wavefront cell of the flattened score loop: item f of na running
+// A source wavefront of one score step: cell (k, slot r) of its stored
+// component lies at row0 + k * P + r, for diagonals lo <= k < lo + w.
+struct SrcRow {
+  int row0, lo;
+  unsigned w;
+};
+template <int P>
+__device__ __forceinline__ SrcRow src_row(const Geo& g) {
+  return SrcRow{(g.base - g.lo) * P, g.lo, (unsigned)g.w};
+}
+
+// One wavefront cell of the shared-lane score loop: item f of na running
 // pairs (pair index fastest) at the score whose geometry is g; load()
 // gathers its sources and applies the recurrences (the mismatch, insertion
 // and deletion candidates, each null past the sequence ends) giving the
 // offset h to extend, store() writes M, I and D.
 template <typename Off, int P, bool LIN = false>
 struct Cell {
-  int r, i, k, n, m, h, iv, dv;
-  __device__ __forceinline__ void load(const Off* M, const Off* I, const Off* D, const uint8_t* act,
-                                       const int16_t* nl, const int16_t* ml, const UGeo* tab, const UGeo& g,
-                                       const Geo& gx, const Geo& go, const Geo& ge, int f, int na,
+  int r, k, kp, n, m, h, iv, dv;
+  __device__ __forceinline__ void load(const Off* M, const Off* I, const Off* D, const uint32_t* act, int glo,
+                                       const SrcRow& sx, const SrcRow& so, const SrcRow& se, int f, int na,
                                        unsigned inv_na) {
     constexpr int NUL = NullOf<Off>::value;
-    i = na > 1 ? (int)__umulhi((unsigned)f, inv_na) : f;
-    r = act[f - i * na];
-    n = nl[r];
-    m = ml[r];
-    k = g.lo + i;
-    const UView<Off, P> v{tab, const_cast<Off*>(M), const_cast<Off*>(I), const_cast<Off*>(D), r};
-    const int mx = get_off<UView<Off, P>, 0>(v, gx, k, NUL);
-    const int mlo = get_off<UView<Off, P>, 0>(v, go, k - 1, NUL);
-    const int mro = get_off<UView<Off, P>, 0>(v, go, k + 1, NUL);
+    const int i = na > 1 ? (int)__umulhi((unsigned)f, inv_na) : f;
+    const uint32_t info = act[f - i * na];
+    r = (int)(info & 0xffu);
+    n = (int)((info >> 8) & 0xfffu);
+    m = (int)(info >> 20);
+    k = glo + i;
+    kp = k * P + r;
+    auto at = [&](const Off* A, const SrcRow& sr, int dk) -> int {
+      return (unsigned)(k + dk - sr.lo) < sr.w ? (int)A[sr.row0 + kp + dk * P] : NUL;
+    };
+    const int mx = at(M, sx, 0);
+    const int mlo = at(M, so, -1);
+    const int mro = at(M, so, 1);
     // gap-linear model (o = 0): I[s-e][k-1] <= M[s-e][k-1] and D[s-e][k+1] <=
     // M[s-e][k+1] (M is the maximum over them), so the M sources alone give
     // the same I and D
-    const int il = LIN ? NUL : get_off<UView<Off, P>, 1>(v, ge, k - 1, NUL);
-    const int dr = LIN ? NUL : get_off<UView<Off, P>, 2>(v, ge, k + 1, NUL);
+    const int il = LIN ? NUL : at(I, se, -1);
+    const int dr = LIN ? NUL : at(D, se, 1);
     // a null source stays negative through the +1 steps of the stored
     // scores, so only the far end needs testing; negative = null
     iv = max(mlo, il) + 1;
@@ -100,9 +114,9 @@ struct Cell {
     if (xv > m || xv - k > n) xv = NUL;
     h = __vimax3_s32(xv, iv, dv);
   }
-  __device__ __forceinline__ void store(Off* M, Off* I, Off* D, const UGeo& g) const {
+  __device__ __forceinline__ void store(Off* M, Off* I, Off* D, int row0) const {
     constexpr int NUL = NullOf<Off>::value;
-    const int c = (g.base + i) * P + r;
+    const int c = row0 + kp;
     M[c] = (Off)(h >= 0 ? h : NUL);
     if (!LIN) {
       I[c] = (Off)iv;
@@ -198,10 +212,6 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
         active = false;
       }
     }
-    if (lane == 0) {
-      W->nl[q] = (int16_t)n;
-      W->ml[q] = (int16_t)m;
-    }
     __syncwarp();
     const int kf = m - n;
     int s_fin = -1, k_end = kf, h_end = m;
@@ -235,7 +245,8 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
     int na = __popc(amask);
     unsigned inv_na = 0;  // ceil(2^32 / na): item / na by one __umulhi
     auto relist = [&]() {
-      if (active && lane == 0) W->act[__popc(amask & ((1u << lane32) - 1u))] = (uint8_t)q;
+      if (active && lane == 0)
+        W->act[__popc(amask & ((1u << lane32) - 1u))] = (uint32_t)q | (uint32_t)n << 8 | (uint32_t)m << 20;
       inv_na = na > 1 ? 0xffffffffu / (unsigned)na + 1u : 0u;
       __syncwarp();
     };
@@ -262,8 +273,9 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
       const int items = na * g0.w;
       for (int f = lane32; f < items; f += 32) {
         const int i = na > 1 ? (int)__umulhi((unsigned)f, inv_na) : f;
-        const int r = W->act[f - i * na];
-        const int rn = W->nl[r], rm = W->ml[r], k = g0.lo + i;
+        const uint32_t info = W->act[f - i * na];
+        const int r = (int)(info & 0xffu), rn = (int)((info >> 8) & 0xfffu), rm = (int)(info >> 20);
+        const int k = g0.lo + i;
         int h = NUL;
         if (k <= rm && -k <= rn) h = extend_diag32(W->pw + r, W->tw + r, rn, rm, k, k > 0 ? k : 0, PS);
         const int c = (g0.base + i) * P + r;
@@ -288,15 +300,16 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
     for (int s = 1; s <= s_hi && na > 0; ++s) {
       const UGeo g = tab[s];
       if (!g.ex) continue;
-      const Geo gx = geo_of(view, s - pen.x, 1);
-      const Geo go = geo_of(view, s - pen.oe, 1);
-      const Geo ge = geo_of(view, s - pen.e, 2);
+      const SrcRow sx = src_row<P>(geo_of(view, s - pen.x, 1));
+      const SrcRow so = src_row<P>(geo_of(view, s - pen.oe, 1));
+      const SrcRow se = src_row<P>(geo_of(view, s - pen.e, 2));
+      const int row0 = (g.base - g.lo) * P;
       const int items = na * g.w;
       for (int f = lane32; f < items; f += 32) {
         Cell<Off, P, LIN> c;
-        c.load(W->M, W->I, W->D, W->act, W->nl, W->ml, tab, g, gx, go, ge, f, na, inv_na);
+        c.load(W->M, W->I, W->D, W->act, g.lo, sx, so, se, f, na, inv_na);
         if (c.h >= 0) c.h = extend_diag32(W->pw + c.r, W->tw + c.r, c.n, c.m, c.k, c.h, PS);
-        c.store(W->M, W->I, W->D, g);
+        c.store(W->M, W->I, W->D, row0);
       }
       __syncwarp();
       bool done;
