@@ -136,13 +136,15 @@ struct LinUView : UView<Off, P> {
 template <typename Off, int P>
 __device__ __forceinline__ int bt_I(const LinUView<Off, P>& v, int s, int k) {
   constexpr int NUL = NullOf<Off>::value;
-  const int ml = get_off<UView<Off, P>, 0>(v, geo_of(v, s - v.e, 1), k - 1, NUL);
+  const UView<Off, P>& u = v;
+  const int ml = get_off<UView<Off, P>, 0>(u, geo_of(u, s - v.e, 1), k - 1, NUL);
   return ml >= 0 && ml + 1 <= v.m ? ml + 1 : NUL;
 }
 template <typename Off, int P>
 __device__ __forceinline__ int bt_D(const LinUView<Off, P>& v, int s, int k) {
   constexpr int NUL = NullOf<Off>::value;
-  const int mr = get_off<UView<Off, P>, 0>(v, geo_of(v, s - v.e, 1), k + 1, NUL);
+  const UView<Off, P>& u = v;
+  const int mr = get_off<UView<Off, P>, 0>(u, geo_of(u, s - v.e, 1), k + 1, NUL);
   return mr >= 0 && mr - k <= v.n ? mr : NUL;
 }
 

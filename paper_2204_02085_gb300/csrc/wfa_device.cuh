@@ -438,7 +438,7 @@ struct ArenaView {
 // table serves every pair of a launch.  ex: bit0 M exists, bit1 I and D
 // exist (they always exist together); base: first cell of the wavefront in a
 // pair's store.
-struct UGeo {
+struct __align__(8) UGeo {
   int16_t lo, w, base;
   uint8_t ex, pad;
 };
@@ -515,6 +515,22 @@ __device__ __forceinline__ Geo geo_of(const V& view, int s, int bit) {
       g.lo = view.lo_of(s);
       g.w = view.hi_of(s) - g.lo + 1;
       g.base = view.base_of(s);
+    }
+  }
+  return g;
+}
+
+// The same for the short kernel's store: one 8-byte load of the table entry.
+template <typename OffT, int P>
+__device__ __forceinline__ Geo geo_of(const UView<OffT, P>& view, int s, int bit) {
+  Geo g{0, 0, 0};
+  if (s >= 0) {
+    const UGeo t = view.tab[s];
+    const int e = t.ex & 2 ? 7 : t.ex;
+    if (e & bit) {
+      g.lo = t.lo;
+      g.w = t.w;
+      g.base = t.base;
     }
   }
   return g;
