@@ -675,25 +675,30 @@ __device__ int wfa_backtrace(const V& view, int n, int m, ScaledPen p, int s_fin
   if (k_end < m - n) emit(kOpI, (uint32_t)((m - n) - k_end));
   while (guard-- > 0) {
     if (s < 0) return -2;
-    if (state == kOpM) {
-      if (s == 0) {
-        // a start on diagonal k: (0, k) or (-k, 0), then matches to h
-        const int h0 = k > 0 ? k : 0;
-        if (h < h0 || k > m || -k > n) return -2;
-        emit(kOpM, (uint32_t)(h - h0));
-        if (k > 0) emit(kOpI, (uint32_t)k);
-        if (k < 0) emit(kOpD, (uint32_t)(-k));
-        break;
-      }
-      int xv = get_off<V, 0>(view, geo_of(view, s - p.x, 1), k, NUL);
+    const bool in_m = state == kOpM;
+    if (in_m && s == 0) {
+      // a start on diagonal k: (0, k) or (-k, 0), then matches to h
+      const int h0 = k > 0 ? k : 0;
+      if (h < h0 || k > m || -k > n) return -2;
+      emit(kOpM, (uint32_t)(h - h0));
+      if (k > 0) emit(kOpI, (uint32_t)k);
+      if (k < 0) emit(kOpD, (uint32_t)(-k));
+      break;
+    }
+    // Every state reads the same three cells (the lanes of a warp walking
+    // different pairs stay together): state M its mismatch, insertion and
+    // deletion candidates M_{s-x}[k], I_s[k], D_s[k]; state I the extension
+    // test's I_{s-e}[k-1]; state D its D_{s-e}[k+1].
+    int xv = get_off<V, 0>(view, geo_of(view, in_m ? s - p.x : -1, 1), k, NUL);
+    const int iv = bt_I(view, in_m ? s : s - p.e, in_m ? k : k - 1);
+    const int dv = bt_D(view, in_m ? s : s - p.e, in_m ? k : k + 1);
+    if (in_m) {
       if (xv >= 0) {
         xv += 1;
         if (xv > m || xv - k > n) xv = NUL;
       } else {
         xv = NUL;
       }
-      const int iv = bt_I(view, s, k);
-      const int dv = bt_D(view, s, k);
       int pick, c;
       if (xv >= 0 && xv >= iv && xv >= dv) {
         pick = kOpX; c = xv;
@@ -716,7 +721,7 @@ __device__ int wfa_backtrace(const V& view, int n, int m, ScaledPen p, int s_fin
       }
     } else if (state == kOpI) {
       emit(kOpI, 1);
-      if (bt_I(view, s - p.e, k - 1) == h - 1) {
+      if (iv == h - 1) {  // extend before open
         s -= p.e;
       } else {
         s -= p.oe;
@@ -726,7 +731,7 @@ __device__ int wfa_backtrace(const V& view, int n, int m, ScaledPen p, int s_fin
       h -= 1;
     } else {
       emit(kOpD, 1);
-      if (bt_D(view, s - p.e, k + 1) == h) {
+      if (dv == h) {
         s -= p.e;
       } else {
         s -= p.oe;
