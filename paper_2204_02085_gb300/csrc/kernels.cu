@@ -295,13 +295,15 @@ cudaError_t plan_one(int device, ShortVariant* v, const char* name) {
 cudaError_t short_plan(int device, ShortPlan* plan) {
   cudaError_t e;
   int i = 0;
-  if ((e = plan_one<1, 127, 208, 31, int8_t>(device, &plan->v[i++], "g1_l127_c208_i8"))) return e;
-  if ((e = plan_one<2, 127, 208, 31, int8_t>(device, &plan->v[i++], "g2_l127_c208_i8"))) return e;
-  if ((e = plan_one<4, 127, 208, 31, int8_t>(device, &plan->v[i++], "g4_l127_c208_i8"))) return e;
-  if ((e = plan_one<8, 127, 208, 31, int8_t>(device, &plan->v[i++], "g8_l127_c208_i8"))) return e;
+  // 197 cells: every wavefront up to scaled score 16 under 4/6/2, and a
+  // block of four G = 2 warps small enough for five blocks per SM
+  if ((e = plan_one<1, 127, 197, 31, int8_t>(device, &plan->v[i++], "g1_l127_c197_i8"))) return e;
+  if ((e = plan_one<2, 127, 197, 31, int8_t>(device, &plan->v[i++], "g2_l127_c197_i8"))) return e;
+  if ((e = plan_one<4, 127, 197, 31, int8_t>(device, &plan->v[i++], "g4_l127_c197_i8"))) return e;
+  if ((e = plan_one<8, 127, 197, 31, int8_t>(device, &plan->v[i++], "g8_l127_c197_i8"))) return e;
   if ((e = plan_one<1, 127, 64, 15, int8_t>(device, &plan->v[i++], "g1_l127_c64_i8"))) return e;
-  if ((e = plan_one<2, 255, 208, 31, int16_t>(device, &plan->v[i++], "g2_l255_c208_i16"))) return e;
-  if ((e = plan_one<4, 255, 208, 31, int16_t>(device, &plan->v[i++], "g4_l255_c208_i16"))) return e;
+  if ((e = plan_one<2, 255, 197, 31, int16_t>(device, &plan->v[i++], "g2_l255_c197_i16"))) return e;
+  if ((e = plan_one<4, 255, 197, 31, int16_t>(device, &plan->v[i++], "g4_l255_c197_i16"))) return e;
   if ((e = plan_one<1, 127, 40, 15, int8_t>(device, &plan->v[i++], "g1_l127_c40_i8"))) return e;
   // gap-linear model (o = 0): M only, so a third of the store per cell
   if ((e = plan_one<1, 127, 64, 15, int8_t, true>(device, &plan->v[i++], "g1_l127_c64_lin"))) return e;
@@ -309,8 +311,8 @@ cudaError_t short_plan(int device, ShortPlan* plan) {
   if ((e = plan_one<2, 255, 256, 31, int16_t, true>(device, &plan->v[i++], "g2_l255_c256_lin_i16"))) return e;
   // ends-free calls (first wavefront over the free starts, end test over the
   // free diagonals)
-  if ((e = plan_one<2, 127, 208, 31, int8_t, false, true>(device, &plan->v[i++], "g2_l127_c208_i8_ef"))) return e;
-  if ((e = plan_one<4, 255, 208, 31, int16_t, false, true>(device, &plan->v[i++], "g4_l255_c208_i16_ef")))
+  if ((e = plan_one<2, 127, 197, 31, int8_t, false, true>(device, &plan->v[i++], "g2_l127_c197_i8_ef"))) return e;
+  if ((e = plan_one<4, 255, 197, 31, int16_t, false, true>(device, &plan->v[i++], "g4_l255_c197_i16_ef")))
     return e;
   if ((e = plan_one<2, 127, 256, 31, int8_t, true, true>(device, &plan->v[i++], "g2_l127_c256_lin_ef"))) return e;
   if ((e = plan_one<2, 255, 256, 31, int16_t, true, true>(device, &plan->v[i++], "g2_l255_c256_lin_i16_ef")))
