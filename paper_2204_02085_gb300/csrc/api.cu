@@ -418,7 +418,7 @@ int run_retries(wfa_gpu_ctx* c, Call& k, wfa::AlignArgs& a) {
   return 0;
 }
 
-constexpr int64_t kTuneSample = 8192;
+constexpr int64_t kTuneSample = 4096;
 
 // Pick the short-kernel variant for a batch of sequences <= 127 bases: the
 // large-store variant scores the first kTuneSample pairs (score only); if
@@ -493,7 +493,8 @@ int wfa_gpu_create(wfa_gpu_ctx** out, int device, size_t scratch_bytes) {
       if (cudaEventCreate(&c->ev[i]) != cudaSuccess) { rc = WFA_GPU_ECUDA; break; }
     if (rc) break;
     if (cudaMalloc(reinterpret_cast<void**>(&c->ctrl), 2 * sizeof(wfa::Ctrl)) != cudaSuccess) { rc = WFA_GPU_ENOMEM; break; }
-    if (cudaHostAlloc(reinterpret_cast<void**>(&c->h_tune), 8192 * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess) {
+    if (cudaHostAlloc(reinterpret_cast<void**>(&c->h_tune), kTuneSample * sizeof(int32_t), cudaHostAllocDefault) !=
+        cudaSuccess) {
       rc = WFA_GPU_ENOMEM;
       break;
     }

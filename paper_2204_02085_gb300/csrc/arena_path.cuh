@@ -98,6 +98,22 @@ struct ArenaViewT {
   }
 };
 
+// geo_of for the arena store: the score's metadata in one 16-byte load (the
+// metadata of a slice starts 16-byte aligned).
+template <typename OffT>
+__device__ __forceinline__ Geo geo_of(const ArenaViewT<OffT>& view, int s, int bit) {
+  Geo g{0, 0, 0};
+  if (s >= 0) {
+    const int4 t = *reinterpret_cast<const int4*>(view.meta + 4 * s);  // lo, hi, base, exist bits
+    if (t.w & bit) {
+      g.lo = t.x;
+      g.w = t.y - t.x + 1;
+      g.base = t.z;
+    }
+  }
+  return g;
+}
+
 // Only the last R scores: score s lives in ring slot s % R, a block
 // [M W][I W][D W] with W the widest possible wavefront; metadata likewise in
 // a ring.  Enough for the recurrences, not for a backtrace.

@@ -342,9 +342,9 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
           int nr;
           if constexpr (LIN) {
             LinUView<Off, P> lv{view, n, m, pen.e};
-            nr = wfa_backtrace(lv, n, m, pen, s_fin, k_end, h_end, a.runs + src, kSlot);
+            nr = wfa_backtrace<true>(lv, n, m, pen, s_fin, k_end, h_end, a.runs + src, kSlot);
           } else {
-            nr = wfa_backtrace(view, n, m, pen, s_fin, k_end, h_end, a.runs + src, kSlot);
+            nr = wfa_backtrace<true>(view, n, m, pen, s_fin, k_end, h_end, a.runs + src, kSlot);
           }
           if (nr == -1) {
             defer_pair(a, pair);  // more runs than a slot holds

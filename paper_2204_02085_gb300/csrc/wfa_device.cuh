@@ -647,7 +647,7 @@ __device__ __forceinline__ int bt_D(const V& view, int s, int k) {
 // Returns the number of runs, -1 if more than cap runs are needed, -2 if the
 // stored wavefronts are inconsistent (which the forward pass never
 // produces).  Single lane.
-template <class V>
+template <bool CONVERGENT = false, class V>
 __device__ int wfa_backtrace(const V& view, int n, int m, ScaledPen p, int s_final, int k_end, int h_end,
                              uint32_t* runs, int cap) {
   using Off = typename V::Off;
@@ -685,13 +685,15 @@ __device__ int wfa_backtrace(const V& view, int n, int m, ScaledPen p, int s_fin
       if (k < 0) emit(kOpD, (uint32_t)(-k));
       break;
     }
-    // Every state reads the same three cells (the lanes of a warp walking
-    // different pairs stay together): state M its mismatch, insertion and
-    // deletion candidates M_{s-x}[k], I_s[k], D_s[k]; state I the extension
-    // test's I_{s-e}[k-1]; state D its D_{s-e}[k+1].
-    int xv = get_off<V, 0>(view, geo_of(view, in_m ? s - p.x : -1, 1), k, NUL);
-    const int iv = bt_I(view, in_m ? s : s - p.e, in_m ? k : k - 1);
-    const int dv = bt_D(view, in_m ? s : s - p.e, in_m ? k : k + 1);
+    // CONVERGENT (lanes of a warp walking different pairs): every state
+    // reads the same three cells, so the lanes stay together -- state M its
+    // mismatch, insertion and deletion candidates M_{s-x}[k], I_s[k],
+    // D_s[k]; state I the extension test's I_{s-e}[k-1]; state D its
+    // D_{s-e}[k+1].  Otherwise (one thread) each state reads only its own.
+    int xv = NUL, iv = NUL, dv = NUL;
+    if (CONVERGENT || in_m) xv = get_off<V, 0>(view, geo_of(view, in_m ? s - p.x : -1, 1), k, NUL);
+    if (CONVERGENT || state != kOpD) iv = bt_I(view, in_m ? s : s - p.e, in_m ? k : k - 1);
+    if (CONVERGENT || state != kOpI) dv = bt_D(view, in_m ? s : s - p.e, in_m ? k : k + 1);
     if (in_m) {
       if (xv >= 0) {
         xv += 1;
