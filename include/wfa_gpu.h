@@ -61,8 +61,9 @@ enum {
                                    too small for some pair's wavefronts */
   WFA_GPU_ECUDA = -3,           /* a CUDA runtime call failed (no device, launch failure) */
   WFA_GPU_ECIGAR_CAPACITY = -4, /* CIGAR words exceed cigar_capacity_words; scores, status
-                                   and out_cigar_offsets are still valid, the CIGAR buffer is
-                                   untouched, and out_cigar_offsets[n] is the size needed */
+                                   and out_cigar_offsets are still valid, out_cigar_offsets[n]
+                                   is the size needed, the CIGAR buffer holds no valid
+                                   alignment (its contents are unspecified) */
   WFA_GPU_ETIMEOUT = -5         /* a bounded device-side wait gave up */
 };
 
@@ -169,7 +170,9 @@ int wfa_gpu_set_ends_free(wfa_gpu_ctx *ctx, int32_t pattern_begin_free, int32_t 
  *
  * Returns WFA_GPU_OK (every pair has a status), or EINVAL, ENOMEM, ECUDA,
  * ECIGAR_CAPACITY (see the enum).  The call returns after all outputs are
- * in the caller's buffers. */
+ * in the caller's buffers.  Host-pointer calls of 2^21 pairs or more whose
+ * outputs are page-locked run in chunks of 2^20 pairs, each chunk's outputs
+ * copied back while the next one computes (same results). */
 int wfa_gpu_align_batch(wfa_gpu_ctx *ctx, int64_t n_pairs,
                         const char *patterns, const int64_t *pattern_offsets,
                         const int32_t *pattern_lengths,

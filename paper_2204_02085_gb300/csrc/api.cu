@@ -98,6 +98,10 @@ struct wfa_gpu_ctx {
   // ends-free alignment: free pattern begin / end, text begin / end lengths
   int32_t ends_free[4] = {0, 0, 0, 0};
   cudaStream_t own_stream = nullptr;
+  // chunked host-pointer calls: output copies of one chunk overlap the next
+  // chunk's work (stream and events of the context)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_chunk = nullptr, ev_copied = nullptr;
   cudaStream_t stream = nullptr;
   int32_t* arena = nullptr;
   size_t arena_bytes = 0;
@@ -488,6 +492,12 @@ int wfa_gpu_create(wfa_gpu_ctx** out, int device, size_t scratch_bytes) {
   int rc = WFA_GPU_OK;
   do {
     if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) { rc = WFA_GPU_ECUDA; break; }
+    if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_chunk, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming) != cudaSuccess) {
+      rc = WFA_GPU_ECUDA;
+      break;
+    }
     c->stream = c->own_stream;
     for (int i = 0; i < kEvents; ++i)
       if (cudaEventCreate(&c->ev[i]) != cudaSuccess) { rc = WFA_GPU_ECUDA; break; }
@@ -551,6 +561,116 @@ int wfa_gpu_set_stream(wfa_gpu_ctx* ctx, void* stream) {
 }  // extern "C"
 
 namespace {
+
+// Host-pointer calls of at least kPipeMinPairs pairs whose outputs are
+// page-locked run in chunks of kPipeChunk pairs: each chunk goes through
+// the whole device sequence (short kernel, arena kernels for its deferred
+// pairs, CIGAR offset scan and compaction, its CIGAR offsets moved to the
+// call's running word count), and its outputs are copied back on the
+// context's copy stream while the next chunk computes.
+constexpr int64_t kPipeMinPairs = 1 << 21;
+constexpr int64_t kPipeChunk = 1 << 20;
+
+int align_pipelined(wfa_gpu_ctx* ctx, Call& k, const wfa::AlignArgs& a, int64_t n, bool plain,
+                    wfa_gpu_penalties pen, int32_t* out_scores, int8_t* out_status, uint32_t* out_cigars,
+                    int64_t cap, int64_t* out_off) {
+  cudaStream_t st = ctx->stream, cs = ctx->copy_stream;
+  const bool score_only = a.score_only != 0;
+  const int64_t nchunks = (n + kPipeChunk - 1) / kPipeChunk;
+  cudaError_t e;
+  if (!score_only && (e = ctx->cig_off.ensure(n + nchunks + 1))) return map_alloc(e);
+  const wfa::Ctrl staged = *ctx->h_ctrl;  // the whole batch's validation: extents, longest sequence
+  int vi = -1;
+  int64_t base = 0, deferred = 0;
+  bool over = false;
+  for (int64_t c = 0; c < nchunks; ++c) {
+    const int64_t b = c * kPipeChunk, m = std::min(kPipeChunk, n - b);
+    wfa::AlignArgs ac = a;
+    ac.n = m;
+    ac.poff = a.poff + b; ac.plen = a.plen + b;
+    ac.toff = a.toff + b; ac.tlen = a.tlen + b;
+    ac.score = a.score + b; ac.status = a.status + b;
+    ac.nruns = a.nruns + b; ac.run_src = a.run_src + b;
+    ac.runs = a.runs + (score_only ? 0 : b * wfa::kSlot);
+    *ctx->h_ctrl = staged;  // counters zero, the batch's extents kept
+    if (!k.ok(cudaMemcpyAsync(ctx->ctrl, ctx->h_ctrl, sizeof(wfa::Ctrl), cudaMemcpyHostToDevice, st)))
+      return fail_cuda(k);
+    if (plain) {
+      if (!k.launched(wfa::launch_route_all(ac, st))) return fail_cuda(k);
+    } else {
+      if (vi < 0) {
+        const bool ef = (a.pb | a.pe | a.tb | a.te) != 0;
+        vi = ef ? ctx->variant_ef_mid[pen.o == 0 ? 1 : 0] : ctx->variant_mid[pen.o == 0 ? 1 : 0];
+        if (staged.max_len <= 127) {
+          vi = autotune_short(ctx, k, ac, m);
+          if (vi < 0) return fail_cuda(k);
+        }
+        ctx->last_variant = vi;
+      }
+      if (!k.launched(wfa::launch_short(ac, ctx->plan.v[vi], st))) return fail_cuda(k);
+    }
+    if (c == nchunks - 1) k.rec(2);
+    // chunk c's CIGAR offsets at [b + c, b + c + m]: apart from chunk c+1's,
+    // which may be written while these are still being copied.  One host
+    // wait per chunk: the control block and the CIGAR total come back
+    // together; a chunk with deferred pairs runs the arena kernels and
+    // scans again.
+    int64_t* off_c = score_only ? nullptr : ctx->cig_off.p + b + c;
+    auto scan = [&]() -> bool {
+      return score_only || (k.launched(wfa::launch_scan(ac.nruns, m, 0, off_c, ctx->scan_tmp.p, st), 3) &&
+                            k.ok(d2h(ctx->h_total, off_c + m, sizeof(int64_t), st)));
+    };
+    if (!k.ok(d2h(ctx->h_ctrl, ctx->ctrl, sizeof(wfa::Ctrl), st)) || !scan() || !k.ok(cudaStreamSynchronize(st)))
+      return fail_cuda(k);
+    const int64_t dc = (int64_t)ctx->h_ctrl->defer_count + ctx->h_ctrl->defer_long_count;
+    deferred += dc;
+    if (dc > 0) {
+      const int rc = run_arena(ctx, k, ac, !plain);
+      if (rc) return rc;
+      if (!scan() || !k.ok(cudaStreamSynchronize(st))) return fail_cuda(k);
+    }
+    if (ctx->h_ctrl->internal_error) return WFA_GPU_ECUDA;
+    if (c == nchunks - 1) k.rec(3);
+    int64_t tot = 0;
+    bool copy_words = false;
+    if (!score_only) {
+      tot = *ctx->h_total;
+      if (base > 0 && !k.launched(wfa::launch_add(off_c, m + 1, base, st))) return fail_cuda(k);
+      over = over || base + tot > cap;
+      copy_words = !over && tot > 0;
+      if (copy_words) {
+        if ((size_t)(base + tot) > ctx->cig.cap) {
+          // the copies in flight read the old buffer: let them finish first
+          if (!k.ok(cudaStreamSynchronize(cs))) return fail_cuda(k);
+          if ((e = ctx->cig.ensure(base + tot))) return map_alloc(e);
+        }
+        if (!k.launched(wfa::launch_compact(m, ac.nruns, ac.run_src, ac.runs, ac.pool, off_c, ctx->cig.p, cap,
+                                            ctx->ctrl, st)))
+          return fail_cuda(k);
+      }
+    }
+    if (c == nchunks - 1) k.rec(4);
+    // this chunk's outputs go back while the next one computes
+    if (!k.ok(cudaEventRecord(ctx->ev_chunk, st)) || !k.ok(cudaStreamWaitEvent(cs, ctx->ev_chunk, 0)))
+      return fail_cuda(k);
+    if (!k.ok(d2h(out_scores + b, ac.score, (size_t)m * sizeof(int32_t), cs)) ||
+        !k.ok(d2h(out_status + b, ac.status, (size_t)m * sizeof(int8_t), cs)))
+      return fail_cuda(k);
+    if (!score_only) {
+      const int64_t cnt = c == nchunks - 1 ? m + 1 : m;
+      if (!k.ok(d2h(out_off + b, off_c, (size_t)cnt * sizeof(int64_t), cs))) return fail_cuda(k);
+      if (copy_words && !k.ok(d2h(out_cigars + base, ctx->cig.p + base, (size_t)tot * sizeof(uint32_t), cs)))
+        return fail_cuda(k);
+    }
+    base += tot;
+  }
+  if (!k.ok(cudaEventRecord(ctx->ev_copied, cs)) || !k.ok(cudaStreamWaitEvent(st, ctx->ev_copied, 0)))
+    return fail_cuda(k);
+  k.rec(5);
+  if (!k.ok(cudaStreamSynchronize(st))) return fail_cuda(k);
+  ctx->last.deferred_pairs = deferred;
+  return over ? WFA_GPU_ECIGAR_CAPACITY : WFA_GPU_OK;
+}
 
 int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t* pattern_offsets,
                 const int32_t* pattern_lengths, const char* texts, const int64_t* text_offsets,
@@ -643,6 +763,27 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
   a.defer_long_list = ctx->defer_long.p;
   a.overflow_list = ctx->overflow.p;
   a.ctrl = ctx->ctrl;
+
+  // large host-pointer call with page-locked outputs: chunked, with the
+  // output copies overlapping the compute
+  if (!dev && !sink && n >= kPipeMinPairs && mapped_range(out_scores, (size_t)n * sizeof(int32_t)) &&
+      mapped_range(out_status, (size_t)n) &&
+      (score_only || (mapped_range(out_cigar_offsets, (size_t)(n + 1) * sizeof(int64_t)) &&
+                      (cap == 0 || mapped_range(out_cigars, (size_t)cap * sizeof(uint32_t)))))) {
+    rc = align_pipelined(ctx, k, a, n, plain, pen, out_scores, out_status, out_cigars, cap, out_cigar_offsets);
+    if (rc < 0 && rc != WFA_GPU_ECIGAR_CAPACITY) return rc;
+    ctx->last.kernel_launches = k.launches;
+    ctx->last.short_variant = ctx->last_variant;
+    if (k.timing) {
+      ctx->last.h2d_ms = elapsed(ctx, 0, 1);
+      ctx->last.align_ms = elapsed(ctx, 1, 2);
+      ctx->last.general_ms = elapsed(ctx, 2, 3);
+      ctx->last.cigar_ms = elapsed(ctx, 3, 4);
+      ctx->last.d2h_ms = elapsed(ctx, 4, 5);
+      ctx->last.total_ms = elapsed(ctx, 0, 5);
+    }
+    return rc;
+  }
 
   if (plain) {
     if (!k.launched(wfa::launch_route_all(a, st))) return fail_cuda(k);
@@ -1121,6 +1262,12 @@ void wfa_gpu_destroy(wfa_gpu_ctx* c) {
   for (int i = 0; i < kEvents; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamDestroy(c->copy_stream);
+  }
+  if (c->ev_chunk) cudaEventDestroy(c->ev_chunk);
+  if (c->ev_copied) cudaEventDestroy(c->ev_copied);
   delete c;
 }
 

@@ -238,6 +238,11 @@ __global__ void sort_scatter_kernel(const AlignArgs a, const int32_t* list, cons
   }
 }
 
+__global__ void add_kernel(int64_t* p, int64_t count, int64_t v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] += v;
+}
+
 int sm_count(int device) {
   int v = 0;
   cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
@@ -387,6 +392,12 @@ cudaError_t launch_sort_longest_first(const AlignArgs& a, const int32_t* list, c
   sort_hist_kernel<<<grid, kAuxBlock, 0, st>>>(a, list, count, aux);
   sort_scan_kernel<<<1, 32, 0, st>>>(aux, aux + kSortBuckets);
   sort_scatter_kernel<<<grid, kAuxBlock, 0, st>>>(a, list, count, aux + kSortBuckets, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add(int64_t* p, int64_t count, int64_t v, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  add_kernel<<<aux_grid(count, current_device()), kAuxBlock, 0, st>>>(p, count, v);
   return cudaGetLastError();
 }
 

@@ -124,6 +124,9 @@ cudaError_t launch_compact(int64_t n, const int32_t* nruns, const int64_t* run_s
                            const uint32_t* pool, const int64_t* off, uint32_t* out, int64_t cap, const Ctrl* ctrl,
                            cudaStream_t st);
 
+// p[0 .. count) += v (int64).
+cudaError_t launch_add(int64_t* p, int64_t count, int64_t v, cudaStream_t st);
+
 // Standalone packer: sequence i -> words[woff[i] ..], invalid[i].
 cudaError_t launch_pack(int64_t n, const char* seqs, const int64_t* off, const int32_t* len, const int64_t* woff,
                         uint64_t* words, int8_t* invalid, cudaStream_t st);

@@ -323,3 +323,59 @@ def test_config2_full_size(pkg, oracle_mod, edits):
         lo, hi = int(off[c0]), int(off[min(c0 + chunk, n)])
         assert np.array_equal(off[c0:c0 + chunk + 1] - lo, ooff)
         assert np.array_equal(w[lo:hi], ow)
+
+
+def _pinned(torch, a):
+    t = torch.empty(a.shape, dtype={np.uint8: torch.uint8, np.int32: torch.int32, np.int64: torch.int64,
+                                    np.int8: torch.int8, np.uint32: torch.int32}[a.dtype.type], pin_memory=True)
+    t.numpy().view(a.dtype)[...] = a
+    return t
+
+
+def test_chunked_host_call_with_page_locked_outputs(pkg, oracle_mod):
+    """2.5M pairs (three chunks) from page-locked host memory into page-locked
+    outputs: the chunked path, whose output copies overlap the next chunk,
+    gives the oracle's results; a few long pairs go through the arena in a
+    middle chunk; a short CIGAR capacity gives ECIGAR_CAPACITY with valid
+    scores and offsets."""
+    import torch
+
+    from paper_2204_02085_gb300 import synth
+
+    core = synth.uniform_reads(2_500_000, 100, 3, seed=77)
+    extra = synth.random_pairs(40, 300, 900, seed=78, edit_rate=0.05)
+    pairs_at = {1_200_000 + 7 * j: extra.pair(j) for j in range(extra.n)}
+    # splice the long pairs into the batch without a Python loop over 2.5M pairs
+    plen = core.pattern_lengths.copy(); tlen = core.text_lengths.copy()
+    pats, txts = [core.patterns], [core.texts]
+    poff = core.pattern_offsets.copy(); toff = core.text_offsets.copy()
+    pbase, tbase = len(core.patterns), len(core.texts)
+    for j, i in enumerate(sorted(pairs_at)):
+        p, t = pairs_at[i]
+        pats.append(np.frombuffer(p, np.uint8)); txts.append(np.frombuffer(t, np.uint8))
+        poff[i], toff[i], plen[i], tlen[i] = pbase, tbase, len(p), len(t)
+        pbase += len(p); tbase += len(t)
+    b = synth.Batch(np.concatenate(pats), poff, plen, np.concatenate(txts), toff, tlen)
+    n = b.n
+    want = oracle_mod.wfa_batch(b, (4, 6, 2), nthreads=NCPU)
+    ins = {k: _pinned(torch, getattr(b, k)) for k in ("patterns", "pattern_offsets", "pattern_lengths", "texts",
+                                                      "text_offsets", "text_lengths")}
+    cap = int(want[3][-1])
+    outs = dict(s=torch.empty(n, dtype=torch.int32, pin_memory=True), st=torch.empty(n, dtype=torch.int8, pin_memory=True),
+                off=torch.empty(n + 1, dtype=torch.int64, pin_memory=True),
+                w=torch.empty(cap, dtype=torch.int32, pin_memory=True))
+    ptr = lambda t: t.data_ptr()  # noqa: E731
+    with pkg.Aligner(0, 2 << 30) as al:
+        for c, code in ((cap, pkg.WFA_GPU_OK), (cap - 1, pkg.WFA_GPU_ECIGAR_CAPACITY)):
+            rc = pkg.wfa_gpu_align_batch(al.ctx, n, ptr(ins["patterns"]), ptr(ins["pattern_offsets"]),
+                                         ptr(ins["pattern_lengths"]), ptr(ins["texts"]), ptr(ins["text_offsets"]),
+                                         ptr(ins["text_lengths"]), (4, 6, 2), 0, pkg.WFA_GPU_TIMING, ptr(outs["s"]),
+                                         ptr(outs["st"]), ptr(outs["w"]), c, ptr(outs["off"]))
+            assert rc == code
+            t = al.timing()
+            assert t["deferred_pairs"] >= 40
+            got_s, got_st, got_off = outs["s"].numpy(), outs["st"].numpy(), outs["off"].numpy()
+            assert np.array_equal(got_s, want[0]) and np.array_equal(got_st, want[1])
+            assert np.array_equal(got_off, want[3])
+            if code == pkg.WFA_GPU_OK:
+                assert np.array_equal(outs["w"].numpy().view(np.uint32), want[2])
