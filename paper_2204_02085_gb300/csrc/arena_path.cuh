@@ -249,12 +249,10 @@ __device__ int team_forward(V& view, const uint32_t* pw, const uint32_t* tw, int
     int bits = 0;
     const Src<Off> sx = src_of(view, gx, 0), so = src_of(view, go, 0);
     const Src<Off> si = src_of(view, gi, 1), sd = src_of(view, gd, 2);
-    for (int k = lo + r; k <= hi; k += T::kSize) {
-      const int mx = sx.at(k, NUL);
-      const int ml = so.at(k - 1, NUL);
-      const int mr = so.at(k + 1, NUL);
-      const int il = si.at(k - 1, NUL);
-      const int dr = sd.at(k + 1, NUL);
+    // two diagonals per thread and round: the ten source loads (previous
+    // wavefronts, mostly from L2) are all issued before either cell is
+    // computed; they never alias this score's block
+    auto cell = [&](int k, int mx, int ml, int mr, int il, int dr) {
       int iv = max(ml, il) + 1;
       if (iv < 0 || iv > m) iv = NUL;
       int dv = max(mr, dr);
@@ -270,6 +268,18 @@ __device__ int team_forward(V& view, const uint32_t* pw, const uint32_t* tw, int
       }
       bits |= (iv >= 0 ? 2 : 0) | (dv >= 0 ? 4 : 0);
       view.put(b, w, k - lo, mv, iv, dv);
+    };
+    for (int k = lo + r; k <= hi; k += 2 * T::kSize) {
+      const int k2 = k + T::kSize;
+      const int mx = sx.at(k, NUL), ml = so.at(k - 1, NUL), mr = so.at(k + 1, NUL);
+      const int il = si.at(k - 1, NUL), dr = sd.at(k + 1, NUL);
+      int mx2 = NUL, ml2 = NUL, mr2 = NUL, il2 = NUL, dr2 = NUL;
+      if (k2 <= hi) {
+        mx2 = sx.at(k2, NUL); ml2 = so.at(k2 - 1, NUL); mr2 = so.at(k2 + 1, NUL);
+        il2 = si.at(k2 - 1, NUL); dr2 = sd.at(k2 + 1, NUL);
+      }
+      cell(k, mx, ml, mr, il, dr);
+      if (k2 <= hi) cell(k2, mx2, ml2, mr2, il2, dr2);
     }
     const int exbits = T::reduce_or(bits, flags, round);  // also the barrier after the writes
     if (exbits == 0) view.release(b, top);
