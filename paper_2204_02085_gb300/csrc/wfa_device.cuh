@@ -157,17 +157,25 @@ __device__ __forceinline__ bool pack_seq_strided32(const char* __restrict__ seq,
 // compares it with the byte folded to upper case.
 __device__ __forceinline__ uint32_t code16_bad(uint4 v, uint32_t* bad16) {
   const uint32_t q[4] = {v.x, v.y, v.z, v.w};
-  uint32_t code = 0, bad = 0;
+  uint32_t code = 0, xs[4], any = 0;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const uint32_t w = q[i];
     const uint32_t c = ((w >> 1) ^ (w >> 2)) & 0x03030303u;
     const uint32_t b0 = c & 0x01010101u, b1 = (c >> 1) & 0x01010101u;
     const uint32_t f = 0x41414141u + 2u * b0 + 6u * b1 + 11u * (b0 & b1);
-    const uint32_t x = (w & 0xDFDFDFDFu) ^ f;                                   // zero byte <=> valid
-    const uint32_t hb = ((((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) >> 7) & 0x01010101u;  // 1 per bad byte
-    bad |= ((hb * 0x01020408u) >> 24 & 0xFu) << (4 * i);
+    xs[i] = (w & 0xDFDFDFDFu) ^ f;  // zero byte <=> valid
+    any |= xs[i];
     code = (code << 8) | ((c * 0x40100401u) >> 24);  // 4 codes, first in the top bits
+  }
+  uint32_t bad = 0;
+  if (any) {  // rare: which bytes are not A/C/G/T
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t x = xs[i];
+      const uint32_t hb = ((((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) >> 7) & 0x01010101u;  // 1 per bad byte
+      bad |= ((hb * 0x01020408u) >> 24 & 0xFu) << (4 * i);
+    }
   }
   *bad16 = bad;
   return code;
