@@ -205,10 +205,15 @@ __device__ __forceinline__ void short_body(const AlignArgs& a, unsigned char* sm
     {
       // all lanes take part: the warp reads its pairs' sequences together
       uint32_t* scratch = reinterpret_cast<uint32_t*>(W->M);
-      const bool okp = pack_warp32<G, C::SPAN>(active ? a.pat + a.poff[pair] : nullptr, n, active, pw, PS, scratch,
-                                               lane, gmask, !a.host_seqs);
-      const bool okt = pack_warp32<G, C::SPAN>(active ? a.txt + a.toff[pair] : nullptr, m, active, tw, PS, scratch,
-                                               lane, gmask, !a.host_seqs);
+      const char* ps = active ? a.pat + a.poff[pair] : nullptr;
+      const char* ts = active ? a.txt + a.toff[pair] : nullptr;
+      bool okp, okt;
+      if (!a.host_seqs) {
+        pack_pair_warp32<G, C::kSpanFit>(ps, n, ts, m, active, pw, tw, PS, scratch, lane, gmask, &okp, &okt);
+      } else {
+        okp = pack_warp32<G, C::SPAN>(ps, n, active, pw, PS, scratch, lane, gmask, false);
+        okt = pack_warp32<G, C::SPAN>(ts, m, active, tw, PS, scratch, lane, gmask, false);
+      }
       if (active && !(okp && okt)) {
         if (lane == 0) write_result(a, pair, 2, -1, 0, 0);
         active = false;

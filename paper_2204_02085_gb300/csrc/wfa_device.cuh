@@ -189,6 +189,109 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// The span (16-byte aligned chunks) holding the active slots' sequences of
+// a warp; `fits`: non-empty and at most span_chunks chunks.  All 32 lanes.
+struct WarpSpan {
+  unsigned long long base;
+  int nch;
+  bool fits;
+};
+__device__ __forceinline__ WarpSpan warp_span(const char* seq, int len, bool active, int span_chunks) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const unsigned long long a = reinterpret_cast<uintptr_t>(seq);
+  unsigned long long lo = active && len > 0 ? a : ~0ull;
+  unsigned long long hi = active && len > 0 ? a + (unsigned)len : 0ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long l2 = __shfl_xor_sync(FULL, lo, o), h2 = __shfl_xor_sync(FULL, hi, o);
+    lo = l2 < lo ? l2 : lo;
+    hi = h2 > hi ? h2 : hi;
+  }
+  WarpSpan w{lo & ~15ull, 0, false};
+  if (hi > lo && hi - w.base <= 16ull * span_chunks) {
+    w.nch = (int)((hi - w.base + 15) >> 4);
+    w.fits = true;
+  }
+  return w;
+}
+
+// Raw span bytes staged at scratch -> (2-bit codes, bad-byte mask) per
+// chunk, in place, 32 chunks a round: a round writes its 8-byte entries
+// below the raw bytes of the rounds still to come; then the zero sentinel
+// entry at nch.  All 32 lanes.
+__device__ __forceinline__ void convert_span(uint32_t* scratch, int nch, int lane32) {
+  const uint4* raw = reinterpret_cast<const uint4*>(scratch);
+  uint2* ent = reinterpret_cast<uint2*>(scratch);
+  for (int c0 = 0; c0 < nch; c0 += 32) {
+    const int c = c0 + lane32;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (c < nch) v = raw[c];
+    __syncwarp();
+    if (c < nch) {
+      uint32_t b16;
+      const uint32_t code = code16_bad(v, &b16);
+      ent[c] = make_uint2(code, b16);
+    }
+  }
+  __syncwarp();
+  if (lane32 == 0) ent[nch] = make_uint2(0u, 0u);
+  __syncwarp();
+}
+
+// A slot cuts its words 0 .. ceil(len/16) (the last one zero) from the
+// converted span entries; returns whether one of its bytes is bad.
+template <int G>
+__device__ __forceinline__ bool cut_words(const uint2* ent, unsigned long long base, const char* seq, int len,
+                                          uint32_t* out, int stride, int lane) {
+  const int nw = (len + 15) >> 4;
+  const int off = (int)(reinterpret_cast<uintptr_t>(seq) - base);  // bytes from the span start
+  const int c0 = off >> 4, r = (off & 15) << 1;
+  bool bad = false;
+  for (int j = lane; j <= nw; j += G) {
+    uint32_t word = 0u;
+    if (j < nw) {
+      const uint2 e0 = ent[c0 + j], e1 = ent[c0 + j + 1];
+      word = __funnelshift_l(e1.x, e0.x, r);
+      const int rem = len - 16 * j;
+      if (rem < 16) word &= ~0u << (32 - 2 * rem);
+      // bad bytes among this word's 16 (at most 2 chunks)
+      const uint32_t m2 = e0.y | (e1.y << 16);
+      if (m2) {
+        const int nb = min(16, rem);
+        const uint32_t in = (nb >= 16 ? 0xFFFFu : ((1u << nb) - 1u)) << (off & 15);
+        if (m2 & in) bad = true;
+      }
+    }
+    out[j * stride] = word;
+  }
+  return bad;
+}
+
+// A slot reads its own chunks (the span is too wide or not staged).
+template <int G>
+__device__ __forceinline__ bool pack_slot_direct(const char* seq, int len, uint32_t* out, int stride, int lane) {
+  const unsigned long long a = reinterpret_cast<uintptr_t>(seq);
+  const int nw = (len + 15) >> 4;
+  bool bad = false;
+  for (int j = lane; j <= nw; j += G) {
+    uint32_t word = 0u;
+    if (j < nw) {
+      // the 16 bytes of word j span at most two aligned chunks
+      const unsigned long long w0 = a + 16ull * j, b0 = w0 & ~15ull;
+      const int h = (int)(w0 - b0), rem = min(16, len - 16 * j);
+      uint32_t m0, m1 = 0u, c1 = 0u;
+      const uint32_t c0 = code16_bad(__ldg(reinterpret_cast<const uint4*>(b0)), &m0);
+      if (h + rem > 16) c1 = code16_bad(__ldg(reinterpret_cast<const uint4*>(b0 + 16)), &m1);
+      word = __funnelshift_l(c1, c0, 2 * h);
+      if (rem < 16) word &= ~0u << (32 - 2 * rem);
+      const uint32_t in = (rem >= 16 ? 0xFFFFu : ((1u << rem) - 1u)) << h;
+      if ((m0 | (m1 << 16)) & in) bad = true;
+    }
+    out[j * stride] = word;
+  }
+  return bad;
+}
+
 // Warp-cooperative packing of one sequence per pair slot of a warp (P pair
 // slots of G lanes).  When the active slots' sequences lie in one span of at
 // most 16 * SPAN_CHUNKS bytes (aligned 16-byte chunks), the warp copies the
@@ -201,98 +304,83 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // than plain loads (host memory read over the link).
 // Returns, per slot, whether every byte of its sequence is A/C/G/T.  All 32
 // lanes call it.
-template <int G, int SPAN_CHUNKS>
-__device__ __forceinline__ bool pack_warp32(const char* seq, int len, bool active, uint32_t* out, int stride,
-                                            uint32_t* scratch, int lane, unsigned gmask, bool async_copy) {
-  constexpr unsigned FULL = 0xffffffffu;
+template <int G>
+__device__ __forceinline__ bool pack_span_warp32(const WarpSpan& sp, const char* seq, int len, bool active,
+                                                 uint32_t* out, int stride, uint32_t* scratch, int lane,
+                                                 unsigned gmask, bool async_copy) {
   const int lane32 = threadIdx.x & 31;
-  const unsigned long long a = reinterpret_cast<uintptr_t>(seq);
-  unsigned long long lo = active && len > 0 ? a : ~0ull;
-  unsigned long long hi = active && len > 0 ? a + (unsigned)len : 0ull;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long l2 = __shfl_xor_sync(FULL, lo, o), h2 = __shfl_xor_sync(FULL, hi, o);
-    lo = l2 < lo ? l2 : lo;
-    hi = h2 > hi ? h2 : hi;
-  }
-  const int nw = (len + 15) >> 4;  // data words of this slot
   bool bad = false;
-  if (hi > lo && hi - (lo & ~15ull) <= 16ull * SPAN_CHUNKS) {
-    const unsigned long long base = lo & ~15ull;
-    const int nch = (int)((hi - base + 15) >> 4);
-    uint2* ent = reinterpret_cast<uint2*>(scratch);  // (2-bit codes, bad-byte mask) per chunk
+  if (sp.fits) {
     if (async_copy) {
-      // device memory: every chunk of the span is copied to shared memory
-      // asynchronously (all loads in flight at once), then converted in
-      // place, 32 chunks a round: a round writes its 8-byte entries below
-      // the raw bytes of the rounds still to come
-      for (int c = lane32; c < nch; c += 32)
-        cp_async16(scratch + 4 * c, reinterpret_cast<const void*>(base + 16ull * c));
+      // device memory: every chunk copied to shared memory asynchronously
+      // (all loads in flight at once), then converted in place
+      for (int c = lane32; c < sp.nch; c += 32)
+        cp_async16(scratch + 4 * c, reinterpret_cast<const void*>(sp.base + 16ull * c));
       cp_async_wait_all();
       __syncwarp();
-      const uint4* raw = reinterpret_cast<const uint4*>(scratch);
-      for (int c0 = 0; c0 < nch; c0 += 32) {
-        const int c = c0 + lane32;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (c < nch) v = raw[c];
-        __syncwarp();
-        if (c < nch) {
-          uint32_t b16;
-          const uint32_t code = code16_bad(v, &b16);
-          ent[c] = make_uint2(code, b16);
-        }
-      }
+      convert_span(scratch, sp.nch, lane32);
     } else {
       // page-locked host memory read in place: plain coalesced loads (the
       // asynchronous copies measured slower over the host link)
-      for (int c = lane32; c < nch; c += 32) {
+      uint2* ent = reinterpret_cast<uint2*>(scratch);
+      for (int c = lane32; c < sp.nch; c += 32) {
         uint32_t b16;
-        const uint32_t code = code16_bad(__ldg(reinterpret_cast<const uint4*>(base + 16ull * c)), &b16);
+        const uint32_t code = code16_bad(__ldg(reinterpret_cast<const uint4*>(sp.base + 16ull * c)), &b16);
         ent[c] = make_uint2(code, b16);
       }
+      __syncwarp();
+      if (lane32 == 0) ent[sp.nch] = make_uint2(0u, 0u);
+      __syncwarp();
     }
-    __syncwarp();
-    if (lane32 == 0) ent[nch] = make_uint2(0u, 0u);
-    __syncwarp();
-    if (active) {
-      const int off = (int)(a - base);  // bytes from the span start
-      const int c0 = off >> 4, r = (off & 15) << 1;
-      for (int j = lane; j <= nw; j += G) {
-        uint32_t word = 0u;
-        if (j < nw) {
-          const uint2 e0 = ent[c0 + j], e1 = ent[c0 + j + 1];
-          word = __funnelshift_l(e1.x, e0.x, r);
-          const int rem = len - 16 * j;
-          if (rem < 16) word &= ~0u << (32 - 2 * rem);
-          // bad bytes among this word's 16 (at most 2 chunks)
-          const uint32_t m2 = e0.y | (e1.y << 16);
-          const int nb = min(16, rem);
-          const uint32_t in = (nb >= 16 ? 0xFFFFu : ((1u << nb) - 1u)) << (off & 15);
-          if (m2 & in) bad = true;
-        }
-        out[j * stride] = word;
-      }
-    }
+    if (active) bad = cut_words<G>(reinterpret_cast<const uint2*>(scratch), sp.base, seq, len, out, stride, lane);
     __syncwarp();
   } else if (active) {
-    for (int j = lane; j <= nw; j += G) {
-      uint32_t word = 0u;
-      if (j < nw) {
-        // the 16 bytes of word j span at most two aligned chunks
-        const unsigned long long w0 = a + 16ull * j, b0 = w0 & ~15ull;
-        const int h = (int)(w0 - b0), rem = min(16, len - 16 * j);
-        uint32_t m0, m1 = 0u, c1 = 0u;
-        const uint32_t c0 = code16_bad(__ldg(reinterpret_cast<const uint4*>(b0)), &m0);
-        if (h + rem > 16) c1 = code16_bad(__ldg(reinterpret_cast<const uint4*>(b0 + 16)), &m1);
-        word = __funnelshift_l(c1, c0, 2 * h);
-        if (rem < 16) word &= ~0u << (32 - 2 * rem);
-        const uint32_t in = (rem >= 16 ? 0xFFFFu : ((1u << rem) - 1u)) << h;
-        if ((m0 | (m1 << 16)) & in) bad = true;
-      }
-      out[j * stride] = word;
-    }
+    bad = pack_slot_direct<G>(seq, len, out, stride, lane);
   }
   return __any_sync(gmask, bad) == 0;
+}
+
+template <int G, int SPAN_CHUNKS>
+__device__ __forceinline__ bool pack_warp32(const char* seq, int len, bool active, uint32_t* out, int stride,
+                                            uint32_t* scratch, int lane, unsigned gmask, bool async_copy) {
+  return pack_span_warp32<G>(warp_span(seq, len, active, SPAN_CHUNKS), seq, len, active, out, stride, scratch,
+                             lane, gmask, async_copy);
+}
+
+// Both sequences of the warp's pairs (device memory): when the pattern span
+// and the text span fit the scratch together, one round of asynchronous
+// copies stages both (one wait instead of two), else one sequence after the
+// other.  Sets *okp / *okt per slot as pack_warp32 returns.
+template <int G, int SCRATCH_CHUNKS>
+__device__ __forceinline__ void pack_pair_warp32(const char* pseq, int n, const char* tseq, int m, bool active,
+                                                 uint32_t* pout, uint32_t* tout, int stride, uint32_t* scratch,
+                                                 int lane, unsigned gmask, bool* okp, bool* okt) {
+  const int lane32 = threadIdx.x & 31;
+  const WarpSpan sp = warp_span(pseq, n, active, SCRATCH_CHUNKS);
+  const WarpSpan st = warp_span(tseq, m, active, SCRATCH_CHUNKS);
+  if (sp.fits && st.fits && sp.nch + st.nch <= SCRATCH_CHUNKS) {
+    uint32_t* tscr = scratch + 4 * sp.nch;  // the text span's raw bytes after the pattern's
+    for (int c = lane32; c < sp.nch; c += 32)
+      cp_async16(scratch + 4 * c, reinterpret_cast<const void*>(sp.base + 16ull * c));
+    for (int c = lane32; c < st.nch; c += 32)
+      cp_async16(tscr + 4 * c, reinterpret_cast<const void*>(st.base + 16ull * c));
+    cp_async_wait_all();
+    __syncwarp();
+    // the pattern's entries stay below its own raw bytes, so below the text's
+    convert_span(scratch, sp.nch, lane32);
+    convert_span(tscr, st.nch, lane32);
+    bool badp = false, badt = false;
+    if (active) {
+      badp = cut_words<G>(reinterpret_cast<const uint2*>(scratch), sp.base, pseq, n, pout, stride, lane);
+      badt = cut_words<G>(reinterpret_cast<const uint2*>(tscr), st.base, tseq, m, tout, stride, lane);
+    }
+    __syncwarp();
+    *okp = __any_sync(gmask, badp) == 0;
+    *okt = __any_sync(gmask, badt) == 0;
+  } else {
+    *okp = pack_span_warp32<G>(sp, pseq, n, active, pout, stride, scratch, lane, gmask, true);
+    *okt = pack_span_warp32<G>(st, tseq, m, active, tout, stride, scratch, lane, gmask, true);
+  }
 }
 
 // ----------------------------------------------------------------- extend
