@@ -165,17 +165,41 @@ __global__ void __launch_bounds__(kScanBlock) scan_apply(const int32_t* in, int6
 
 // ---------------------------------------------------------------- compact
 
-__global__ void compact_kernel(int64_t n, const int32_t* nruns, const int64_t* run_src, const uint32_t* runs,
-                               const uint32_t* pool, const int64_t* off, uint32_t* out, int64_t cap,
-                               const Ctrl* ctrl) {
+// One warp per 32 consecutive pairs: the lanes write the pairs' words to
+// consecutive output positions (coalesced); lane w's word belongs to the
+// last of the 32 pairs whose offset is <= its position (binary search over
+// the offsets in shared memory; a pair without runs shares the next pair's
+// offset, so the search lands on a pair that has the word).
+__global__ void __launch_bounds__(kAuxBlock) compact_kernel(int64_t n, const int32_t* nruns, const int64_t* run_src,
+                                                             const uint32_t* runs, const uint32_t* pool,
+                                                             const int64_t* off, uint32_t* out, int64_t cap,
+                                                             const Ctrl* ctrl) {
   if (off[n] > cap || (ctrl && *(volatile const int32_t*)&ctrl->bad_input)) return;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const int c = nruns[i];
-    if (c <= 0) continue;
-    const int64_t o = off[i], src = run_src[i];
-    const uint32_t* r = src >= 0 ? runs + src : pool + (-src - 1);
-    for (int j = 0; j < c; ++j) out[o + j] = r[c - 1 - j];
+  __shared__ int64_t s_off[kAuxBlock / 32][32];
+  __shared__ int64_t s_src[kAuxBlock / 32][32];
+  __shared__ int32_t s_cnt[kAuxBlock / 32][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5 << 5; i0 < n; i0 += nwarps * 32) {
+    const int cnt = n - i0 < 32 ? (int)(n - i0) : 32;
+    const int64_t i = i0 + lane;
+    if (lane < cnt) {
+      s_off[wib][lane] = off[i];
+      s_src[wib][lane] = run_src[i];
+      s_cnt[wib][lane] = nruns[i];
+    }
+    const int64_t begin = off[i0], end = off[i0 + cnt];
+    __syncwarp();
+    for (int64_t w = begin + lane; w < end; w += 32) {
+      int l = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1)
+        if (l + step < cnt && s_off[wib][l + step] <= w) l += step;
+      const int64_t src = s_src[wib][l];
+      const uint32_t* r = src >= 0 ? runs + src : pool + (-src - 1);
+      out[w] = r[s_cnt[wib][l] - 1 - (int)(w - s_off[wib][l])];  // runs are stored last first
+    }
+    __syncwarp();
   }
 }
 
