@@ -269,10 +269,23 @@ int stage_inputs(wfa_gpu_ctx* c, Call& k, int64_t n, bool dev, const char* pat, 
     }
   }
   if ((e = c->scan_tmp.ensure(wfa::scan_tmp_elems(n)))) return map_alloc(e);
+  bool validated = false;
+  if (!poff && !toff) {
+    // back-to-back sequences: both offset scans and the checks in one pass
+    if ((e = c->poff.ensure(n + 1)) || (e = c->toff.ensure(n + 1))) return map_alloc(e);
+    if (!k.ok(cudaMemsetAsync(c->ctrl, 0, sizeof(wfa::Ctrl), st)) ||
+        !k.launched(wfa::launch_offsets_validate(*d_plen, *d_tlen, n, c->poff.p, c->toff.p, c->scan_tmp.p, c->ctrl,
+                                                 st), 3))
+      return WFA_GPU_ECUDA;
+    *d_poff = c->poff.p;
+    *d_toff = c->toff.p;
+    validated = true;
+  }
   // offsets: caller's (staged if host) or the exclusive scan of the lengths
   const void* mpo = (poff && !dev) ? mapped_range(poff, n * sizeof(int64_t)) : nullptr;
   const void* mto = (toff && !dev) ? mapped_range(toff, n * sizeof(int64_t)) : nullptr;
-  if (poff && dev) {
+  if (validated) {
+  } else if (poff && dev) {
     *d_poff = poff;
   } else if (mpo) {
     *d_poff = static_cast<const int64_t*>(mpo);
@@ -285,7 +298,8 @@ int stage_inputs(wfa_gpu_ctx* c, Call& k, int64_t n, bool dev, const char* pat, 
     }
     *d_poff = c->poff.p;
   }
-  if (toff && dev) {
+  if (validated) {
+  } else if (toff && dev) {
     *d_toff = toff;
   } else if (mto) {
     *d_toff = static_cast<const int64_t*>(mto);
@@ -298,8 +312,9 @@ int stage_inputs(wfa_gpu_ctx* c, Call& k, int64_t n, bool dev, const char* pat, 
     }
     *d_toff = c->toff.p;
   }
-  if (!k.ok(cudaMemsetAsync(c->ctrl, 0, sizeof(wfa::Ctrl), st))) return WFA_GPU_ECUDA;
-  if (!k.launched(wfa::launch_validate(n, *d_poff, *d_plen, *d_toff, *d_tlen, c->ctrl, st))) return WFA_GPU_ECUDA;
+  if (!validated && (!k.ok(cudaMemsetAsync(c->ctrl, 0, sizeof(wfa::Ctrl), st)) ||
+                     !k.launched(wfa::launch_validate(n, *d_poff, *d_plen, *d_toff, *d_tlen, c->ctrl, st))))
+    return WFA_GPU_ECUDA;
   if (!k.ok(d2h(c->h_ctrl, c->ctrl, sizeof(wfa::Ctrl), st)) || !k.ok(cudaStreamSynchronize(st)))
     return WFA_GPU_ECUDA;
   if (c->h_ctrl->bad_input) return WFA_GPU_EINVAL;
@@ -927,15 +942,23 @@ int enqueue_device_work(wfa_gpu_ctx* c, Call& k, int64_t n, const char* pat, con
   if (!k.ok(cudaMemsetAsync(c->ctrl, 0, sizeof(wfa::Ctrl), st))) return WFA_GPU_ECUDA;
   const int64_t* d_poff = poff;
   const int64_t* d_toff = toff;
-  if (!d_poff) {
-    if (!k.launched(wfa::launch_scan(plen, n, 0, c->poff.p, c->scan_tmp.p, st), 3)) return WFA_GPU_ECUDA;
+  if (!poff && !toff) {
+    if (!k.launched(wfa::launch_offsets_validate(plen, tlen, n, c->poff.p, c->toff.p, c->scan_tmp.p, c->ctrl, st),
+                    3))
+      return WFA_GPU_ECUDA;
     d_poff = c->poff.p;
-  }
-  if (!d_toff) {
-    if (!k.launched(wfa::launch_scan(tlen, n, 0, c->toff.p, c->scan_tmp.p, st), 3)) return WFA_GPU_ECUDA;
     d_toff = c->toff.p;
+  } else {
+    if (!d_poff) {
+      if (!k.launched(wfa::launch_scan(plen, n, 0, c->poff.p, c->scan_tmp.p, st), 3)) return WFA_GPU_ECUDA;
+      d_poff = c->poff.p;
+    }
+    if (!d_toff) {
+      if (!k.launched(wfa::launch_scan(tlen, n, 0, c->toff.p, c->scan_tmp.p, st), 3)) return WFA_GPU_ECUDA;
+      d_toff = c->toff.p;
+    }
+    if (!k.launched(wfa::launch_validate(n, d_poff, plen, d_toff, tlen, c->ctrl, st))) return WFA_GPU_ECUDA;
   }
-  if (!k.launched(wfa::launch_validate(n, d_poff, plen, d_toff, tlen, c->ctrl, st))) return WFA_GPU_ECUDA;
   if (!k.ok(cudaEventRecordWithFlags(c->ev[1], st, cudaEventRecordExternal))) return WFA_GPU_ECUDA;
   wfa::AlignArgs a = device_args(c, n, pat, d_poff, plen, txt, d_toff, tlen, pen, max_score, score_only,
                                  out_scores, out_status);

@@ -137,7 +137,28 @@ __global__ void __launch_bounds__(kScanBlock) scan_reduce(const int32_t* in, int
   if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
 }
 
+// pattern and text lengths in one pass: the two tile-sum arrays side by side
+__global__ void __launch_bounds__(kScanBlock) scan_reduce2(const int32_t* in1, const int32_t* in2, int64_t n,
+                                                           int64_t* tile_sums) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int64_t a1 = 0, a2 = 0;
+#pragma unroll
+  for (int r = 0; r < kScanRows; ++r) {
+    a1 += scan_value(in1, base + r * kScanBlock + threadIdx.x, n, 0);
+    a2 += scan_value(in2, base + r * kScanBlock + threadIdx.x, n, 0);
+  }
+  int64_t t1, t2;
+  block_exclusive(a1, &t1);
+  block_exclusive(a2, &t2);
+  if (threadIdx.x == 0) {
+    tile_sums[blockIdx.x] = t1;
+    tile_sums[gridDim.x + blockIdx.x] = t2;
+  }
+}
+
+// tile offsets of array blockIdx.x (tile_sums + blockIdx.x * ntiles)
 __global__ void __launch_bounds__(kScanBlock) scan_tiles(int64_t* tile_sums, int64_t ntiles) {
+  tile_sums += (int64_t)blockIdx.x * ntiles;
   int64_t carry = 0;
   for (int64_t b = 0; b < ntiles; b += kScanBlock) {
     const int64_t i = b + threadIdx.x;
@@ -147,6 +168,49 @@ __global__ void __launch_bounds__(kScanBlock) scan_tiles(int64_t* tile_sums, int
     if (i < ntiles) tile_sums[i] = carry + ex;
     carry += total;
   }
+}
+
+// offsets of both sequences (out[n] = the totals) and the input checks of
+// validate_kernel on the way (lengths in range; offsets come from the scan)
+__global__ void __launch_bounds__(kScanBlock) scan_apply2_validate(const int32_t* in1, const int32_t* in2, int64_t n,
+                                                                   const int64_t* tile_off, int64_t* out1,
+                                                                   int64_t* out2, Ctrl* ctrl) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int64_t c1 = tile_off[blockIdx.x], c2 = tile_off[gridDim.x + blockIdx.x];
+  long long pe = 0, te = 0;
+  int ml = 0;
+  bool bad = false;
+  for (int r = 0; r < kScanRows; ++r) {
+    const int64_t i = base + r * kScanBlock + threadIdx.x;
+    const int64_t v1 = scan_value(in1, i, n, 0), v2 = scan_value(in2, i, n, 0);
+    int64_t t1, t2;
+    const int64_t e1 = block_exclusive(v1, &t1);
+    const int64_t e2 = block_exclusive(v2, &t2);
+    if (i <= n) {
+      out1[i] = c1 + e1;
+      out2[i] = c2 + e2;
+    }
+    if (i < n) {
+      if (v1 < 0 || v2 < 0 || v1 > ((1 << 28) - 1) || v2 > ((1 << 28) - 1)) {
+        bad = true;
+      } else {
+        pe = max(pe, (long long)(c1 + e1 + v1));
+        te = max(te, (long long)(c2 + e2 + v2));
+        ml = max(ml, (int)max(v1, v2));
+      }
+    }
+    c1 += t1;
+    c2 += t2;
+  }
+  pe = warp_max64(pe);
+  te = warp_max64(te);
+  ml = __reduce_max_sync(0xffffffffu, ml);
+  if ((threadIdx.x & 31) == 0) {
+    if (pe) atomicMax(&ctrl->pat_extent, pe);
+    if (te) atomicMax(&ctrl->txt_extent, te);
+    if (ml) atomicMax(&ctrl->max_len, ml);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(&ctrl->bad_input, 1);
 }
 
 __global__ void __launch_bounds__(kScanBlock) scan_apply(const int32_t* in, int64_t n, int kind,
@@ -432,7 +496,17 @@ cudaError_t launch_validate(int64_t n, const int64_t* poff, const int32_t* plen,
   return cudaGetLastError();
 }
 
-int64_t scan_tmp_elems(int64_t n) { return (n + 1 + kScanTile - 1) / kScanTile + 1; }
+// room for two tile-sum arrays (launch_offsets_validate)
+int64_t scan_tmp_elems(int64_t n) { return 2 * ((n + 1 + kScanTile - 1) / kScanTile) + 2; }
+
+cudaError_t launch_offsets_validate(const int32_t* plen, const int32_t* tlen, int64_t n, int64_t* poff,
+                                    int64_t* toff, int64_t* tmp, Ctrl* ctrl, cudaStream_t st) {
+  const int64_t ntiles = (n + 1 + kScanTile - 1) / kScanTile;
+  scan_reduce2<<<(unsigned)ntiles, kScanBlock, 0, st>>>(plen, tlen, n, tmp);
+  scan_tiles<<<2, kScanBlock, 0, st>>>(tmp, ntiles);
+  scan_apply2_validate<<<(unsigned)ntiles, kScanBlock, 0, st>>>(plen, tlen, n, tmp, poff, toff, ctrl);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_scan(const int32_t* in, int64_t n, int kind, int64_t* out, int64_t* tmp, cudaStream_t st) {
   // tiles cover indices 0..n (out[n] is the total)

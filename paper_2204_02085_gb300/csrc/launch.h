@@ -107,6 +107,12 @@ constexpr int kSortBuckets = 64;
 cudaError_t launch_sort_longest_first(const AlignArgs& a, const int32_t* list, const int32_t* count, int64_t n_cap,
                                       int32_t* aux, int32_t* out, cudaStream_t st);
 
+// Offsets of back-to-back patterns and texts (both exclusive scans of the
+// lengths, [n] = totals) and the checks and extents of launch_validate, in
+// one pass of three kernels; ctrl must be zeroed first.
+cudaError_t launch_offsets_validate(const int32_t* plen, const int32_t* tlen, int64_t n, int64_t* poff,
+                                    int64_t* toff, int64_t* tmp, Ctrl* ctrl, cudaStream_t st);
+
 // Validate lengths / offsets, record max(offset + length) extents.
 cudaError_t launch_validate(int64_t n, const int64_t* poff, const int32_t* plen, const int64_t* toff,
                             const int32_t* tlen, Ctrl* ctrl, cudaStream_t st);
