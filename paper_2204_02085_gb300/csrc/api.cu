@@ -106,7 +106,8 @@ struct wfa_gpu_ctx {
   int32_t* arena = nullptr;
   size_t arena_bytes = 0;
   int teams_medium = 1;  // one-warp arena teams
-  int teams_long = 1;    // one-CTA arena teams
+  int teams_long = 1;    // one-CTA arena teams of kLongTeamWide warps
+  int teams_narrow = 1;  // one-CTA arena teams of kLongTeamNarrow warps
   wfa::ShortPlan plan{};
   // short-kernel variants (indices into plan.v), per penalty model (0
   // gap-affine, 1 gap-linear): candidates for sequences <= 127 bases,
@@ -346,6 +347,15 @@ int stage_inputs(wfa_gpu_ctx* c, Call& k, int64_t n, bool dev, const char* pat, 
 
 int run_retries(wfa_gpu_ctx* c, Call& k, wfa::AlignArgs& a);
 
+// Long pairs go to narrow one-CTA teams when there are more than this many.
+// A narrow team has half the threads: about 1.2x the wide teams' throughput
+// over many pairs, but each pair takes about 1.65x longer, and a call ends
+// with its last pairs; past about four waves of wide teams the throughput
+// wins.  Never when the arena gives no more narrow teams than wide ones.
+int narrow_above(const wfa_gpu_ctx* c) {
+  return c->teams_narrow > c->teams_long ? 4 * c->teams_long : INT32_MAX;
+}
+
 // The arena kernels over the pairs the short kernel deferred (medium pairs
 // on one-warp teams, long ones on one-CTA teams), then retries of the pairs
 // that did not fit: fewer, larger arena slices on one-CTA teams, or a larger
@@ -374,12 +384,13 @@ int run_arena(wfa_gpu_ctx* c, Call& k, wfa::AlignArgs& a, bool longest_first) {
   // no more teams than pairs: small batches leave the GPU to concurrent work
   // and get larger arena slices
   const int tm = std::min<int>(c->teams_medium, hc->defer_count);
-  const int tl = std::min<int>(c->teams_long, hc->defer_long_count);
-  if (tm > 0 && !k.launched(wfa::launch_arena(false, a, medium, &dc->defer_count, &dc->next_medium,
+  const bool narrow = hc->defer_long_count > narrow_above(c);
+  const int tl = std::min<int>(narrow ? c->teams_narrow : c->teams_long, hc->defer_long_count);
+  if (tm > 0 && !k.launched(wfa::launch_arena(1, a, medium, &dc->defer_count, &dc->next_medium,
                                               &dc->overflow_count, reinterpret_cast<unsigned char*>(c->arena),
                                               (arena / tm) & ~255L, tm, st)))
     return WFA_GPU_ECUDA;
-  if (tl > 0 && !k.launched(wfa::launch_arena(true, a, lng, &dc->defer_long_count, &dc->next_long,
+  if (tl > 0 && !k.launched(wfa::launch_arena(narrow ? wfa::kLongTeamNarrow : wfa::kLongTeamWide, a, lng, &dc->defer_long_count, &dc->next_long,
                                               &dc->overflow_count, reinterpret_cast<unsigned char*>(c->arena),
                                               (arena / tl) & ~255L, tl, st)))
     return WFA_GPU_ECUDA;
@@ -428,7 +439,7 @@ int run_retries(wfa_gpu_ctx* c, Call& k, wfa::AlignArgs& a) {
     wfa::AlignArgs ar = a;
     ar.overflow_list = out;
     const int nt = std::max(1, std::min(teams, hc->retry_count));
-    if (!k.launched(wfa::launch_arena(true, ar, in, &dc->retry_count, &dc->next_retry, &dc->overflow_count,
+    if (!k.launched(wfa::launch_arena(wfa::kLongTeamWide, ar, in, &dc->retry_count, &dc->next_retry, &dc->overflow_count,
                                       reinterpret_cast<unsigned char*>(c->arena), (arena / nt) & ~255L, nt, st)))
       return WFA_GPU_ECUDA;
     if (!k.ok(d2h(hc, dc, sizeof(wfa::Ctrl), st)) || !k.ok(cudaStreamSynchronize(st))) return WFA_GPU_ECUDA;
@@ -541,21 +552,27 @@ int wfa_gpu_create(wfa_gpu_ctx** out, int device, size_t scratch_bytes) {
     int nsm = 1;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
     // as many teams as fit on the GPU at once, each with an arena slice of
-    // at least 256 KiB (one-warp teams) or 4 MiB (one-CTA teams); pairs that
-    // outgrow their slice are retried with larger ones
-    int tm = 16, tl = 2;
-    if (wfa::arena_occupancy(false, &tm) != cudaSuccess || wfa::arena_occupancy(true, &tl) != cudaSuccess) {
+    // at least 256 KiB (one-warp teams), 4 MiB (wide one-CTA teams) or 8 MiB
+    // (narrow ones, which run many more pairs at once: smaller slices sent
+    // pairs of a few kbp to the retries); pairs that outgrow their slice are
+    // retried with larger ones
+    int tm = 16, tl = 2, tn = 4;
+    if (wfa::arena_occupancy(1, &tm) != cudaSuccess || wfa::arena_occupancy(wfa::kLongTeamWide, &tl) != cudaSuccess ||
+        wfa::arena_occupancy(wfa::kLongTeamNarrow, &tn) != cudaSuccess) {
       rc = WFA_GPU_ECUDA;
       break;
     }
     const long arena_b = (long)c->arena_bytes;
     c->teams_medium = (int)std::max(1L, std::min((long)nsm * tm, arena_b / (256L << 10)));
     c->teams_long = (int)std::max(1L, std::min((long)nsm * tl, arena_b / (4L << 20)));
-    if (const char* ev = std::getenv("WFA_GPU_TEAMS")) {  // tuning override: "<medium>,<long>"
-      int a = 0, b = 0;
-      if (std::sscanf(ev, "%d,%d", &a, &b) == 2 && a > 0 && b > 0) {
+    c->teams_narrow = (int)std::max(1L, std::min((long)nsm * tn, arena_b / (8L << 20)));
+    if (const char* ev = std::getenv("WFA_GPU_TEAMS")) {  // tuning override: "<medium>,<wide>[,<narrow>]"
+      int a = 0, b = 0, d = 0;
+      const int got = std::sscanf(ev, "%d,%d,%d", &a, &b, &d);
+      if (got >= 2 && a > 0 && b > 0) {
         c->teams_medium = a;
         c->teams_long = b;
+        c->teams_narrow = got == 3 && d > 0 ? d : b;
       }
     }
   } while (0);
@@ -983,10 +1000,17 @@ int enqueue_device_work(wfa_gpu_ctx* c, Call& k, int64_t n, const char* pat, con
     medium = c->sorted.p;
     lng = c->sorted_long.p;
   }
-  if (!k.launched(wfa::launch_arena(false, a, medium, &dc->defer_count, &dc->next_medium, &dc->overflow_count,
+  // both one-CTA widths: the deferred count picks one on the device
+  const int32_t narrow_lo = narrow_above(c);
+  if (!k.launched(wfa::launch_arena(1, a, medium, &dc->defer_count, &dc->next_medium, &dc->overflow_count,
                                     ab, (arena / c->teams_medium) & ~255L, c->teams_medium, st)) ||
-      !k.launched(wfa::launch_arena(true, a, lng, &dc->defer_long_count, &dc->next_long,
-                                    &dc->overflow_count, ab, (arena / c->teams_long) & ~255L, c->teams_long, st)))
+      !k.launched(wfa::launch_arena(wfa::kLongTeamWide, a, lng, &dc->defer_long_count, &dc->next_long,
+                                    &dc->overflow_count, ab, (arena / c->teams_long) & ~255L, c->teams_long, st, 0,
+                                    narrow_lo)) ||
+      (narrow_lo < INT32_MAX &&
+       !k.launched(wfa::launch_arena(wfa::kLongTeamNarrow, a, lng, &dc->defer_long_count, &dc->next_long,
+                                     &dc->overflow_count, ab, (arena / c->teams_narrow) & ~255L, c->teams_narrow, st,
+                                     narrow_lo))))
     return WFA_GPU_ECUDA;
   if (!k.ok(cudaEventRecordWithFlags(c->ev[3], st, cudaEventRecordExternal))) return WFA_GPU_ECUDA;
   if (!score_only) {

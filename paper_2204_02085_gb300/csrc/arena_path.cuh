@@ -375,7 +375,6 @@ __device__ void arena_body(const AlignArgs& a, const int32_t* list, const int32_
   const int team = WPP == 1 ? (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) : (int)blockIdx.x;
   if (team >= nteams) return;  // whole team: uniform
   if (*(volatile const int32_t*)&a.ctrl->bad_input) return;  // inputs rejected by the validation kernel
-  if (*(volatile const int32_t*)count == 0) return;  // nothing deferred (a graph replays the launch anyway)
   const int team_in_block = WPP == 1 ? (int)(threadIdx.x >> 5) : 0;
   // seq_words 64-bit words per sequence = 2 * seq_words 32-bit words
   const size_t team_smem = sizeof(TeamShm) + 2 * (size_t)seq_words * sizeof(uint64_t);

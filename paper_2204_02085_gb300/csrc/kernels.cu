@@ -34,8 +34,13 @@ __global__ void __launch_bounds__(kShortBlock, 8) short_kernel(const AlignArgs a
 template <int WPP>
 __global__ void __launch_bounds__(WPP == 1 ? 128 : 32 * WPP)
     arena_kernel(const AlignArgs a, const int32_t* list, const int32_t* count, int32_t* next, int32_t* overflow_count,
-                 unsigned char* arena, long slot_bytes, int nteams, int seq_words) {
+                 unsigned char* arena, long slot_bytes, int nteams, int seq_words, int32_t count_lo,
+                 int32_t count_hi) {
   extern __shared__ __align__(16) unsigned char smem[];
+  const int32_t c = *(volatile const int32_t*)count;
+  // nothing deferred (a graph replays the launch anyway), or the other team
+  // width takes this list
+  if (c <= count_lo || c > count_hi) return;
   arena_body<WPP>(a, list, count, next, overflow_count, arena, slot_bytes, nteams, seq_words, smem);
 }
 
@@ -411,10 +416,14 @@ cudaError_t short_plan(int device, ShortPlan* plan) {
   if ((e = plan_one<2, 255, 256, 31, int16_t, true, true>(device, &plan->v[i++], "g2_l255_c256_lin_i16_ef")))
     return e;
   plan->count = i;
-  // the one-CTA arena kernel keeps two sequences of up to 32,768 bases in
+  // the one-CTA arena kernels keep two sequences of up to 32,768 bases in
   // shared memory
   const size_t arena_smem = sizeof(TeamShm) + 2 * (size_t)(32768 / 32 + 2) * sizeof(uint64_t);
-  return cudaFuncSetAttribute(arena_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)arena_smem);
+  if ((e = cudaFuncSetAttribute(arena_kernel<kLongTeamWide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)arena_smem)))
+    return e;
+  return cudaFuncSetAttribute(arena_kernel<kLongTeamNarrow>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)arena_smem);
 }
 
 cudaError_t launch_short(const AlignArgs& a, const ShortVariant& v, cudaStream_t st) {
@@ -433,40 +442,48 @@ cudaError_t launch_route_all(const AlignArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t arena_occupancy(bool long_team, int* teams_per_sm) {
+cudaError_t arena_occupancy(int team_warps, int* teams_per_sm) {
   int per_sm = 0;
   cudaError_t e;
-  if (!long_team) {
+  if (team_warps == 1) {
     const int seq_words = kMediumMaxLen / 32 + 2;
     const size_t smem = 4 * (sizeof(TeamShm) + 2 * (size_t)seq_words * sizeof(uint64_t));
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, arena_kernel<1>, 128, smem);
     *teams_per_sm = 4 * per_sm;
   } else {
     const size_t smem = sizeof(TeamShm) + 2 * (size_t)(32768 / 32 + 2) * sizeof(uint64_t);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, arena_kernel<8>, 256, smem);
+    e = team_warps == kLongTeamNarrow
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, arena_kernel<kLongTeamNarrow>,
+                                                            32 * kLongTeamNarrow, smem)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, arena_kernel<kLongTeamWide>, 32 * kLongTeamWide,
+                                                            smem);
     *teams_per_sm = per_sm;
   }
   if (*teams_per_sm < 1) *teams_per_sm = 1;
   return e;
 }
 
-cudaError_t launch_arena(bool long_team, const AlignArgs& a, const int32_t* list, const int32_t* count,
+cudaError_t launch_arena(int team_warps, const AlignArgs& a, const int32_t* list, const int32_t* count,
                          int32_t* next, int32_t* overflow_count, unsigned char* arena, long slot_bytes, int nteams,
-                         cudaStream_t st) {
+                         cudaStream_t st, int32_t count_lo, int32_t count_hi) {
   if (nteams < 1) return cudaSuccess;
-  if (!long_team) {
+  if (team_warps == 1) {
     // four one-warp teams per block; sequences of medium pairs in shared memory
     const int seq_words = kMediumMaxLen / 32 + 2;
     const size_t smem = 4 * (sizeof(TeamShm) + 2 * (size_t)seq_words * sizeof(uint64_t));
     const int grid = (nteams + 3) / 4;
     arena_kernel<1><<<grid, 128, smem, st>>>(a, list, count, next, overflow_count, arena, slot_bytes, nteams,
-                                            seq_words);
+                                            seq_words, count_lo, count_hi);
   } else {
     // one CTA per team; sequences up to 32,768 bases in shared memory
     const int seq_words = 32768 / 32 + 2;
     const size_t smem = sizeof(TeamShm) + 2 * (size_t)seq_words * sizeof(uint64_t);
-    arena_kernel<8><<<nteams, 256, smem, st>>>(a, list, count, next, overflow_count, arena, slot_bytes, nteams,
-                                              seq_words);
+    if (team_warps == kLongTeamNarrow)
+      arena_kernel<kLongTeamNarrow><<<nteams, 32 * kLongTeamNarrow, smem, st>>>(
+          a, list, count, next, overflow_count, arena, slot_bytes, nteams, seq_words, count_lo, count_hi);
+    else
+      arena_kernel<kLongTeamWide><<<nteams, 32 * kLongTeamWide, smem, st>>>(
+          a, list, count, next, overflow_count, arena, slot_bytes, nteams, seq_words, count_lo, count_hi);
   }
   return cudaGetLastError();
 }

@@ -61,6 +61,11 @@ struct AlignArgs {
 // longest sequence handled by a one-warp arena team; longer pairs go to a
 // one-CTA team
 constexpr int kMediumMaxLen = 2048;
+// A one-CTA arena team (pairs longer than kMediumMaxLen) has 8 warps when
+// few long pairs are deferred (each pair's latency sets the call's) and 4
+// when they outnumber the 8-warp teams that fit (more teams in flight).
+constexpr int kLongTeamWide = 8;
+constexpr int kLongTeamNarrow = 4;
 
 constexpr int kSlot = 16;  // CIGAR runs a short-kernel pair may keep
 
@@ -91,11 +96,16 @@ cudaError_t launch_short(const AlignArgs& a, const ShortVariant& v, cudaStream_t
 // The plain path: every pair onto the arena work lists.
 cudaError_t launch_route_all(const AlignArgs& a, cudaStream_t st);
 
-// Resident teams per SM of an arena kernel (occupancy calculator).
-cudaError_t arena_occupancy(bool long_team, int* teams_per_sm);
-cudaError_t launch_arena(bool long_team, const AlignArgs& a, const int32_t* list, const int32_t* count,
+// Resident teams per SM of an arena kernel with teams of team_warps warps
+// (1: one-warp teams of medium pairs; kLongTeamWide or kLongTeamNarrow:
+// one-CTA teams of long pairs).
+cudaError_t arena_occupancy(int team_warps, int* teams_per_sm);
+// The launch works through the list only while count_lo < *count <=
+// count_hi: a graph holds both one-CTA widths and the count, known on the
+// device only, picks the one that runs.
+cudaError_t launch_arena(int team_warps, const AlignArgs& a, const int32_t* list, const int32_t* count,
                          int32_t* next, int32_t* overflow_count, unsigned char* arena, long slot_bytes, int nteams,
-                         cudaStream_t st);
+                         cudaStream_t st, int32_t count_lo = 0, int32_t count_hi = 0x7fffffff);
 
 // Longest-first order of a work list (batched path): list[0 .. *count) ->
 // out, by the longer sequence of each pair in kSortBuckets equal-width
