@@ -85,6 +85,7 @@ bool pen_ok(const wfa_gpu_penalties& p) {
 }
 
 constexpr int kEvents = 6;  // start, inputs, align, general, cigar, end
+constexpr int kRing = 3;    // ring slots of streamed inputs: copies run two chunks ahead
 constexpr int64_t kPoolInitWords = 1 << 22;
 
 }  // namespace
@@ -102,6 +103,12 @@ struct wfa_gpu_ctx {
   // chunk's work (stream and events of the context)
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_chunk = nullptr, ev_copied = nullptr;
+  // chunked calls with page-locked, back-to-back host sequences: chunk c's
+  // bases go to ring slot c % kRing (patterns, then texts) on in_stream
+  // while the chunks before compute; ev_in[s]: slot s filled, ev_free[s]:
+  // its last reader done
+  cudaStream_t in_stream = nullptr;
+  cudaEvent_t ev_in[kRing] = {}, ev_free[kRing] = {};
   cudaStream_t stream = nullptr;
   int32_t* arena = nullptr;
   size_t arena_bytes = 0;
@@ -125,6 +132,9 @@ struct wfa_gpu_ctx {
   wfa::Ctrl* ctrl = nullptr;    // device
   wfa::Ctrl* h_ctrl = nullptr;  // pinned host mirror
   int64_t* h_total = nullptr;   // pinned host scalar
+  // device addresses of h_ctrl and h_total (kernels write them)
+  wfa::Ctrl* h_ctrl_dev = nullptr;
+  int64_t* h_total_dev = nullptr;
   cudaEvent_t ev[kEvents] = {};
   wfa_gpu_timing last{};
   // inputs staged from host memory, and computed offsets
@@ -139,6 +149,9 @@ struct wfa_gpu_ctx {
   DevBuf<uint32_t> cig;
   // page-locked staging of pageable host outputs (bytes)
   HostBuf<unsigned char> h_score, h_status, h_off, h_cig;
+  // streamed inputs: the device ring and the chunks' first offsets
+  DevBuf<char> ring;
+  HostBuf<int64_t> h_bounds;
   // internal
   DevBuf<int32_t> nruns, defer, defer_long, overflow;
   DevBuf<int32_t> sorted, sorted_long, sort_aux;  // longest-first work lists (batched path)
@@ -193,6 +206,20 @@ struct Call {
 int fail_cuda(Call& k) {
   (void)k;
   return WFA_GPU_ECUDA;
+}
+
+// The control block and the CIGAR word total to their page-locked host
+// mirrors, and a control block to the device, as one-block kernels rather
+// than copies: on a host-pointer call the copy engines may be busy with
+// bulk copies of other streams or contexts (launch_put_ctrl says why).
+bool ctrl_to_host(Call& k, cudaStream_t st) {
+  return k.launched(wfa::launch_copy_small(k.c->h_ctrl_dev, k.c->ctrl, sizeof(wfa::Ctrl), st));
+}
+bool total_to_host(Call& k, const int64_t* src, cudaStream_t st) {
+  return k.launched(wfa::launch_copy_small(k.c->h_total_dev, src, sizeof(int64_t), st));
+}
+bool ctrl_to_device(Call& k, wfa::Ctrl* dst, const wfa::Ctrl& v, cudaStream_t st) {
+  return k.launched(wfa::launch_put_ctrl(dst, v, st));
 }
 
 int map_alloc(cudaError_t e) { return e == cudaErrorMemoryAllocation ? WFA_GPU_ENOMEM : WFA_GPU_ECUDA; }
@@ -274,7 +301,7 @@ int stage_inputs(wfa_gpu_ctx* c, Call& k, int64_t n, bool dev, const char* pat, 
   if (!poff && !toff) {
     // back-to-back sequences: both offset scans and the checks in one pass
     if ((e = c->poff.ensure(n + 1)) || (e = c->toff.ensure(n + 1))) return map_alloc(e);
-    if (!k.ok(cudaMemsetAsync(c->ctrl, 0, sizeof(wfa::Ctrl), st)) ||
+    if (!ctrl_to_device(k, c->ctrl, wfa::Ctrl{}, st) ||
         !k.launched(wfa::launch_offsets_validate(*d_plen, *d_tlen, n, c->poff.p, c->toff.p, c->scan_tmp.p, c->ctrl,
                                                  st), 3))
       return WFA_GPU_ECUDA;
@@ -313,11 +340,10 @@ int stage_inputs(wfa_gpu_ctx* c, Call& k, int64_t n, bool dev, const char* pat, 
     }
     *d_toff = c->toff.p;
   }
-  if (!validated && (!k.ok(cudaMemsetAsync(c->ctrl, 0, sizeof(wfa::Ctrl), st)) ||
+  if (!validated && (!ctrl_to_device(k, c->ctrl, wfa::Ctrl{}, st) ||
                      !k.launched(wfa::launch_validate(n, *d_poff, *d_plen, *d_toff, *d_tlen, c->ctrl, st))))
     return WFA_GPU_ECUDA;
-  if (!k.ok(d2h(c->h_ctrl, c->ctrl, sizeof(wfa::Ctrl), st)) || !k.ok(cudaStreamSynchronize(st)))
-    return WFA_GPU_ECUDA;
+  if (!ctrl_to_host(k, st) || !k.ok(cudaStreamSynchronize(st))) return WFA_GPU_ECUDA;
   if (c->h_ctrl->bad_input) return WFA_GPU_EINVAL;
   if (dev) {
     *d_pat = pat;
@@ -394,7 +420,7 @@ int run_arena(wfa_gpu_ctx* c, Call& k, wfa::AlignArgs& a, bool longest_first) {
                                               &dc->overflow_count, reinterpret_cast<unsigned char*>(c->arena),
                                               (arena / tl) & ~255L, tl, st)))
     return WFA_GPU_ECUDA;
-  if (!k.ok(d2h(hc, dc, sizeof(wfa::Ctrl), st)) || !k.ok(cudaStreamSynchronize(st))) return WFA_GPU_ECUDA;
+  if (!ctrl_to_host(k, st) || !k.ok(cudaStreamSynchronize(st))) return WFA_GPU_ECUDA;
   return run_retries(c, k, a);
 }
 
@@ -435,14 +461,14 @@ int run_retries(wfa_gpu_ctx* c, Call& k, wfa::AlignArgs& a) {
     hc->next_retry = 0;
     hc->overflow_count = 0;
     hc->pool_short = 0;
-    if (!k.ok(cudaMemcpyAsync(dc, hc, sizeof(wfa::Ctrl), cudaMemcpyHostToDevice, st))) return WFA_GPU_ECUDA;
+    if (!ctrl_to_device(k, dc, *hc, st)) return WFA_GPU_ECUDA;
     wfa::AlignArgs ar = a;
     ar.overflow_list = out;
     const int nt = std::max(1, std::min(teams, hc->retry_count));
     if (!k.launched(wfa::launch_arena(wfa::kLongTeamWide, ar, in, &dc->retry_count, &dc->next_retry, &dc->overflow_count,
                                       reinterpret_cast<unsigned char*>(c->arena), (arena / nt) & ~255L, nt, st)))
       return WFA_GPU_ECUDA;
-    if (!k.ok(d2h(hc, dc, sizeof(wfa::Ctrl), st)) || !k.ok(cudaStreamSynchronize(st))) return WFA_GPU_ECUDA;
+    if (!ctrl_to_host(k, st) || !k.ok(cudaStreamSynchronize(st))) return WFA_GPU_ECUDA;
     std::swap(in, out);
   }
   return 0;
@@ -520,10 +546,16 @@ int wfa_gpu_create(wfa_gpu_ctx** out, int device, size_t scratch_bytes) {
     if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) { rc = WFA_GPU_ECUDA; break; }
     if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_chunk, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->in_stream, cudaStreamNonBlocking) != cudaSuccess) {
       rc = WFA_GPU_ECUDA;
       break;
     }
+    for (int i = 0; i < kRing; ++i)
+      if (cudaEventCreateWithFlags(&c->ev_in[i], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->ev_free[i], cudaEventDisableTiming) != cudaSuccess)
+        rc = WFA_GPU_ECUDA;
+    if (rc) break;
     c->stream = c->own_stream;
     for (int i = 0; i < kEvents; ++i)
       if (cudaEventCreate(&c->ev[i]) != cudaSuccess) { rc = WFA_GPU_ECUDA; break; }
@@ -534,8 +566,10 @@ int wfa_gpu_create(wfa_gpu_ctx** out, int device, size_t scratch_bytes) {
       rc = WFA_GPU_ENOMEM;
       break;
     }
-    if (cudaHostAlloc(reinterpret_cast<void**>(&c->h_ctrl), sizeof(wfa::Ctrl), cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc(reinterpret_cast<void**>(&c->h_total), sizeof(int64_t), cudaHostAllocDefault) != cudaSuccess) {
+    if (cudaHostAlloc(reinterpret_cast<void**>(&c->h_ctrl), sizeof(wfa::Ctrl), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostAlloc(reinterpret_cast<void**>(&c->h_total), sizeof(int64_t), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->h_ctrl_dev), c->h_ctrl, 0) != cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->h_total_dev), c->h_total, 0) != cudaSuccess) {
       rc = WFA_GPU_ENOMEM;
       break;
     }
@@ -599,19 +633,91 @@ namespace {
 // the whole device sequence (short kernel, arena kernels for its deferred
 // pairs, CIGAR offset scan and compaction, its CIGAR offsets moved to the
 // call's running word count), and its outputs are copied back on the
-// context's copy stream while the next chunk computes.
+// context's copy stream while the next chunk computes.  Page-locked
+// sequences stored back to back (offsets computed here) are streamed in the
+// same way: the copy engine moves later chunks' bases into a device ring
+// while this chunk computes (the link's rate is the same for both, but a
+// kernel that reads host memory in place waits on every load it sends over
+// the link, where the copy engine's transfers hold up no computation).
 constexpr int64_t kPipeMinPairs = 1 << 21;
-constexpr int64_t kPipeChunk = 1 << 20;
+constexpr int64_t kPipeChunk = 1 << 19;
+
+// Host inputs a chunked call streams chunk by chunk (null: none): the
+// sequences, and the lengths when they are page-locked too (else they are
+// on the device already).
+struct StreamIn {
+  const char* pat;
+  const char* txt;
+  const int32_t* plen;
+  const int32_t* tlen;
+};
+
+// Waits for the input stream when a chunked call returns: no copy of the
+// caller's buffers outlives the call, also when it fails.
+struct InStreamDrain {
+  cudaStream_t s;
+  ~InStreamDrain() {
+    if (s) cudaStreamSynchronize(s);
+  }
+};
 
 int align_pipelined(wfa_gpu_ctx* ctx, Call& k, const wfa::AlignArgs& a, int64_t n, bool plain,
                     wfa_gpu_penalties pen, int32_t* out_scores, int8_t* out_status, uint32_t* out_cigars,
-                    int64_t cap, int64_t* out_off) {
-  cudaStream_t st = ctx->stream, cs = ctx->copy_stream;
+                    int64_t cap, int64_t* out_off, const StreamIn* sin) {
+  cudaStream_t st = ctx->stream, cs = ctx->copy_stream, is = ctx->in_stream;
   const bool score_only = a.score_only != 0;
   const int64_t nchunks = (n + kPipeChunk - 1) / kPipeChunk;
   cudaError_t e;
   if (!score_only && (e = ctx->cig_off.ensure(n + nchunks + 1))) return map_alloc(e);
   const wfa::Ctrl staged = *ctx->h_ctrl;  // the whole batch's validation: extents, longest sequence
+  // each chunk's starting control block: counters zero, the batch's extents
+  // and longest sequence kept
+  wfa::Ctrl staged_zero{};
+  staged_zero.pat_extent = staged.pat_extent;
+  staged_zero.txt_extent = staged.txt_extent;
+  staged_zero.max_len = staged.max_len;
+  InStreamDrain drain{sin ? is : nullptr};
+  // streamed inputs: each chunk's first pattern and text offsets (the
+  // device scans'), the ring slot size, and the first chunk's copy
+  // ring slot layout: pattern bases (slot bytes), text bases (slot bytes),
+  // pattern lengths, text lengths (lens bytes each)
+  const int64_t *hp = nullptr, *ht = nullptr;
+  int64_t slot = 0;
+  const int64_t lens = (kPipeChunk * (int64_t)sizeof(int32_t) + 255) & ~(int64_t)255;
+  auto slot_at = [&](int64_t c) { return ctx->ring.p + (size_t)(c % kRing) * (size_t)(2 * slot + 2 * lens); };
+  auto copy_in = [&](int64_t c) -> bool {
+    const int s2 = (int)(c % kRing);
+    char* rp = slot_at(c);
+    const int64_t b = c * kPipeChunk, m = std::min(kPipeChunk, n - b);
+    return k.ok(cudaStreamWaitEvent(is, ctx->ev_free[s2], 0)) &&
+           k.ok(h2d(rp, sin->pat + hp[c], (size_t)(hp[c + 1] - hp[c]), is)) &&
+           k.ok(h2d(rp + slot, sin->txt + ht[c], (size_t)(ht[c + 1] - ht[c]), is)) &&
+           (!sin->plen || (k.ok(h2d(rp + 2 * slot, sin->plen + b, (size_t)m * sizeof(int32_t), is)) &&
+                           k.ok(h2d(rp + 2 * slot + lens, sin->tlen + b, (size_t)m * sizeof(int32_t), is)))) &&
+           k.ok(cudaEventRecord(ctx->ev_in[s2], is));
+  };
+  if (sin) {
+    if ((e = ctx->h_bounds.ensure((size_t)(2 * (nchunks + 1))))) return map_alloc(e);
+    int64_t* hb = ctx->h_bounds.p;
+    const size_t pitch = (size_t)kPipeChunk * sizeof(int64_t);
+    if (!k.ok(cudaMemcpy2DAsync(hb, sizeof(int64_t), a.poff, pitch, sizeof(int64_t), (size_t)nchunks,
+                                cudaMemcpyDeviceToHost, st)) ||
+        !k.ok(cudaMemcpy2DAsync(hb + nchunks + 1, sizeof(int64_t), a.toff, pitch, sizeof(int64_t),
+                                (size_t)nchunks, cudaMemcpyDeviceToHost, st)) ||
+        !k.ok(cudaStreamSynchronize(st)))
+      return fail_cuda(k);
+    // back to back: the scans' totals are the extents
+    hb[nchunks] = staged.pat_extent;
+    hb[2 * nchunks + 1] = staged.txt_extent;
+    hp = hb;
+    ht = hb + nchunks + 1;
+    for (int64_t c = 0; c < nchunks; ++c) slot = std::max(slot, std::max(hp[c + 1] - hp[c], ht[c + 1] - ht[c]));
+    // 16 bytes of slack: the packer reads whole aligned 16-byte chunks
+    slot = (slot + 16 + 255) & ~(int64_t)255;
+    if ((e = ctx->ring.ensure((size_t)(kRing * (2 * slot + 2 * lens))))) return map_alloc(e);
+    for (int64_t c = 0; c < std::min<int64_t>(kRing - 1, nchunks); ++c)
+      if (!copy_in(c)) return fail_cuda(k);
+  }
   int vi = -1;
   int64_t base = 0, deferred = 0;
   bool over = false;
@@ -624,9 +730,24 @@ int align_pipelined(wfa_gpu_ctx* ctx, Call& k, const wfa::AlignArgs& a, int64_t 
     ac.score = a.score + b; ac.status = a.status + b;
     ac.nruns = a.nruns + b; ac.run_src = a.run_src + b;
     ac.runs = a.runs + (score_only ? 0 : b * wfa::kSlot);
-    *ctx->h_ctrl = staged;  // counters zero, the batch's extents kept
-    if (!k.ok(cudaMemcpyAsync(ctx->ctrl, ctx->h_ctrl, sizeof(wfa::Ctrl), cudaMemcpyHostToDevice, st)))
-      return fail_cuda(k);
+    if (sin) {
+      // the chunk's bases at ring slot c % kRing: base addresses moved back by
+      // the chunk's first offsets (integer arithmetic; the kernels add the
+      // pairs' offsets, which land inside the slot)
+      const int s2 = (int)(c % kRing);
+      char* sp = slot_at(c);
+      const uintptr_t rp = reinterpret_cast<uintptr_t>(sp);
+      ac.pat = reinterpret_cast<const char*>(rp - (uintptr_t)hp[c]);
+      ac.txt = reinterpret_cast<const char*>(rp + (uintptr_t)slot - (uintptr_t)ht[c]);
+      ac.host_seqs = 0;
+      if (sin->plen) {
+        ac.plen = reinterpret_cast<const int32_t*>(sp + 2 * slot);
+        ac.tlen = reinterpret_cast<const int32_t*>(sp + 2 * slot + lens);
+      }
+      if (!k.ok(cudaStreamWaitEvent(st, ctx->ev_in[s2], 0))) return fail_cuda(k);
+    }
+    *ctx->h_ctrl = staged_zero;
+    if (!ctrl_to_device(k, ctx->ctrl, staged_zero, st)) return fail_cuda(k);
     if (plain) {
       if (!k.launched(wfa::launch_route_all(ac, st))) return fail_cuda(k);
     } else {
@@ -641,6 +762,8 @@ int align_pipelined(wfa_gpu_ctx* ctx, Call& k, const wfa::AlignArgs& a, int64_t 
       }
       if (!k.launched(wfa::launch_short(ac, ctx->plan.v[vi], st))) return fail_cuda(k);
     }
+    // later chunks' bases move while this one computes
+    if (sin && c + kRing - 1 < nchunks && !copy_in(c + kRing - 1)) return fail_cuda(k);
     if (c == nchunks - 1) k.rec(2);
     // chunk c's CIGAR offsets at [b + c, b + c + m]: apart from chunk c+1's,
     // which may be written while these are still being copied.  One host
@@ -650,10 +773,9 @@ int align_pipelined(wfa_gpu_ctx* ctx, Call& k, const wfa::AlignArgs& a, int64_t 
     int64_t* off_c = score_only ? nullptr : ctx->cig_off.p + b + c;
     auto scan = [&]() -> bool {
       return score_only || (k.launched(wfa::launch_scan(ac.nruns, m, 0, off_c, ctx->scan_tmp.p, st), 3) &&
-                            k.ok(d2h(ctx->h_total, off_c + m, sizeof(int64_t), st)));
+                            total_to_host(k, off_c + m, st));
     };
-    if (!k.ok(d2h(ctx->h_ctrl, ctx->ctrl, sizeof(wfa::Ctrl), st)) || !scan() || !k.ok(cudaStreamSynchronize(st)))
-      return fail_cuda(k);
+    if (!ctrl_to_host(k, st) || !scan() || !k.ok(cudaStreamSynchronize(st))) return fail_cuda(k);
     const int64_t dc = (int64_t)ctx->h_ctrl->defer_count + ctx->h_ctrl->defer_long_count;
     deferred += dc;
     if (dc > 0) {
@@ -661,6 +783,8 @@ int align_pipelined(wfa_gpu_ctx* ctx, Call& k, const wfa::AlignArgs& a, int64_t 
       if (rc) return rc;
       if (!scan() || !k.ok(cudaStreamSynchronize(st))) return fail_cuda(k);
     }
+    // the chunk's bases are read no more: its ring slot may be refilled
+    if (sin && !k.ok(cudaEventRecord(ctx->ev_free[c % kRing], st))) return fail_cuda(k);
     if (ctx->h_ctrl->internal_error) return WFA_GPU_ECUDA;
     if (c == nchunks - 1) k.rec(3);
     int64_t tot = 0;
@@ -802,7 +926,15 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
       mapped_range(out_status, (size_t)n) &&
       (score_only || (mapped_range(out_cigar_offsets, (size_t)(n + 1) * sizeof(int64_t)) &&
                       (cap == 0 || mapped_range(out_cigars, (size_t)cap * sizeof(uint32_t)))))) {
-    rc = align_pipelined(ctx, k, a, n, plain, pen, out_scores, out_status, out_cigars, cap, out_cigar_offsets);
+    const size_t pe = (size_t)ctx->h_ctrl->pat_extent, te = (size_t)ctx->h_ctrl->txt_extent;
+    const bool lens_mapped = mapped_range(pattern_lengths, (size_t)n * sizeof(int32_t)) &&
+                             mapped_range(text_lengths, (size_t)n * sizeof(int32_t));
+    const StreamIn sin{patterns, texts, lens_mapped ? pattern_lengths : nullptr,
+                       lens_mapped ? text_lengths : nullptr};
+    const bool streamed = host_seqs && !pattern_offsets && !text_offsets && mapped_range(patterns, pe) &&
+                          mapped_range(texts, te);
+    rc = align_pipelined(ctx, k, a, n, plain, pen, out_scores, out_status, out_cigars, cap, out_cigar_offsets,
+                         streamed ? &sin : nullptr);
     if (rc < 0 && rc != WFA_GPU_ECIGAR_CAPACITY) return rc;
     ctx->last.kernel_launches = k.launches;
     ctx->last.short_variant = ctx->last_variant;
@@ -830,8 +962,7 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
     if (!k.launched(wfa::launch_short(a, ctx->plan.v[vi], st))) return fail_cuda(k);
   }
   k.rec(2);
-  if (!k.ok(d2h(ctx->h_ctrl, ctx->ctrl, sizeof(wfa::Ctrl), st)) || !k.ok(cudaStreamSynchronize(st)))
-    return fail_cuda(k);
+  if (!ctrl_to_host(k, st) || !k.ok(cudaStreamSynchronize(st))) return fail_cuda(k);
   ctx->last.deferred_pairs = (int64_t)ctx->h_ctrl->defer_count + ctx->h_ctrl->defer_long_count;
   if (ctx->last.deferred_pairs > 0) {
     rc = run_arena(ctx, k, a, !plain);
@@ -849,8 +980,7 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
       d_off = ctx->cig_off.p;
     }
     if (!k.launched(wfa::launch_scan(ctx->nruns.p, n, 0, d_off, ctx->scan_tmp.p, st), 3)) return fail_cuda(k);
-    if (!k.ok(d2h(ctx->h_total, d_off + n, sizeof(int64_t), st)) || !k.ok(cudaStreamSynchronize(st)))
-      return fail_cuda(k);
+    if (!total_to_host(k, d_off + n, st) || !k.ok(cudaStreamSynchronize(st))) return fail_cuda(k);
     total = *ctx->h_total;
     if (total <= cap && total > 0 && sink) {
       out_cigars = ctx->cig_sink(ctx->cig_sink_user, total);
@@ -1297,7 +1427,9 @@ void wfa_gpu_destroy(wfa_gpu_ctx* c) {
   c->overflow.release(); c->run_src.release(); c->scan_tmp.release(); c->runs.release();
   c->sorted.release(); c->sorted_long.release(); c->sort_aux.release();
   c->defer_long.release(); c->pool.release();
+  if (c->in_stream) cudaStreamSynchronize(c->in_stream);
   c->h_score.release(); c->h_status.release(); c->h_off.release(); c->h_cig.release();
+  c->ring.release(); c->h_bounds.release();
   if (c->arena) cudaFree(c->arena);
   if (c->ctrl) cudaFree(c->ctrl);
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
@@ -1315,6 +1447,11 @@ void wfa_gpu_destroy(wfa_gpu_ctx* c) {
   }
   if (c->ev_chunk) cudaEventDestroy(c->ev_chunk);
   if (c->ev_copied) cudaEventDestroy(c->ev_copied);
+  if (c->in_stream) cudaStreamDestroy(c->in_stream);
+  for (int i = 0; i < kRing; ++i) {
+    if (c->ev_in[i]) cudaEventDestroy(c->ev_in[i]);
+    if (c->ev_free[i]) cudaEventDestroy(c->ev_free[i]);
+  }
   delete c;
 }
 

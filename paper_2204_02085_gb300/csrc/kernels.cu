@@ -336,6 +336,14 @@ __global__ void add_kernel(int64_t* p, int64_t count, int64_t v) {
     p[i] += v;
 }
 
+// Small transfers as kernels (see launch_put_ctrl).
+__global__ void put_ctrl_kernel(Ctrl* dst, const Ctrl v) { *dst = v; }
+
+__global__ void copy_small_kernel(uint32_t* dst, const uint32_t* src, int words) {
+  if ((int)threadIdx.x < words) dst[threadIdx.x] = src[threadIdx.x];
+  __threadfence_system();  // page-locked host destination: visible once the stream is done
+}
+
 int sm_count(int device) {
   int v = 0;
   cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
@@ -497,6 +505,22 @@ cudaError_t launch_sort_longest_first(const AlignArgs& a, const int32_t* list, c
   sort_hist_kernel<<<grid, kAuxBlock, 0, st>>>(a, list, count, aux);
   sort_scan_kernel<<<1, 32, 0, st>>>(aux, aux + kSortBuckets);
   sort_scatter_kernel<<<grid, kAuxBlock, 0, st>>>(a, list, count, aux + kSortBuckets, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_put_ctrl(Ctrl* dst, const Ctrl& v, cudaStream_t st) {
+  put_ctrl_kernel<<<1, 1, 0, st>>>(dst, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_small(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return cudaSuccess;
+  if (bytes % 4 != 0 || bytes > 4096 || reinterpret_cast<uintptr_t>(dst) % 4 != 0 ||
+      reinterpret_cast<uintptr_t>(src) % 4 != 0)
+    return cudaErrorInvalidValue;
+  const int words = (int)(bytes / 4);
+  copy_small_kernel<<<1, (unsigned)((words + 31) / 32 * 32), 0, st>>>(static_cast<uint32_t*>(dst),
+                                                                      static_cast<const uint32_t*>(src), words);
   return cudaGetLastError();
 }
 

@@ -143,6 +143,16 @@ cudaError_t launch_compact(int64_t n, const int32_t* nruns, const int64_t* run_s
 // p[0 .. count) += v (int64).
 cudaError_t launch_add(int64_t* p, int64_t count, int64_t v, cudaStream_t st);
 
+// Small transfers as one-block kernels.  A copy engine serves the copies of
+// every stream in order, so a small copy queued behind another stream's
+// bulk copy (a chunk of input bases, a chunk of outputs) waits for all of
+// it; a kernel's loads and stores do not.  launch_put_ctrl writes v (a
+// kernel argument) to dst; launch_copy_small copies bytes (a multiple of 4,
+// at most 4 KiB, both addresses 4-byte aligned; dst may be the device
+// address of page-locked host memory).
+cudaError_t launch_put_ctrl(Ctrl* dst, const Ctrl& v, cudaStream_t st);
+cudaError_t launch_copy_small(void* dst, const void* src, size_t bytes, cudaStream_t st);
+
 // Standalone packer: sequence i -> words[woff[i] ..], invalid[i].
 cudaError_t launch_pack(int64_t n, const char* seqs, const int64_t* off, const int32_t* len, const int64_t* woff,
                         uint64_t* words, int8_t* invalid, cudaStream_t st);

@@ -379,3 +379,75 @@ def test_chunked_host_call_with_page_locked_outputs(pkg, oracle_mod):
             assert np.array_equal(got_off, want[3])
             if code == pkg.WFA_GPU_OK:
                 assert np.array_equal(outs["w"].numpy().view(np.uint32), want[2])
+
+
+def _splice_back_to_back(core, repl):
+    """A back-to-back batch equal to ``core`` (itself back to back) with the
+    pairs at the keys of ``repl`` replaced by the (pattern, text) bytes given
+    there; built from a few large slices."""
+    from paper_2204_02085_gb300 import synth
+
+    idx = sorted(repl)
+    plen = core.pattern_lengths.copy()
+    tlen = core.text_lengths.copy()
+    pats, txts = [], []
+    prev = 0
+    for i in idx:
+        pats.append(core.patterns[core.pattern_offsets[prev]:core.pattern_offsets[i]])
+        txts.append(core.texts[core.text_offsets[prev]:core.text_offsets[i]])
+        p, t = repl[i]
+        pats.append(np.frombuffer(p, np.uint8))
+        txts.append(np.frombuffer(t, np.uint8))
+        plen[i], tlen[i] = len(p), len(t)
+        prev = i + 1
+    pats.append(core.patterns[core.pattern_offsets[prev]:] if prev < core.n else core.patterns[:0])
+    txts.append(core.texts[core.text_offsets[prev]:] if prev < core.n else core.texts[:0])
+    poff = np.zeros(core.n, np.int64)
+    toff = np.zeros(core.n, np.int64)
+    np.cumsum(plen[:-1], out=poff[1:])
+    np.cumsum(tlen[:-1], out=toff[1:])
+    return synth.Batch(np.concatenate(pats), poff, plen, np.concatenate(txts), toff, tlen)
+
+
+def test_streamed_host_call_back_to_back(pkg, oracle_mod):
+    """2.5M pairs stored back to back in page-locked host memory, no offset
+    arrays, page-locked outputs: the chunked path streams each chunk's bases
+    into a two-slot device ring while the chunk before computes.  Long pairs
+    in the middle chunk (the arena kernels read them from the ring), an
+    empty pattern and a pattern with a non-ACGT byte in the ragged last
+    chunk; the results equal the oracle's bit for bit, on two calls in a row
+    on one context (the ring's slots refilled)."""
+    import torch
+
+    from paper_2204_02085_gb300 import synth
+
+    core = synth.uniform_reads(2_500_000, 100, 4, seed=91)
+    extra = synth.random_pairs(30, 400, 1500, seed=92, edit_rate=0.05)
+    repl = {1_300_000 + 11 * j: extra.pair(j) for j in range(extra.n)}
+    p, t = core.pair(2_400_001)
+    repl[2_400_001] = (b"", t)
+    p, t = core.pair(2_499_998)
+    repl[2_499_998] = (p[:50] + b"N" + p[51:], t)
+    b = _splice_back_to_back(core, repl)
+    n = b.n
+    want = oracle_mod.wfa_batch(b, (4, 6, 2), nthreads=NCPU)
+    assert want[1][2_499_998] == 2 and want[1][2_400_001] == 0
+    ins = {k: _pinned(torch, getattr(b, k)) for k in ("patterns", "pattern_lengths", "texts", "text_lengths")}
+    cap = int(want[3][-1])
+    ptr = lambda t: t.data_ptr()  # noqa: E731
+    with pkg.Aligner(0, 2 << 30) as al:
+        for _ in range(2):
+            outs = dict(s=torch.full((n,), -7, dtype=torch.int32, pin_memory=True),
+                        st=torch.full((n,), 9, dtype=torch.int8, pin_memory=True),
+                        off=torch.zeros(n + 1, dtype=torch.int64, pin_memory=True),
+                        w=torch.zeros(cap, dtype=torch.int32, pin_memory=True))
+            rc = pkg.wfa_gpu_align_batch(al.ctx, n, ptr(ins["patterns"]), None, ptr(ins["pattern_lengths"]),
+                                         ptr(ins["texts"]), None, ptr(ins["text_lengths"]), (4, 6, 2), 0,
+                                         pkg.WFA_GPU_TIMING, ptr(outs["s"]), ptr(outs["st"]), ptr(outs["w"]), cap,
+                                         ptr(outs["off"]))
+            assert rc == pkg.WFA_GPU_OK
+            assert al.timing()["deferred_pairs"] >= 30
+            assert np.array_equal(outs["s"].numpy(), want[0])
+            assert np.array_equal(outs["st"].numpy(), want[1])
+            assert np.array_equal(outs["off"].numpy(), want[3])
+            assert np.array_equal(outs["w"].numpy().view(np.uint32), want[2])
