@@ -606,6 +606,8 @@ def main():
 
     ms, timings, clocks = timed("batched", args.steps, sample_clocks=True)
     pairs_per_step = sum(b.n for b in batches)
+    # aligned bases per step: sum over pairs of (n + m) / 2
+    bases_per_step = sum(float(b.pattern_lengths.sum()) + float(b.text_lengths.sum()) for b in batches) / 2.0
     value = pairs_per_step * world * args.steps / (ms / 1000.0)
     other_modes = {}
     for mode, steps in (("eager", args.steps), ("plain", max(2, args.steps // 4))):
@@ -761,6 +763,7 @@ def main():
                 "phase_ms_per_call": {k: round(float(np.mean([t[k] for t in e2e_phases[-2 * e2e_steps:]])), 3)
                                       for k in ("h2d_ms", "align_ms", "general_ms", "cigar_ms", "d2h_ms",
                                                 "total_ms")} if e2e_phases else None},
+        "aligned_bases_per_s": value * bases_per_step / pairs_per_step,
         "gpu_launches": launches,
         "clocks": clocks,
         "mode": "batched: default path, each batch's device work replayed from a CUDA graph",
