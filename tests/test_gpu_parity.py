@@ -409,14 +409,16 @@ def _splice_back_to_back(core, repl):
     return synth.Batch(np.concatenate(pats), poff, plen, np.concatenate(txts), toff, tlen)
 
 
-def test_streamed_host_call_back_to_back(pkg, oracle_mod):
+@pytest.mark.parametrize("lengths_pinned", [True, False])
+def test_streamed_host_call_back_to_back(pkg, oracle_mod, lengths_pinned):
     """2.5M pairs stored back to back in page-locked host memory, no offset
     arrays, page-locked outputs: the chunked path streams each chunk's bases
-    into a two-slot device ring while the chunk before computes.  Long pairs
-    in the middle chunk (the arena kernels read them from the ring), an
-    empty pattern and a pattern with a non-ACGT byte in the ragged last
-    chunk; the results equal the oracle's bit for bit, on two calls in a row
-    on one context (the ring's slots refilled)."""
+    (and its lengths, when those are page-locked too; else they are copied
+    to the device once) into a device ring while earlier chunks compute.
+    Long pairs in the middle chunk (the arena kernels read them from the
+    ring), an empty pattern and a pattern with a non-ACGT byte in the ragged
+    last chunk; the results equal the oracle's bit for bit, on two calls in
+    a row on one context (the ring's slots refilled)."""
     import torch
 
     from paper_2204_02085_gb300 import synth
@@ -432,7 +434,9 @@ def test_streamed_host_call_back_to_back(pkg, oracle_mod):
     n = b.n
     want = oracle_mod.wfa_batch(b, (4, 6, 2), nthreads=NCPU)
     assert want[1][2_499_998] == 2 and want[1][2_400_001] == 0
-    ins = {k: _pinned(torch, getattr(b, k)) for k in ("patterns", "pattern_lengths", "texts", "text_lengths")}
+    ins = {k: _pinned(torch, getattr(b, k)) for k in ("patterns", "texts")}
+    for k in ("pattern_lengths", "text_lengths"):
+        ins[k] = _pinned(torch, getattr(b, k)) if lengths_pinned else torch.from_numpy(getattr(b, k).copy())
     cap = int(want[3][-1])
     ptr = lambda t: t.data_ptr()  # noqa: E731
     with pkg.Aligner(0, 2 << 30) as al:
