@@ -171,8 +171,12 @@ int wfa_gpu_set_ends_free(wfa_gpu_ctx *ctx, int32_t pattern_begin_free, int32_t 
  * Returns WFA_GPU_OK (every pair has a status), or EINVAL, ENOMEM, ECUDA,
  * ECIGAR_CAPACITY (see the enum).  The call returns after all outputs are
  * in the caller's buffers.  Host-pointer calls of 2^21 pairs or more whose
- * outputs are page-locked run in chunks of 2^20 pairs, each chunk's outputs
- * copied back while the next one computes (same results). */
+ * outputs are page-locked run in chunks of 2^19 pairs, each chunk's outputs
+ * copied back while the next one computes; when in addition both sequence
+ * arrays are page-locked and stored back to back (both offset arrays NULL),
+ * each chunk's bases (and its lengths, if page-locked) are copied into a
+ * device ring two chunks ahead of the computation instead of being read in
+ * place.  Same results either way. */
 int wfa_gpu_align_batch(wfa_gpu_ctx *ctx, int64_t n_pairs,
                         const char *patterns, const int64_t *pattern_offsets,
                         const int32_t *pattern_lengths,
