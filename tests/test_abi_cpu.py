@@ -154,3 +154,19 @@ def test_header_constants_match_binding():
             seen += 1
     assert seen >= 10
     assert p.WFA_GPU_SERVER_MERGE_PAIRS == 65536 and p.WFA_GPU_MAX_SEQ_LEN == (1 << 28) - 1
+
+
+def test_missing_library_fails_loudly():
+    """Without libwfa_gpu.so the binding raises at once: there is no CPU
+    fallback behind the product API."""
+    import subprocess
+    import sys
+
+    code = ("import paper_2204_02085_gb300 as p\n"
+            "try:\n"
+            "    p.load('/nonexistent/libwfa_gpu.so')\n"
+            "except ImportError as e:\n"
+            "    print('raised', 'not built' in str(e))\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip() == "raised True"
