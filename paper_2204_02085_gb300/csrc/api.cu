@@ -127,6 +127,11 @@ struct wfa_gpu_ctx {
   // ends-free calls, per model: <= 127 bases and <= 255 bases
   int variant_ef[2] = {11, 13};
   int variant_ef_mid[2] = {12, 14};
+  // lane-per-pair variants (gap-affine, global), smallest store first: any
+  // penalties, and with the geometry of scaled penalties 2/4/1 compiled in
+  int lane_variants[4] = {15, 16, 17, 18};
+  int lane_ct_variants[4] = {19, 20, 21, 22};
+  bool lane_on = true;      // WFA_GPU_LANE=0 turns them off (comparisons)
   int variant_forced = -1;  // tuning override (WFA_GPU_SHORT_VARIANT)
   int last_variant = -1;
   wfa::Ctrl* ctrl = nullptr;    // device
@@ -477,24 +482,37 @@ int run_retries(wfa_gpu_ctx* c, Call& k, wfa::AlignArgs& a) {
 constexpr int64_t kTuneSample = 4096;
 
 // Pick the short-kernel variant for a batch of sequences <= 127 bases: the
-// large-store variant scores the first kTuneSample pairs (score only); if
-// nearly all of them end at a score the small-store variant can hold, the
-// small one (more pairs resident per SM) runs the batch.  Returns the
-// variant index, or -1 on a CUDA error.
+// large-store variant scores the first kTuneSample pairs (score only); the
+// smallest store that holds nearly all of them (more pairs resident per SM,
+// and for the lane-per-pair kernel fewer lockstep cells) runs the batch.
+// Gap-affine global calls use the lane-per-pair variants unless the context
+// turned them off.  Returns the variant index, or -1 on a CUDA error.
 int autotune_short(wfa_gpu_ctx* c, Call& k, const wfa::AlignArgs& a_in, int64_t n) {
   const int model = a_in.oes == a_in.es ? 1 : 0;  // o = 0: gap-linear
   if ((a_in.pb | a_in.pe | a_in.tb | a_in.te) != 0) return c->variant_ef[model];  // ends-free: one variant
-  if (c->variant_forced >= 0 && c->plan.v[c->variant_forced].linear == model &&
-      !c->plan.v[c->variant_forced].ends_free)
-    return c->variant_forced;
-  const int* small = c->variants_small[model];
-  const int big = c->variant_big[model];
-  wfa::UGeo tab[64];
+  if (c->variant_forced >= 0) {
+    const wfa::ShortVariant& f = c->plan.v[c->variant_forced];
+    const bool ct_ok = f.ct_x == 0 || (f.ct_x == a_in.xs && f.ct_oe == a_in.oes && f.ct_e == a_in.es);
+    if (f.linear == model && !f.ends_free && ct_ok) return c->variant_forced;
+  }
   const wfa::ScaledPen pen{a_in.xs, a_in.oes, a_in.es};
-  int s_store[3];
-  for (int j = 0; j < 3; ++j) {
-    const wfa::ShortVariant& v = c->plan.v[small[j]];
-    s_store[j] = wfa::build_ugeo(tab, v.scap, v.cells, pen, -std::min(a_in.pb, v.max_len), std::min(a_in.tb, v.max_len));
+  const bool lane = model == 0 && c->lane_on;
+  const wfa::ShortVariant& ct = c->plan.v[c->lane_ct_variants[0]];
+  const bool lane_ct = lane && ct.ct_x == a_in.xs && ct.ct_oe == a_in.oes && ct.ct_e == a_in.es;
+  const int* cand = lane_ct ? c->lane_ct_variants : lane ? c->lane_variants : c->variants_small[model];
+  const int ncand = lane ? 4 : 3;
+  const int big = cand[ncand - 1];
+  int s_store[4];
+  for (int j = 0; j < ncand; ++j) {
+    const wfa::ShortVariant& v = c->plan.v[cand[j]];
+    if (v.kind == 1) {
+      wfa::LaneGeo g;
+      wfa::lane_geometry(a_in, v.cells, v.rw, &g);
+      s_store[j] = g.s_store;
+    } else {
+      wfa::UGeo tab[64];
+      s_store[j] = wfa::build_ugeo(tab, v.scap, v.cells, pen, 0, 0);
+    }
   }
   const int64_t m = std::min(n, kTuneSample);
   cudaStream_t st = c->stream;
@@ -509,21 +527,22 @@ int autotune_short(wfa_gpu_ctx* c, Call& k, const wfa::AlignArgs& a_in, int64_t 
   a.nruns = c->tune_aux.p;
   a.run_src = c->tune_src.p;
   a.defer_list = c->overflow.p;  // scratch: the sample's deferrals are discarded
+  a.defer_long_list = c->overflow.p;
   a.ctrl = c->ctrl + 1;
   if (!k.ok(cudaMemsetAsync(a.ctrl, 0, sizeof(wfa::Ctrl), st))) return -1;
   // pairs the sample run defers keep score -1
   if (!k.ok(cudaMemsetAsync(a.score, 0xff, m * sizeof(int32_t), st))) return -1;
   if (!k.launched(wfa::launch_short(a, c->plan.v[big], st))) return -1;
   if (!k.ok(d2h(c->h_tune, c->tune_score.p, m * sizeof(int32_t), st)) || !k.ok(cudaStreamSynchronize(st))) return -1;
-  int64_t fit[3] = {0, 0, 0}, tot = 0;
+  int64_t fit[4] = {0, 0, 0, 0}, tot = 0;
   for (int64_t i = 0; i < m; ++i) {
     const int sc = c->h_tune[i];
     if (sc < 0) continue;  // deferred, invalid or over the bound: not informative
     ++tot;
-    for (int j = 0; j < 3; ++j) fit[j] += (sc / a.g <= s_store[j]);
+    for (int j = 0; j < ncand; ++j) fit[j] += (sc / a.g <= s_store[j]);
   }
-  for (int j = 0; j < 3; ++j)
-    if (tot == 0 || fit[j] * 100 >= tot * 99) return small[j];
+  for (int j = 0; j < ncand; ++j)
+    if (tot == 0 || fit[j] * 100 >= tot * 99) return cand[j];
   return big;
 }
 
@@ -578,6 +597,12 @@ int wfa_gpu_create(wfa_gpu_ctx** out, int device, size_t scratch_bytes) {
     if (c->arena_bytes < 4096) { rc = WFA_GPU_EINVAL; break; }
     if (cudaMalloc(reinterpret_cast<void**>(&c->arena), c->arena_bytes) != cudaSuccess) { rc = WFA_GPU_ENOMEM; break; }
     if (wfa::short_plan(device, &c->plan) != cudaSuccess) { rc = WFA_GPU_ECUDA; break; }
+    if (c->plan.count < 23 || c->plan.v[c->lane_variants[0]].kind != 1 || c->plan.v[c->lane_variants[3]].kind != 1 ||
+        c->plan.v[c->lane_ct_variants[0]].ct_x == 0 || c->plan.v[c->lane_ct_variants[3]].ct_x == 0) {
+      rc = WFA_GPU_ECUDA;
+      break;
+    }
+    if (const char* ev = std::getenv("WFA_GPU_LANE")) c->lane_on = std::atoi(ev) != 0;
     // tuning override: WFA_GPU_SHORT_VARIANT=<index> for the <= 127-base case
     if (const char* ev = std::getenv("WFA_GPU_SHORT_VARIANT")) {
       const int v = std::atoi(ev);

@@ -9,9 +9,14 @@
 //                   global scratch arena, pairs taken from a device work
 //                   queue (atomic counter)
 //   validate/scan/compact/pack  bookkeeping around them
+#include <algorithm>
+#include <type_traits>
 #include <climits>
 
+#include <cstring>
+
 #include "arena_path.cuh"
+#include "lane_path.cuh"
 #include "launch.h"
 #include "short_path.cuh"
 #include "wfa_device.cuh"
@@ -27,6 +32,15 @@ __global__ void __launch_bounds__(kShortBlock, 8) short_kernel(const AlignArgs a
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_last;
   short_body<G, LMAX, CELLS, SCAP, Off, LIN, EF>(a, smem, &s_last);
+}
+
+// One lane per pair, the warp's pairs in lockstep (lane_path.cuh); Fwd is
+// the forward pass: geometry from the table (any penalties) or fixed at
+// compile time (one scaled penalty set).
+template <int LMAX, int CELLS, int RW, int SPAN, int WPB, class Fwd>
+__global__ void __launch_bounds__(32 * WPB) lane_kernel(const AlignArgs a, const LaneGeo g) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  lane_body<LMAX, CELLS, RW, SPAN, Fwd>(a, g, smem);
 }
 
 // ----------------------------------------------------------- arena kernels
@@ -391,10 +405,65 @@ cudaError_t plan_one(int device, ShortVariant* v, const char* name) {
   v->scap = SCAP;
   v->linear = LIN ? 1 : 0;
   v->ends_free = EF ? 1 : 0;
+  v->kind = 0;
+  v->rw = 0;
+  v->ct_x = v->ct_oe = v->ct_e = 0;
+  return cudaSuccess;
+}
+
+// Raw sequence bytes a lane-per-pair warp stages at once: both spans of 32
+// back-to-back pairs of up to 127 bases (kLaneSpan), or one (kLaneSpan1:
+// small stores, where the scratch would otherwise set the shared memory).
+constexpr int kLaneSpan = 8192;
+constexpr int kLaneSpan1 = 4096;
+
+// A lane-per-pair variant; CT_X, CT_OE, CT_E: the scaled penalties whose
+// geometry is compiled in (0: any penalties, geometry from the table).
+template <int LMAX, int CELLS, int RW, int WPB, int CT_X = 0, int CT_OE = 0, int CT_E = 0, int SPAN = kLaneSpan>
+cudaError_t plan_lane(int device, ShortVariant* v, const char* name) {
+  using C = LaneCfg<LMAX, CELLS, RW, SPAN>;
+  using Fwd = typename std::conditional<CT_X == 0, LaneRunForward,
+                                        LaneCtForward<(CT_X ? CT_X : 1), (CT_OE ? CT_OE : 1), (CT_E ? CT_E : 1), CELLS,
+                                                      RW>>::type;
+  auto k = lane_kernel<LMAX, CELLS, RW, SPAN, WPB, Fwd>;
+  const size_t smem = C::smem_bytes(WPB);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * WPB, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  v->grid = sm_count(device) * per_sm;
+  v->block = 32 * WPB;
+  v->smem = smem;
+  v->max_len = LMAX;
+  v->pairs_per_block = 32 * WPB;
+  v->kernel = reinterpret_cast<const void*>(k);
+  v->name = name;
+  v->cells = CELLS;
+  v->scap = 31;
+  v->linear = 0;
+  v->ends_free = 0;
+  v->kind = 1;
+  v->rw = RW;
+  v->ct_x = CT_X;
+  v->ct_oe = CT_OE;
+  v->ct_e = CT_E;
   return cudaSuccess;
 }
 
 }  // namespace
+
+void lane_geometry(const AlignArgs& a, int cells, int rw, LaneGeo* g) {
+  std::memset(g, 0, sizeof *g);
+  const int last = build_ugeo(g->tab, 31, cells, ScaledPen{a.xs, a.oes, a.es}, 0, 0);
+  const LaneLayout L = lane_layout(g->tab, last, a.es, rw);
+  g->s_store = (a.pb | a.pe | a.tb | a.te) != 0 ? -1 : L.s_store;  // global alignment only
+  g->off_i = L.off_i;
+  g->off_d = L.off_d;
+  g->span_i = L.span_i;
+  g->span_d = L.span_d;
+}
 
 // The short-kernel variants: (lanes per pair, longest sequence, cells per
 // pair, largest score index, offset type, gap-linear model).
@@ -423,6 +492,18 @@ cudaError_t short_plan(int device, ShortPlan* plan) {
   if ((e = plan_one<2, 127, 256, 31, int8_t, true, true>(device, &plan->v[i++], "g2_l127_c256_lin_ef"))) return e;
   if ((e = plan_one<2, 255, 256, 31, int16_t, true, true>(device, &plan->v[i++], "g2_l255_c256_lin_i16_ef")))
     return e;
+  // one lane per pair (gap-affine, global): stores of scores 0-8, 0-9, 0-12
+  // and 0-16 under 4/6/2; any penalties (15-18), and with the geometry of
+  // scaled penalties x = 2, o + e = 4, e = 1 (4/6/2 and its multiples)
+  // compiled in (19-22)
+  if ((e = plan_lane<127, 40, 16, 4, 0, 0, 0, kLaneSpan1>(device, &plan->v[i++], "lane_l127_c40"))) return e;
+  if ((e = plan_lane<127, 64, 16, 4, 0, 0, 0, kLaneSpan1>(device, &plan->v[i++], "lane_l127_c64"))) return e;
+  if ((e = plan_lane<127, 104, 32, 2>(device, &plan->v[i++], "lane_l127_c104"))) return e;
+  if ((e = plan_lane<127, 197, 32, 2>(device, &plan->v[i++], "lane_l127_c197"))) return e;
+  if ((e = plan_lane<127, 40, 16, 4, 2, 4, 1, kLaneSpan1>(device, &plan->v[i++], "lane_ct241_l127_c40"))) return e;
+  if ((e = plan_lane<127, 64, 16, 4, 2, 4, 1, kLaneSpan1>(device, &plan->v[i++], "lane_ct241_l127_c64"))) return e;
+  if ((e = plan_lane<127, 104, 32, 2, 2, 4, 1>(device, &plan->v[i++], "lane_ct241_l127_c104"))) return e;
+  if ((e = plan_lane<127, 197, 32, 2, 2, 4, 1>(device, &plan->v[i++], "lane_ct241_l127_c197"))) return e;
   plan->count = i;
   // the one-CTA arena kernels keep two sequences of up to 32,768 bases in
   // shared memory
@@ -440,6 +521,12 @@ cudaError_t launch_short(const AlignArgs& a, const ShortVariant& v, cudaStream_t
   const int64_t need = (a.n + v.pairs_per_block - 1) / v.pairs_per_block;
   if (need < grid) grid = (int)need;
   AlignArgs copy = a;
+  if (v.kind == 1) {
+    LaneGeo g;
+    lane_geometry(a, v.cells, v.rw, &g);
+    void* args[] = {&copy, &g};
+    return cudaLaunchKernel(v.kernel, dim3(grid), dim3(v.block), args, v.smem, st);
+  }
   void* args[] = {&copy};
   return cudaLaunchKernel(v.kernel, dim3(grid), dim3(v.block), args, v.smem, st);
 }

@@ -1,0 +1,544 @@
+// lane_path.cuh -- body of the lane-per-pair short-read kernel: every lane
+// of a warp owns one pair, and the warp's 32 pairs advance through the
+// scores together over the uniform wavefront geometry.
+//
+// The recurrences are the gap-affine WFA of the paper's method (Sec. I),
+// with penalties scaled by g = gcd(x, o, e):
+//
+//   I_s[k] = max(M_{s-o-e}[k-1], I_{s-e}[k-1]) + 1
+//   D_s[k] = max(M_{s-o-e}[k+1], D_{s-e}[k+1])
+//   M_s[k] = extend(max(M_{s-x}[k] + 1, I_s[k], D_s[k]))
+//
+// Storage, all of it [row][32 lanes] so that a lane only ever touches its
+// own bank whatever row it reads:
+//
+//   * M of every stored score, one byte per cell: u = B_k - h, the distance
+//     of the offset h to the end of diagonal k (B_k = min(m, n + k)).  In
+//     these terms the sequence-end tests vanish: a mismatch step is u - 1,
+//     an insertion min(u_M, u_I) - [k > m - n], a deletion
+//     min(u_M, u_D) - [k < m - n] (B_k - B_{k-1} = [k <= m - n]); an offset
+//     past the end wraps to a large unsigned value, which every later
+//     minimum ignores; extension lowers u by the matches, at most to 0; the
+//     end cell is u = 0 on diagonal m - n.
+//   * I and D only for the scores the recurrences still read, in place:
+//     I_s[k] lives at position k - s/e (row s mod e), where I_{s-e}[k-1]
+//     was, and D_s[k] at k + s/e, where D_{s-e}[k+1] was; a cell reads its
+//     source and overwrites it with its own value.  Positions never written
+//     hold the null offset (lane_layout checks, per penalty set, that every
+//     read finds the previous score's value or an unwritten position).
+//
+//   * two bit streams in cell order (32 cells to a word): whether I_s[k]
+//     extended I_{s-e}[k-1] (I_{s-e}[k-1] >= M_{s-o-e}[k-1]; ties extend),
+//     and the same for D.  A row's bits collect in two registers and join
+//     the streams once the row is done.
+//
+// The backtrace needs I_s[k] and D_s[k] only on the cells it visits: it
+// follows the extension bits from (s, k) along (s - j e, k - j) to the
+// opening level J, and I_s[k] = M_{s-Je-o-e}[k-J-1] + 1 + J (null past the
+// text end, or when the walk leaves the stored rows); D_s[k] the same
+// towards k + j with D_s[k] = M_{s-Je-o-e}[k+J+1].  With M, this is all
+// the walk of the method's tie-break needs.
+//
+// Two forward passes share the packing, the batch loop, the cell loop and
+// the backtrace: LaneRunForward reads the geometry of any penalties from a
+// table; LaneCtForward<x, o+e, e> has the geometry of one scaled penalty
+// set at compile time, so every source row, range and store address of the
+// cell loop is a constant.
+//
+// Extension compares 16 bases a round (XOR of two 2-bit packed windows,
+// count leading zeros).  The first round of every cell runs in the cell
+// loop; cells whose first 16 bases all matched finish in a second pass in
+// which every lane works through its own pending cells one round at a time,
+// so a long match on one pair does not hold up the other 31.
+#pragma once
+
+#include "launch.h"
+#include "short_path.cuh"
+#include "wfa_device.cuh"
+
+namespace wfa {
+
+// Layout of the in-place I and D rows for the geometry tab of scores
+// 0..last (see LaneGeo): the largest prefix of scores whose wavefronts are
+// at most 32 diagonals wide (a lane's pending extensions are a 32-bit mask),
+// whose rows fit rw positions, and whose row reads each find the value the
+// score e before wrote there (source diagonal inside that score's range) or
+// a position no score wrote (null), checked by replaying the writes.
+struct LaneLayout {
+  int s_store, off_i, off_d, span_i, span_d;
+};
+__host__ __device__ constexpr LaneLayout lane_layout(const UGeo* tab, int last, int E, int rw) {
+  LaneLayout out{-1, 0, 0, 0, 0};
+  for (int s = 1; s <= last; ++s)
+    if ((tab[s].ex & 1) && tab[s].w > 32) {
+      last = s - 1;
+      break;
+    }
+  for (; last >= 0; --last) {
+    int mi = 1 << 30, xi = -(1 << 30), md = 1 << 30, xd = -(1 << 30);
+    for (int s = 0; s <= last; ++s) {
+      if (!(tab[s].ex & 1)) continue;
+      const int q = s / E, lo = tab[s].lo, hi = tab[s].lo + tab[s].w - 1;
+      mi = lo - q < mi ? lo - q : mi;
+      xi = hi - q > xi ? hi - q : xi;
+      md = lo + q < md ? lo + q : md;
+      xd = hi + q > xd ? hi + q : xd;
+    }
+    const int span_i = xi - mi + 1, span_d = xd - md + 1, off_i = -mi, off_d = -md;
+    if (E * span_i > rw || E * span_d > rw || E * span_i > 64 || E * span_d > 64) continue;
+    int wi[64] = {}, wd[64] = {};
+    for (int i = 0; i < 64; ++i) wi[i] = wd[i] = -1;
+    bool ok = true;
+    for (int s = 0; s <= last && ok; ++s) {
+      if (!(tab[s].ex & 1)) continue;
+      const int q = s / E, r = s % E, lo = tab[s].lo, hi = tab[s].lo + tab[s].w - 1;
+      const int prev = s - E;
+      const bool has_prev = prev >= 0 && (tab[prev].ex & 1);
+      const int plo = has_prev ? tab[prev].lo : 0, phi = has_prev ? tab[prev].lo + tab[prev].w - 1 : -1;
+      for (int k = lo; k <= hi && ok; ++k) {
+        const int pi = r * span_i + k - q + off_i, pd = r * span_d + k + q + off_d;
+        if (s > 0) {
+          const int want_i = has_prev && k - 1 >= plo && k - 1 <= phi ? prev : -1;
+          const int want_d = has_prev && k + 1 >= plo && k + 1 <= phi ? prev : -1;
+          ok = wi[pi] == want_i && wd[pd] == want_d;
+        }
+      }
+      for (int k = lo; k <= hi; ++k) {
+        wi[r * span_i + k - q + off_i] = s;
+        wd[r * span_d + k + q + off_d] = s;
+      }
+    }
+    if (ok) {
+      out = LaneLayout{last, off_i, off_d, span_i, span_d};
+      break;
+    }
+  }
+  return out;
+}
+
+// The compile-time geometry of the lane-per-pair kernel for scaled
+// penalties (X, OE = o + e, E) and a store of CELLS cells, RW row positions.
+template <int X, int OE, int E, int CELLS, int RW>
+struct LaneCtGeo {
+  UGeo tab[32];
+  LaneLayout L;
+  constexpr LaneCtGeo() : tab{}, L{} {
+    const int last = build_ugeo(tab, 31, CELLS, ScaledPen{X, OE, E}, 0, 0);
+    L = lane_layout(tab, last, E, RW);
+  }
+};
+
+// Shared memory of one warp of the lane-per-pair kernel: packed sequences,
+// then a region that holds the raw sequence bytes while packing and the
+// wavefront store afterwards (M offsets, extension bits, the I and D rows).
+template <int LMAX, int CELLS, int RW, int SPAN_BYTES>
+struct LaneCfg {
+  static_assert(LMAX <= 127, "one-byte offsets");
+  static constexpr int NW = LMAX / 16 + 2;  // packed 16-base words a window may touch
+  static constexpr int kHBytes = CELLS * 32;
+  static constexpr int kXWords = (CELLS + 31) / 32;  // words of each bit stream
+  static constexpr int kXBytes = 2 * kXWords * 4 * 32;
+  static constexpr int kRowBytes = 2 * RW * 32;
+  static constexpr int kStore = kHBytes + kXBytes + kRowBytes;
+  static constexpr int kUnion = ((kStore > SPAN_BYTES ? kStore : SPAN_BYTES) + 15) / 16 * 16;
+  static constexpr int kSpanFit = kUnion / 16;
+  struct WarpShm {
+    uint32_t pw[NW * 32];
+    uint32_t tw[NW * 32];
+    alignas(16) unsigned char u[kUnion];
+  };
+  static constexpr size_t kTabBytes = (sizeof(UGeo) * 32 + 15) / 16 * 16;
+  static constexpr size_t smem_bytes(int warps) { return kTabBytes + (size_t)warps * sizeof(WarpShm); }
+};
+
+// One lane's view of its pair and store during the forward pass.
+struct LaneSt {
+  const uint32_t* pw;  // packed pattern words, word j at pw[j * 32]
+  const uint32_t* tw;  // packed text words
+  uint8_t* H;          // store cell c at H[c * 32]: u of M_s[k]
+  uint32_t* XI;        // I extension bits of cells 32 w .. 32 w + 31 at XI[w * 32]
+  uint32_t* XD;        // D extension bits, likewise
+  uint32_t ai, ad;     // the bits of the words being filled
+  int cnext;           // the next cell to be written (cells run in order)
+  uint8_t* IR;         // I row position p at IR[p * 32]
+  uint8_t* DR;         // D row position p at DR[p * 32]
+  int n, m, kf;
+  int s_hi;            // last score to try (store and caller's bound)
+  bool active;         // not finished (and a real pair)
+  int s_fin;           // scaled score once finished
+};
+
+// A lane's remaining extension rounds for the cells of one score whose first
+// 16 bases matched (bit i: item i); each pass of the loop runs one round on
+// every lane that has a cell left.
+__device__ __forceinline__ void lane_pending(LaneSt& st, uint32_t pend, int lo, int base) {
+  constexpr unsigned FULL = 0xffffffffu;
+  int ci = -1, ck = 0, cb = 0, ch = 0;
+  while (__any_sync(FULL, pend != 0 || ci >= 0)) {
+    if (ci < 0 && pend) {
+      ci = __ffs(pend) - 1;
+      pend &= pend - 1;
+      ck = lo + ci;
+      cb = min(st.m, st.n + ck);
+      ch = cb - (int)st.H[(base + ci) * 32];
+    }
+    if (ci >= 0) {
+      const uint32_t d = window32s(st.pw, ch - ck, 32) ^ window32s(st.tw, ch, 32);
+      const int eq = __clz(d) >> 1;
+      ch += eq;
+      if (eq < 16 || ch >= cb) {
+        st.H[(base + ci) * 32] = (uint8_t)(cb - min(ch, cb));
+        ci = -1;
+      }
+    }
+  }
+}
+
+// One score's row: the cells of items i = 0 .. w-1 (diagonal lo + i), stored
+// at cells base + i.  Sources: row s - x has item i at cell cx + i while
+// 0 <= i - ax < wx, row s - o - e likewise (ao, wo, co) for diagonals k - 1
+// and k + 1; the I and D rows at positions pi0 + i and pd0 + i.  Then the
+// pending extensions and the end test.  Called with constants by the
+// compile-time forward pass.
+__device__ __forceinline__ void lane_row(LaneSt& st, int s, int lo, int w, int base, int ax, int wx, int cx, int ao,
+                                         int wo, int co, int pi0, int pd0) {
+  const int m = st.m;
+  const int t0 = lo - st.kf;  // k - (m - n) at item 0
+  const int nk0 = st.n + lo;  // n + k at item 0
+  const uint8_t* H = st.H;
+  // u of M_{s-o-e} on diagonals k - 1, k (carried) and k + 1 (loaded)
+  auto ldo = [&](int item) -> uint32_t {
+    return (unsigned)(item - ao) < (unsigned)wo ? (uint32_t)H[(co + item) * 32] : 0xFFu;
+  };
+  uint32_t oa = ldo(-1), ob = ldo(0);
+  uint32_t pend = 0;
+  uint32_t bitv = 1, im = 0, dm = 0;  // this row's extension bits
+#pragma unroll 1
+  for (int i = 0; i < w; ++i) {
+    const uint32_t oc = ldo(i + 1);
+    const uint32_t mx = (unsigned)(i - ax) < (unsigned)wx ? (uint32_t)H[(cx + i) * 32] : 0xFFu;
+    const uint32_t il = st.IR[(pi0 + i) * 32];  // I_{s-e}[k-1]
+    const uint32_t dr = st.DR[(pd0 + i) * 32];  // D_{s-e}[k+1]
+    const int t = t0 + i;
+    const bool ei = il <= oa, ed = dr <= oc;  // extension (ties extend)
+    const uint32_t uI = (ei ? il : oa) - (t > 0 ? 1u : 0u);
+    const uint32_t uD = (ed ? dr : oc) - (t < 0 ? 1u : 0u);
+    if (ei) im |= bitv;
+    if (ed) dm |= bitv;
+    bitv <<= 1;
+    uint32_t uM = min(mx - 1u, min(uI, uD));
+    if (uM < 128u) {
+      const int h = min(m, nk0 + i) - (int)uM;
+      const uint32_t d = window32s(st.pw, h - (lo + i), 32) ^ window32s(st.tw, h, 32);
+      const uint32_t eq = __clz(d) >> 1;
+      if (eq == 16u && uM > 16u) pend |= 1u << i;
+      uM -= min(eq, uM);
+    }
+    st.H[(base + i) * 32] = (uint8_t)uM;
+    st.IR[(pi0 + i) * 32] = (uint8_t)uI;
+    st.DR[(pd0 + i) * 32] = (uint8_t)uD;
+    oa = ob;
+    ob = oc;
+  }
+  // the row's bits join the streams at bit base (cells run in order: the
+  // words before hold the earlier rows)
+  {
+    const int r = base & 31, wi = base >> 5;
+    st.ai |= im << r;
+    st.ad |= dm << r;
+    if (r + w >= 32) {
+      st.XI[wi * 32] = st.ai;
+      st.XD[wi * 32] = st.ad;
+      st.ai = r ? im >> (32 - r) : 0u;
+      st.ad = r ? dm >> (32 - r) : 0u;
+    }
+  }
+  st.cnext = base + w;
+  lane_pending(st, pend, lo, base);
+  if (st.active && (unsigned)(st.kf - lo) < (unsigned)w && H[(base + st.kf - lo) * 32] == 0) {
+    st.s_fin = s;
+    st.active = false;
+  }
+}
+
+// Score 0: diagonal 0 alone, u = B_0 - extend(0).
+__device__ __forceinline__ void lane_score0(LaneSt& st) {
+  const int u0 = st.active ? min(st.m, st.n) - extend_diag32(st.pw, st.tw, st.n, st.m, 0, 0, 32) : 0xFF;
+  st.H[0] = (uint8_t)u0;
+  st.ai = st.ad = 0;  // cell 0 has no gap
+  st.cnext = 1;
+  if (st.active && st.kf == 0 && u0 == 0) {
+    st.s_fin = 0;
+    st.active = false;
+  }
+}
+
+// Forward pass over a geometry table (any penalties).
+struct LaneRunForward {
+  static __device__ __forceinline__ void run(LaneSt& st, const UGeo* tab, const LaneGeo& lg, int X, int OE,
+                                             int E) {
+    constexpr unsigned FULL = 0xffffffffu;
+    lane_score0(st);
+    for (int s = 1; s <= st.s_hi && __any_sync(FULL, st.active); ++s) {
+      const UGeo g = tab[s];
+      if (!(g.ex & 1)) continue;
+      int ax = 0, wx = 0, cx = 0, ao = 0, wo = 0, co = 0;
+      if (s - X >= 0 && (tab[s - X].ex & 1)) {
+        const UGeo t = tab[s - X];
+        ax = t.lo - g.lo;  // item of the source's first diagonal
+        wx = t.w;
+        cx = t.base - ax;
+      }
+      if (s - OE >= 0 && (tab[s - OE].ex & 1)) {
+        const UGeo t = tab[s - OE];
+        ao = t.lo - g.lo;
+        wo = t.w;
+        co = t.base - ao;
+      }
+      const int q = s / E, r = s - q * E;
+      lane_row(st, s, g.lo, g.w, g.base, ax, wx, cx, ao, wo, co, r * lg.span_i + g.lo - q + lg.off_i,
+               r * lg.span_d + g.lo + q + lg.off_d);
+    }
+  }
+};
+
+// Forward pass with the geometry of scaled penalties (X, OE, E) known at
+// compile time.
+template <int X, int OE, int E, int CELLS, int RW>
+struct LaneCtForward {
+  static constexpr LaneCtGeo<X, OE, E, CELLS, RW> G{};
+  static_assert(G.L.s_store >= 0, "no score fits the store");
+
+  template <int S>
+  static __device__ __forceinline__ void score(LaneSt& st) {
+    constexpr UGeo g = G.tab[S];
+    constexpr bool HXS = S >= X && (G.tab[S >= X ? S - X : 0].ex & 1);
+    constexpr UGeo gx = G.tab[S >= X ? S - X : 0];
+    constexpr int AX = HXS ? gx.lo - g.lo : 0, WX = HXS ? gx.w : 0, CX = HXS ? gx.base - AX : 0;
+    constexpr bool HOS = S >= OE && (G.tab[S >= OE ? S - OE : 0].ex & 1);
+    constexpr UGeo go = G.tab[S >= OE ? S - OE : 0];
+    constexpr int AO = HOS ? go.lo - g.lo : 0, WO = HOS ? go.w : 0, CO = HOS ? go.base - AO : 0;
+    constexpr int Q = S / E, R = S % E;
+    constexpr int PI0 = R * G.L.span_i + g.lo - Q + G.L.off_i;
+    constexpr int PD0 = R * G.L.span_d + g.lo + Q + G.L.off_d;
+    lane_row(st, S, g.lo, g.w, g.base, AX, WX, CX, AO, WO, CO, PI0, PD0);
+  }
+
+  template <int S>
+  static __device__ __forceinline__ void scores(LaneSt& st) {
+    if constexpr (S <= G.L.s_store) {
+      if (S > st.s_hi || !__any_sync(0xffffffffu, st.active)) return;
+      if constexpr ((G.tab[S].ex & 1) != 0) score<S>(st);
+      scores<S + 1>(st);
+    }
+  }
+
+  static __device__ __forceinline__ void run(LaneSt& st, const UGeo*, const LaneGeo&, int, int, int) {
+    lane_score0(st);
+    scores<1>(st);
+  }
+};
+
+// Walk back from (M, s, m - n, m) over the lane's store (cell c: u of M at
+// H[c*32], extension bits at bit c mod 32 of XI / XD[(c/32)*32]) and write
+// the run-length CIGAR words, last run first.  Returns the number of runs,
+// -1 when more than cap are needed, -2 when the store is inconsistent
+// (never, for a store the forward pass wrote).
+__device__ __forceinline__ int lane_backtrace(const UGeo* tab, const uint8_t* H, const uint32_t* XI,
+                                              const uint32_t* XD, int n, int m,
+                                              int X, int OE, int E, int s, int k, int h, uint32_t* runs, int cap) {
+  uint32_t cur_op = 0xF, cur_len = 0;
+  int nr = 0;
+  bool over = false, bad = false;
+  auto emit = [&](uint32_t op, int len) {
+    if (len < 0) bad = true;
+    if (len <= 0) return;
+    if (op == cur_op) {
+      cur_len += (uint32_t)len;
+      return;
+    }
+    if (cur_len) {
+      if (nr < cap) runs[nr] = (cur_len << 4) | cur_op;
+      else over = true;
+      ++nr;
+    }
+    cur_op = op;
+    cur_len = (uint32_t)len;
+  };
+  const int s_top = s;
+  // store cell of (ss, kk), or -1 outside the stored rows
+  auto cell = [&](int ss, int kk) -> int {
+    if ((unsigned)ss > (unsigned)s_top) return -1;
+    const UGeo t = tab[ss];
+    const unsigned i = (unsigned)(kk - t.lo);
+    return ((t.ex & 1) && i < (unsigned)t.w) ? t.base + (int)i : -1;
+  };
+  // the offset h of M_ss[kk], or -1 (outside, or null)
+  auto mh = [&](int ss, int kk) -> int {
+    const int c = cell(ss, kk);
+    if (c < 0) return -1;
+    const int u = H[c * 32];
+    return u < 128 ? min(m, n + kk) - u : -1;
+  };
+  // I_ss[kk] (dk = -1) or D_ss[kk] (dk = +1): follow the extension bits
+  // to the opening level *J; -1 when null
+  auto gap = [&](int ss, int kk, int dk, int* J) -> int {
+    const uint32_t* XS = dk < 0 ? XI : XD;
+    int j = 0;
+    for (;; ++j) {
+      const int c = cell(ss - j * E, kk + dk * j);
+      if (c < 0) return -1;
+      if (!((XS[(c >> 5) * 32] >> (c & 31)) & 1u)) break;
+    }
+    *J = j;
+    const int src = mh(ss - j * E - OE, kk + dk * (j + 1));
+    if (src < 0) return -1;
+    const int v = dk < 0 ? src + 1 + j : src;
+    return (dk < 0 ? v > m : v - kk > n) ? -1 : v;
+  };
+  for (int guard = 2 * s_top + 8; guard > 0 && !bad; --guard) {
+    if (s == 0) {
+      if (k != 0) bad = true;
+      emit(kOpM, h);
+      break;
+    }
+    const int xm = mh(s - X, k);
+    const int xv = xm >= 0 && xm + 1 <= min(m, n + k) ? xm + 1 : -1;
+    int ij = 0, dj = 0;
+    const int iv = gap(s, k, -1, &ij);
+    const int dv = gap(s, k, 1, &dj);
+    if (xv >= 0 && xv >= iv && xv >= dv) {
+      emit(kOpM, h - xv);
+      emit(kOpX, 1);
+      s -= X;
+      h = xv - 1;
+    } else if (iv >= 0 && iv >= dv) {
+      emit(kOpM, h - iv);
+      emit(kOpI, ij + 1);
+      s -= ij * E + OE;
+      k -= ij + 1;
+      h = iv - ij - 1;
+    } else if (dv >= 0) {
+      emit(kOpM, h - dv);
+      emit(kOpD, dj + 1);
+      s -= dj * E + OE;
+      k += dj + 1;
+      h = dv;
+    } else {
+      return -2;
+    }
+    if (s < 0) return -2;
+  }
+  if (bad || s != 0) return -2;
+  if (cur_len) {
+    if (nr < cap) runs[nr] = (cur_len << 4) | cur_op;
+    else over = true;
+    ++nr;
+  }
+  return over ? -1 : nr;
+}
+
+// The lane-per-pair kernel body (global gap-affine alignment, both sequences
+// <= LMAX).  Pairs longer than LMAX, or whose score passes the last stored
+// wavefront (but not the caller's max_score), are deferred to the arena
+// kernels, as are pairs whose CIGAR needs more than kSlot runs.
+template <int LMAX, int CELLS, int RW, int SPAN_BYTES, class Fwd>
+__device__ __forceinline__ void lane_body(const AlignArgs& a, const LaneGeo& lg, unsigned char* smem) {
+  using C = LaneCfg<LMAX, CELLS, RW, SPAN_BYTES>;
+  if (*(volatile int32_t*)&a.ctrl->bad_input) return;  // inputs rejected by the validation kernel
+  UGeo* tab = reinterpret_cast<UGeo*>(smem);
+  for (int i = threadIdx.x; i < 32; i += blockDim.x) tab[i] = lg.tab[i];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto* W = reinterpret_cast<typename C::WarpShm*>(smem + C::kTabBytes + warp * sizeof(typename C::WarpShm));
+  const int s_store = lg.s_store;
+  const int X = a.xs, OE = a.oes, E = a.es;
+  LaneSt st;
+  st.pw = W->pw + lane;
+  st.tw = W->tw + lane;
+  st.H = W->u + lane;
+  st.XI = reinterpret_cast<uint32_t*>(W->u + C::kHBytes) + lane;
+  st.XD = st.XI + C::kXWords * 32;
+  st.IR = W->u + C::kHBytes + C::kXBytes + lane;
+  st.DR = st.IR + RW * 32;
+  st.s_hi = min(s_store, a.s_cap);
+  const int64_t wpb = blockDim.x >> 5;
+  const int64_t stride = (int64_t)gridDim.x * wpb * 32;
+  for (int64_t first = ((int64_t)blockIdx.x * wpb + warp) * 32; first < a.n; first += stride) {
+    const int64_t pair = first + lane;
+    bool active = pair < a.n;
+    int n = 0, m = 0;
+    if (active) {
+      n = a.plen[pair];
+      m = a.tlen[pair];
+      if (n > LMAX || m > LMAX || s_store < 0) {
+        defer_pair(a, pair);
+        active = false;
+      }
+    }
+    {
+      // all lanes take part: the warp reads its pairs' sequences together
+      uint32_t* scratch = reinterpret_cast<uint32_t*>(W->u);
+      const char* ps = active ? a.pat + a.poff[pair] : nullptr;
+      const char* ts = active ? a.txt + a.toff[pair] : nullptr;
+      const unsigned gm = 1u << lane;
+      bool okp, okt;
+      if (!a.host_seqs) {
+        pack_pair_warp32<1, C::kSpanFit>(ps, n, ts, m, active, W->pw + lane, W->tw + lane, 32, scratch, 0, gm,
+                                         &okp, &okt);
+      } else {
+        okp = pack_warp32<1, C::kSpanFit>(ps, n, active, W->pw + lane, 32, scratch, 0, gm, false);
+        okt = pack_warp32<1, C::kSpanFit>(ts, m, active, W->tw + lane, 32, scratch, 0, gm, false);
+      }
+      if (active && !(okp && okt)) {
+        write_result(a, pair, 2, -1, 0, 0);
+        active = false;
+      }
+    }
+    __syncwarp();  // the packer's scratch becomes the store
+    {
+      // the I and D rows start null
+      const uint32_t nul = 0xFFFFFFFFu;
+      uint4* z = reinterpret_cast<uint4*>(W->u + C::kHBytes + C::kXBytes);
+      for (int i = lane; i < C::kRowBytes / 16; i += 32) z[i] = make_uint4(nul, nul, nul, nul);
+      __syncwarp();
+    }
+    if (!active) n = m = 0;  // idle lanes run with empty sequences: every offset stays null
+    st.n = n;
+    st.m = m;
+    st.kf = m - n;
+    st.active = active;
+    st.s_fin = -1;
+    Fwd::run(st, tab, lg, X, OE, E);
+    if (st.cnext & 31) {  // the last, partly filled words
+      st.XI[(st.cnext >> 5) * 32] = st.ai;
+      st.XD[(st.cnext >> 5) * 32] = st.ad;
+    }
+    if (pair < a.n) {
+      if (st.active) {
+        // every stored score was tried: beyond the caller's bound, or beyond
+        // what this kernel stores (then the arena kernel takes the pair)
+        if (a.s_cap <= s_store) write_result(a, pair, 1, -1, 0, 0);
+        else defer_pair(a, pair);
+      } else if (st.s_fin >= 0) {
+        if (a.score_only) {
+          write_result(a, pair, 0, st.s_fin * a.g, 0, 0);
+        } else {
+          const int64_t src = pair * kSlot;
+          const int nr = lane_backtrace(tab, st.H, st.XI, st.XD, n, m, X, OE, E, st.s_fin, st.kf, m, a.runs + src, kSlot);
+          if (nr == -1) {
+            defer_pair(a, pair);  // more runs than a slot holds
+          } else if (nr < 0) {
+            atomicExch(&a.ctrl->internal_error, 1);
+            write_result(a, pair, 0, st.s_fin * a.g, 0, src);
+          } else {
+            write_result(a, pair, 0, st.s_fin * a.g, nr, src);
+          }
+        }
+      }
+    }
+    __syncwarp();  // the store is the next batch's packing scratch
+  }
+}
+
+}  // namespace wfa

@@ -70,7 +70,9 @@ constexpr int kLongTeamNarrow = 4;
 constexpr int kSlot = 16;  // CIGAR runs a short-kernel pair may keep
 
 // Fused short-read kernel (pack + wavefronts in shared memory + backtrace),
-// one instantiation per variant.
+// one instantiation per variant.  kind 0: the running pairs of a warp share
+// its lanes cell by cell (short_path.cuh); kind 1: one lane per pair, the
+// warp's 32 pairs in lockstep over a host-built geometry (lane_path.cuh).
 struct ShortVariant {
   const void* kernel;
   const char* name;
@@ -81,13 +83,32 @@ struct ShortVariant {
   int scap;     // largest score index of the geometry table
   int linear;   // 1: gap-linear model only (o = 0; M stored, I and D derived)
   int ends_free;  // 1: for ends-free calls only
+  int kind;     // 0 shared-lane, 1 lane-per-pair
+  int rw;       // kind 1: positions of each in-place I and D row
+  int ct_x, ct_oe, ct_e;  // kind 1: scaled penalties compiled in (0: any)
 };
 struct ShortPlan {
-  ShortVariant v[16];
+  ShortVariant v[24];
   int count;
 };
 cudaError_t short_plan(int device, ShortPlan* plan);
 cudaError_t launch_short(const AlignArgs& a, const ShortVariant& v, cudaStream_t st);
+
+// Geometry of the lane-per-pair kernel for one call (a kernel parameter):
+// the uniform table of scores 0..31, the last score the kernel stores (-1:
+// it takes no pair, e.g. ends-free calls), and where the in-place I and D
+// rows keep each score: I_s[k] at position (s mod e) * span_i + k - s/e +
+// off_i, D_s[k] at (s mod e) * span_d + k + s/e + off_d.
+struct LaneGeo {
+  UGeo tab[32];
+  int32_t s_store, off_i, off_d, span_i, span_d, pad[3];
+};
+// Fills g for the call's penalties and a variant of `cells` cells and
+// in-place rows of `rw` positions (lane_layout in lane_path.cuh: the last
+// stored score is the largest whose wavefronts fit the cells, are at most 32
+// diagonals wide, fit the rows, and whose row reads each find the previous
+// score's value or a position not yet written).
+void lane_geometry(const AlignArgs& a, int cells, int rw, LaneGeo* g);
 
 // Arena kernels for pairs deferred by the short kernel: pairs list[0 ..
 // *count), taken through the work-queue head *next; `nteams` teams (one

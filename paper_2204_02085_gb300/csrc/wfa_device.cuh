@@ -542,8 +542,9 @@ struct __align__(8) UGeo {
 // Fill tab[0..scap] for penalties p and a first wavefront on diagonals
 // lo0 .. hi0; wavefronts whose cells would pass cellcap are marked absent
 // and the last storable score is returned (-1: not even the first).
-__host__ __device__ inline int build_ugeo(UGeo* tab, int scap, int cellcap, ScaledPen p, int lo0 = 0,
-                                          int hi0 = 0) {
+// constexpr: the lane-per-pair kernel also builds its table at compile time.
+__host__ __device__ constexpr int build_ugeo(UGeo* tab, int scap, int cellcap, ScaledPen p, int lo0 = 0,
+                                            int hi0 = 0) {
   int top = 0, last = scap;
   for (int s = 0; s <= scap; ++s) {
     UGeo g{0, 0, 0, 0, 0};
@@ -559,9 +560,21 @@ __host__ __device__ inline int build_ugeo(UGeo* tab, int scap, int cellcap, Scal
       const bool eE = s - p.e >= 0 && (tab[s - p.e].ex & 2);
       exG = eO || eE;
       exM = eX || exG;
-      if (eX) { lo = min(lo, (int)tab[s - p.x].lo); hi = max(hi, tab[s - p.x].lo + tab[s - p.x].w - 1); }
-      if (eO) { lo = min(lo, tab[s - p.oe].lo - 1); hi = max(hi, tab[s - p.oe].lo + tab[s - p.oe].w); }
-      if (eE) { lo = min(lo, tab[s - p.e].lo - 1); hi = max(hi, tab[s - p.e].lo + tab[s - p.e].w); }
+      if (eX) {
+        const int l = tab[s - p.x].lo, h = tab[s - p.x].lo + tab[s - p.x].w - 1;
+        lo = l < lo ? l : lo;
+        hi = h > hi ? h : hi;
+      }
+      if (eO) {
+        const int l = tab[s - p.oe].lo - 1, h = tab[s - p.oe].lo + tab[s - p.oe].w;
+        lo = l < lo ? l : lo;
+        hi = h > hi ? h : hi;
+      }
+      if (eE) {
+        const int l = tab[s - p.e].lo - 1, h = tab[s - p.e].lo + tab[s - p.e].w;
+        lo = l < lo ? l : lo;
+        hi = h > hi ? h : hi;
+      }
     }
     if (exM) {
       const int w = hi - lo + 1;
