@@ -42,22 +42,33 @@ EDITS = (2, 4)
 SEED = 1
 CIGAR_WORDS_PER_PAIR = 16
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
-# integer lanes per SM per clock (32-bit add/logic/min/max) and SM count of a
-# GB300; the ALU roofline peak is their product with the maximum SM clock
-INT_LANES_PER_SM = 128
 N_SM = 152
-# algorithmic integer operations (work model of one wavefront cell, one
-# extra 32-base extension window, one backtrace step)
-OPS_PER_CELL = 32
-OPS_PER_EXTRA_WINDOW = 18
-OPS_PER_BT_STEP = 12
+# Integer work of the method, per unit and instruction class (the derivation
+# is in the design notes): a wavefront cell is the three recurrences (three
+# maxima, two +1, three sequence-end tests with their selects) and one
+# 16-base extension window (two word indices, two funnel shifts, XOR,
+# count-leading-zeros, halving, the advance and its end clamp); its shared
+# memory traffic is the five source offsets, the three results and the four
+# packed words of the window.  A further window repeats the window part; a
+# backtrace step reads the three candidates of its cell and picks one.
+WORK = {"cell": {"alu": 22, "xu": 1, "lsu": 12},
+        "window": {"alu": 9, "xu": 1, "lsu": 4},
+        "bt_step": {"alu": 8, "xu": 0, "lsu": 3}}
+# per-SM throughput of each class in lanes per clock on sm_100-class SMs:
+# the integer ALU pipe (add, min/max, compare, select, logic, shifts) 64, the
+# XU pipe (count leading zeros) 16, shared-memory accesses 32 (one warp-wide
+# access a clock), instruction issue 128 (four schedulers x 32 lanes)
+PIPE_RATE = {"alu": 64, "xu": 16, "lsu": 32, "issue": 128}
+# the flat model of earlier measurements: every op at the issue rate
+FLAT_OPS = {"cell": 32, "window": 18, "bt_step": 12}
 # DRAM traffic of the short kernel (dram__bytes_read.sum + dram__bytes_write.sum
 # from ncu on 1M-pair launches of the same workload, per pair; the traffic of
 # a launch grows in proportion to its pairs), valid for the device sources
 # whose digest is "sha" (kernel_sources_digest); any change to them voids it
-NCU_TRAFFIC = {"sha": "833bd94eef7f6030", "bytes_per_pair": {2: 289.90, 4: 297.69},
-               "summary": "profiles/short_kernel_1Mx100bp_E2_E4_ncu_full.md"}
-KERNEL_SOURCES = ("wfa_device.cuh", "short_path.cuh", "arena_path.cuh", "kernels.cu", "launch.h")
+NCU_TRAFFIC = {"sha": "833bd94eef7f6030", "bytes_per_pair": {2: 289.90, 4: 297.69}}
+# the short kernel of the timed region at the time of that capture
+NCU_KERNEL = "short_kernel"
+KERNEL_SOURCES = ("wfa_device.cuh", "short_path.cuh", "arena_path.cuh", "lane_path.cuh", "kernels.cu", "launch.h")
 
 
 def kernel_sources_digest() -> str:
@@ -84,6 +95,10 @@ def parse():
     ap.add_argument("--short-variant", type=int, default=None,
                     help="force one short-read kernel variant (tuning; default: the library's autotuner)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-pointer (end-to-end) measurement")
+    ap.add_argument("--no-samples", action="store_true",
+                    help="skip the bounded mixed-length and serving samples of the default run")
+    ap.add_argument("--mixed-pairs", type=int, default=200_000, help="pairs of the mixed-length sample")
+    ap.add_argument("--serving-requests", type=int, default=400, help="requests of the serving sample")
     ap.add_argument("--arena-gb", type=float, default=None,
                     help="scratch arena size for configs 3 and 4 (default: 16 and 64 GiB)")
     ap.add_argument("--requests", type=int, default=2000, help="requests in the serving trace (config 5)")
@@ -198,23 +213,64 @@ def make_batches(n_pairs: int, rank: int, edits=EDITS):
 def cpu_oracle_run(batches, sample: int, threads: int | None = None):
     """The oracle (plain CPU WFA, score + CIGAR) on the first `sample` pairs
     of each batch, all host cores (or `threads`).  Returns (pairs, seconds,
-    threads, counts)."""
+    threads, [(pairs, counters) per batch])."""
     import oracle
     from paper_2204_02085_gb300 import synth
 
     oracle.build()
     threads = threads or host_cores()
     pairs = 0
-    cnt = oracle.Counts()
+    cnts = []
     t0 = time.perf_counter()
     for b in batches:
         k = min(sample, b.n)
         sub = synth.Batch(b.patterns, b.pattern_offsets[:k], b.pattern_lengths[:k], b.texts, b.text_offsets[:k],
                           b.text_lengths[:k])
+        cnt = oracle.Counts()
         oracle.wfa_batch(sub, PEN, nthreads=threads, runs_per_pair=64, counts=cnt)
+        cnts.append((k, cnt))
         pairs += k
     dt = time.perf_counter() - t0
-    return pairs, dt, threads, cnt
+    return pairs, dt, threads, cnts
+
+
+def integer_roofline(cnts, n_launch, ms_launch, sm_mhz: float) -> dict:
+    """The integer-issue bound of the short kernel's launches from the
+    oracle's counters ([(pairs counted, Counts)] per batch), the pairs and
+    measured milliseconds of each launch, and the SM clock.  Per pair: cells,
+    further 16-base windows ((compares - cells) / 16) and backtrace steps,
+    times WORK per class; each class at its pipe's rate (PIPE_RATE), the
+    slowest pipe binding.  Also the flat model (every op at the issue rate)."""
+    clk = N_SM * sm_mhz * 1e6  # SM clocks per second, summed over SMs
+    pipes = {p: {"ops_per_pair": 0.0, "time_ms": 0.0} for p in PIPE_RATE}
+    flat_ops, flat_ms, meas_ms = 0.0, 0.0, 0.0
+    for (k, c), n, ms in zip(cnts, n_launch, ms_launch):
+        units = {"cell": c.cells / k, "window": max(0.0, (c.char_compares - c.cells) / 16.0) / k,
+                 "bt_step": c.bt_steps / k}
+        per = {p: sum(units[u] * WORK[u].get(p, 0) for u in units) for p in ("alu", "xu", "lsu")}
+        per["issue"] = sum(per.values())
+        for p, v in per.items():
+            pipes[p]["ops_per_pair"] += v * n
+            pipes[p]["time_ms"] += v * n / (PIPE_RATE[p] * clk) * 1e3
+        fo = sum(units[u] * FLAT_OPS[u] for u in units)
+        flat_ops += fo * n
+        flat_ms += fo * n / (PIPE_RATE["issue"] * clk) * 1e3
+        meas_ms += ms
+    ntot = float(sum(n_launch))
+    for p, d in pipes.items():
+        d["peak"] = PIPE_RATE[p] * clk / 1e12
+        d["achieved"] = d["ops_per_pair"] / (meas_ms / 1e3) / 1e12
+        d["frac"] = d["time_ms"] / meas_ms
+        d["ops_per_pair"] /= ntot
+    bind = max(pipes, key=lambda p: pipes[p]["time_ms"])
+    b = pipes[bind]
+    flat = {"ops_per_pair": flat_ops / ntot, "peak": PIPE_RATE["issue"] * clk / 1e12,
+            "achieved": flat_ops / (meas_ms / 1e3) / 1e12, "frac": flat_ms / meas_ms, "unit": "Tops/s"}
+    return {"bound": "alu", "pipe": bind, "achieved": b["achieved"], "peak": b["peak"], "unit": "Tops/s",
+            "frac": b["frac"], "time_ms": b["time_ms"], "measured_ms": meas_ms, "pipes": pipes, "flat": flat,
+            "peak_source": "152 SMs x lanes per clock of the pipe (ALU 64, XU 16, shared memory 32, issue 128) x "
+                           "%.0f MHz" % sm_mhz,
+            "work_per_unit": WORK}
 
 
 def headline_config(n_pairs: int, world: int, edits=EDITS) -> dict:
@@ -419,24 +475,23 @@ def run_models(args):
     return 0
 
 
-def run_serving(args):
-    """Configuration 5: a Poisson stream of requests (2,000 per second;
-    batch sizes log-uniform 1-4,096 pairs; lengths log-uniform 100-5,000 bp;
-    edit rate U[2%, 8%]; seed 5) replayed in real time against the
-    continuous-batching server (2 slots by default; queued requests of the
-    same parameters are merged into one call), then all queued at once
-    (capacity), then without a server: one request at a time in arrival order
-    on the default path, and on the plain path.  Requests are windows of a
-    pool of page-locked pairs, built before the clock starts."""
+def serving_experiment(R: int, workers: int, burst: bool = True, one: bool = True, plain: bool = True) -> dict:
+    """Configuration 5's trace: a Poisson stream of R requests (2,000 per
+    second; batch sizes log-uniform 1-4,096 pairs; lengths log-uniform
+    100-5,000 bp; edit rate U[2%, 8%]; seed 5) replayed in real time against
+    the continuous-batching server (`workers` slots; queued requests of the
+    same parameters are merged into one call); then, if asked, all queued at
+    once (capacity), and without a server: one request at a time in arrival
+    order on the default path and on the plain path (the baseline of issuing
+    each batch to the plain kernels).  Requests are windows of a pool of
+    page-locked pairs, built before the clock starts."""
     import threading as th
 
     import torch
 
     import paper_2204_02085_gb300 as pkg
-    from paper_2204_02085_gb300 import build as gpu_build
     from paper_2204_02085_gb300 import synth
 
-    gpu_build.build()
     rng = np.random.Generator(np.random.PCG64(5))
     pool_n = 60_000
     pool = synth.mixed_reads(pool_n, 100, 5000, 0.08, 0.0, seed=5, rate_lo=0.02)
@@ -449,7 +504,6 @@ def run_serving(args):
 
     pool = synth.Batch(pin(pool.patterns), pin(pool.pattern_offsets), pin(pool.pattern_lengths), pin(pool.texts),
                        pin(pool.text_offsets), pin(pool.text_lengths))
-    R = args.requests
     gaps = rng.exponential(1.0 / 2000.0, size=R)
     arrivals = np.cumsum(gaps) - gaps[0]
     sizes = np.minimum(np.exp(rng.uniform(0, np.log(4096), size=R)).astype(np.int64), pool_n)
@@ -462,13 +516,13 @@ def run_serving(args):
     caps = [int(b.pattern_lengths.sum() + b.text_lengths.sum()) + 1 for b in reqs]
     total_pairs = int(sizes.sum())
 
-    def replay(workers, plain, burst=False):
+    def replay(workers, burst=False):
         with pkg.Server(0, workers=workers, memory_budget_bytes=32 << 30) as srv:
             # warm-up, untimed: kernels loaded, then a burst so that every
             # slot grows its buffers to merged-batch size
             for b, c in zip(reqs[:4], caps[:4]):
-                srv.wait(srv.submit(b, PEN, cigar_capacity=c, plain=plain))
-            for rid in [srv.submit(b, PEN, cigar_capacity=c, plain=plain) for b, c in zip(reqs[:256], caps[:256])]:
+                srv.wait(srv.submit(b, PEN, cigar_capacity=c))
+            for rid in [srv.submit(b, PEN, cigar_capacity=c) for b, c in zip(reqs[:256], caps[:256])]:
                 srv.wait(rid)
             ids, stats = [None] * R, [None] * R
             done = th.Event()
@@ -487,13 +541,13 @@ def run_serving(args):
                 delay = arrivals[j] - (time.perf_counter() - t0)
                 if delay > 0 and not burst:
                     time.sleep(delay)
-                ids[j] = srv.submit(reqs[j], PEN, cigar_capacity=caps[j], plain=plain)
+                ids[j] = srv.submit(reqs[j], PEN, cigar_capacity=caps[j])
             done.wait()
             w.join()
         lat = np.array([(s.end_s - s.submit_s) * 1000.0 for s in stats])
         span = max(s.end_s for s in stats) - min(s.submit_s for s in stats)
         calls = len({(s.worker, s.start_s) for s in stats})
-        return {"workers": workers, "plain": plain, "calls": calls, "pairs_per_call": total_pairs / calls,
+        return {"workers": workers, "calls": calls, "pairs_per_call": total_pairs / calls,
                 "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
                 "pairs_per_s": total_pairs / span, "span_s": span,
@@ -518,22 +572,94 @@ def run_serving(args):
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "mean_ms": float(lat.mean()), "pairs_per_s": total_pairs / span, "span_s": span, "all_ok": True}
 
-    serving = replay(args.workers, False)
-    saturated = replay(args.workers, False, burst=True)  # every request queued at once: capacity
-    one = one_at_a_time(False) if args.baselines else None
-    plain = one_at_a_time(True) if args.baselines else None
+    out = {"requests": R, "offered_pairs": total_pairs,
+           "offered_pairs_per_s": total_pairs / float(arrivals[-1] or 1.0),
+           "serving": replay(workers)}
+    if burst:
+        out["saturated"] = replay(workers, burst=True)  # every request queued at once: capacity
+    if one:
+        out["one_at_a_time"] = one_at_a_time(False)
+    if plain:
+        out["plain_per_batch"] = one_at_a_time(True)
+        out["p99_plain_over_serving"] = out["plain_per_batch"]["p99_ms"] / out["serving"]["p99_ms"]
+    return out
+
+
+def run_serving(args):
+    """Configuration 5 (serving): see serving_experiment; rank 0 only."""
+    from paper_2204_02085_gb300 import build as gpu_build
+
+    gpu_build.build()
+    R = args.requests
+    res = serving_experiment(R, args.workers, burst=True, one=bool(args.baselines), plain=bool(args.baselines))
+    serving = res["serving"]
     line = {"metric": "pairs/s and p50/p99 latency (config 5, serving)", "value": serving["pairs_per_s"],
             "unit": "pairs/s", "n_gpus": 1, "steps": R, "warmup": 260, "ms_per_step": serving["mean_ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
             "config": {"workload": "%d requests, Poisson 2,000/s, batch sizes log-uniform 1-4,096, lengths "
                                    "log-uniform 100-5,000 bp, edit rate U[2%%,8%%], penalties 4/6/2, score+CIGAR"
-                                   % R, "offered_pairs": total_pairs,
-                       "offered_pairs_per_s": total_pairs / float(arrivals[-1] or 1.0)},
-            "serving": serving, "saturated": saturated, "one_at_a_time": one, "plain_per_batch": plain,
-            "p99_plain_over_serving": plain["p99_ms"] / serving["p99_ms"] if plain else None}
+                                   % R, "offered_pairs": res["offered_pairs"],
+                       "offered_pairs_per_s": res["offered_pairs_per_s"]},
+            **{k: v for k, v in res.items() if k not in ("requests", "offered_pairs", "offered_pairs_per_s")}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def mixed_sample(n: int, steps: int, warmup: int) -> dict:
+    """The first n pairs of configuration 3 (text length log-uniform
+    100-2,000 bp, edit rate U[0, 10%], 5% tandem repeats, seed 3), device
+    resident, score + CIGAR, through the batched path (graph replay), the
+    eager path and the plain baseline: pairs/s of each."""
+    import torch
+
+    import paper_2204_02085_gb300 as pkg
+    from paper_2204_02085_gb300 import synth
+
+    dev = torch.device("cuda:0")
+    b = synth.mixed_reads(n, 100, 2000, 0.10, 0.05, seed=3)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    d = dict(pat=t(b.patterns), plen=t(b.pattern_lengths), txt=t(b.texts), tlen=t(b.text_lengths),
+             s=torch.empty(n, dtype=torch.int32, device=dev), st=torch.empty(n, dtype=torch.int8, device=dev),
+             off=torch.empty(n + 1, dtype=torch.int64, device=dev))
+    stream = torch.cuda.Stream(dev)
+    res = {}
+    with pkg.Aligner(0, scratch_bytes=16 << 30) as al:
+        al.set_stream(stream)
+        w = torch.empty(1, dtype=torch.int32, device=dev)
+        al.align_device(d["pat"], None, d["plen"], d["txt"], None, d["tlen"], d["s"], d["st"], w, d["off"], pen=PEN)
+        w = torch.empty(int(d["off"][-1]) + 1, dtype=torch.int32, device=dev)
+        ref = None
+        for mode, extra in (("batched", dict(graph=True)), ("eager", {}), ("plain", dict(plain=True))):
+            def call():
+                rc = al.align_device(d["pat"], None, d["plen"], d["txt"], None, d["tlen"], d["s"], d["st"], w,
+                                     d["off"], pen=PEN, timing=True, **extra)
+                assert rc == pkg.WFA_GPU_OK
+                return al.timing()
+            for _ in range(warmup):
+                call()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ts = []
+            e0.record(stream)
+            for _ in range(steps):
+                ts.append(call())
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / steps
+            sc = d["s"].cpu().numpy()
+            if ref is None:
+                ref = sc.copy()
+            assert np.array_equal(ref, sc), "modes disagree on the mixed sample"
+            res[mode] = {"pairs_per_s": n / (ms / 1000.0), "ms_per_call": ms,
+                         "short_kernel_ms": round(float(np.mean([x["align_ms"] for x in ts])), 3),
+                         "arena_ms": round(float(np.mean([x["general_ms"] for x in ts])), 3),
+                         "deferred_pairs": int(ts[-1]["deferred_pairs"]),
+                         "short_variant": al.variant_name(int(ts[-1]["short_variant"]))}
+    res["batched_over_plain"] = res["batched"]["pairs_per_s"] / res["plain"]["pairs_per_s"]
+    res["workload"] = ("first %d pairs of the mixed-length configuration (100-2,000 bp, 0-10%% edits, 5%% "
+                       "tandem repeats, seed 3), score+CIGAR, %d timed calls per mode" % (n, steps))
+    return res
 
 
 def main():
@@ -589,9 +715,12 @@ def main():
 
     # modes: "batched" = the default path with each batch's device work
     # replayed from a CUDA graph (captured on the first call); "eager" = the
-    # default path launched call by call; "plain" = the baseline path (every
-    # pair on one-warp arena teams, no short-read kernel)
-    MODES = {"batched": dict(graph=True), "eager": {}, "plain": dict(plain=True)}
+    # default path launched call by call; "plain" = the baseline (the same
+    # kernels call by call with one fixed variant: no sampling autotuner, no
+    # longest-first order, no graph); "arena_only" = every pair on one-warp
+    # arena teams, no short-read kernel
+    MODES = {"batched": dict(graph=True), "eager": {}, "plain": dict(plain=True),
+             "arena_only": dict(arena_only=True)}
 
     def device_step(mode, collect=None):
         for d in dbat:
@@ -634,7 +763,7 @@ def main():
     bases_per_step = sum(float(b.pattern_lengths.sum()) + float(b.text_lengths.sum()) for b in batches) / 2.0
     value = pairs_per_step * world * args.steps / (ms / 1000.0)
     other_modes = {}
-    for mode, steps in (("eager", args.steps), ("plain", max(2, args.steps // 4))):
+    for mode, steps in (("eager", args.steps), ("plain", args.steps), ("arena_only", max(2, args.steps // 4))):
         mms, mts, _ = timed(mode, steps)
         other_modes[mode] = {"pairs_per_s": pairs_per_step * world * steps / (mms / 1000.0),
                              "ms_per_step": mms / steps, "steps": steps,
@@ -733,7 +862,6 @@ def main():
 
     # algorithmic bytes per pair: 2L ASCII in, lengths in, score + status +
     # CIGAR offset + 4 bytes per CIGAR run out
-    roof = {}
     align_ms = float(np.mean([per_batch[e]["align_ms"] for e in args.edits]))
     n_per_launch = float(np.mean([b.n for b in batches]))
     bytes_per_pair = []
@@ -744,34 +872,36 @@ def main():
     hbm_gbs = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
     achieved_gbs = bpp * n_per_launch / (align_ms / 1000.0) / 1e9
     hbm_time_ms = bpp * n_per_launch / (hbm_gbs * 1e9) * 1000.0
+    hbm = {"achieved": achieved_gbs, "peak": hbm_gbs, "unit": "GB/s", "frac": achieved_gbs / hbm_gbs,
+           "time_ms": hbm_time_ms, "peak_source": peak_src}
     alu = None
-    if cnt is not None and cnt.cells > 0:
-        pairs_counted = 2 * min(args.cpu_sample, args.pairs)
-        extra_windows = cnt.char_compares // 32
-        ops_per_pair = (OPS_PER_CELL * cnt.cells + OPS_PER_EXTRA_WINDOW * extra_windows
-                        + OPS_PER_BT_STEP * cnt.bt_steps) / pairs_counted
+    if cnt is not None:
         sm_max = float(peaks.get("sm_max_mhz", PEAKS_FALLBACK["sm_max_mhz"]))
-        alu_peak = N_SM * INT_LANES_PER_SM * sm_max * 1e6 / 1e12  # Tops/s
-        alu_achieved = ops_per_pair * n_per_launch / (align_ms / 1000.0) / 1e12
-        alu_time_ms = ops_per_pair * n_per_launch / (alu_peak * 1e12) * 1000.0
-        alu = {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Tops/s",
-               "frac": alu_achieved / alu_peak, "ops_per_pair": ops_per_pair,
-               "peak_source": "152 SMs x 128 int32 lanes x %.0f MHz" % sm_max}
-    if alu is not None and alu_time_ms > hbm_time_ms:
+        alu = integer_roofline(cnt, [b.n for b in batches], [per_batch[e]["align_ms"] for e in args.edits], sm_max)
+    if alu is not None and alu["time_ms"] > hbm_time_ms:
         roof = dict(alu)
-        roof["hbm"] = {"achieved": achieved_gbs, "peak": hbm_gbs, "unit": "GB/s", "frac": achieved_gbs / hbm_gbs}
+        roof["hbm"] = hbm
     else:
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_gbs, "unit": "GB/s",
                 "frac": achieved_gbs / hbm_gbs, "peak_source": peak_src}
         if alu is not None:
-            roof["alu"] = {k: alu[k] for k in ("achieved", "peak", "unit", "frac", "ops_per_pair")}
-    roof["kernel"] = "short_kernel (fused pack + wavefront + backtrace)"
+            roof["alu"] = alu
+    roof["kernel"] = "the short-read wavefront kernel (fused pack + wavefront + backtrace)"
     roof["bytes_per_pair"] = bpp
     roof["avg_launch_ms"] = align_ms
     roof["traffic"] = None
     if kernel_sources_digest() == NCU_TRAFFIC["sha"] and all(e in NCU_TRAFFIC["bytes_per_pair"] for e in args.edits):
         roof["traffic"] = float(np.mean([NCU_TRAFFIC["bytes_per_pair"][e] * b.n for e, b in zip(args.edits, batches)]))
-        roof["traffic_source"] = "ncu dram bytes of 1M-pair launches scaled to the launch (%s)" % NCU_TRAFFIC["summary"]
+        roof["traffic_source"] = ("ncu dram bytes of 1M-pair launches of %s, scaled to the launch (device sources "
+                                  "%s)" % (NCU_KERNEL, NCU_TRAFFIC["sha"]))
+
+    # bounded samples of the other workloads the metric names: batched vs
+    # plain on mixed lengths, and p50/p99 latency of the serving trace
+    samples = {}
+    if not args.no_samples:
+        samples["mixed_lengths_sample"] = mixed_sample(args.mixed_pairs, steps=3, warmup=2)
+        samples["serving_sample"] = serving_experiment(args.serving_requests, args.workers, burst=False, one=False,
+                                                       plain=True)
 
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
@@ -791,7 +921,9 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
         "mode": "batched: default path, each batch's device work replayed from a CUDA graph",
-        "vs_plain": {"batched_over_plain": value / other_modes["plain"]["pairs_per_s"], **other_modes},
+        "vs_plain": {"batched_over_plain": value / other_modes["plain"]["pairs_per_s"],
+                     "batched_over_eager": value / other_modes["eager"]["pairs_per_s"], **other_modes},
+        **samples,
         "by_edit_rate": {"E=%d%%" % e: {"pairs_per_s_kernel_path": batches[i].n / (per_batch[e]["total_ms"] / 1000.0),
                                          "align_kernel_ms": per_batch[e]["align_ms"],
                                          "call_ms": per_batch[e]["total_ms"],

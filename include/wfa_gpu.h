@@ -80,15 +80,21 @@ enum {
   WFA_GPU_DEVICE_PTRS = 2u, /* every input and output pointer is device memory on the
                                context's device (default: host memory) */
   WFA_GPU_TIMING = 4u,      /* record per-phase device times for wfa_gpu_last_timing */
-  WFA_GPU_PLAIN = 8u,       /* the plain path, kept as a baseline for comparisons: every
-                               pair on one-warp (or, above 2,048 bases, one-CTA) arena
-                               teams from a work queue, without the short-read kernel,
-                               its variants or the autotuner; same results */
-  WFA_GPU_GRAPH = 16u       /* with WFA_GPU_DEVICE_PTRS: for batches repeated with the same
+  WFA_GPU_PLAIN = 8u,       /* the plain baseline for comparisons: the same kernels launched
+                               call by call with one fixed short-read variant (the largest
+                               store of the call's length class and penalty model), no
+                               sampling autotuner, the arena kernels' work lists in pair
+                               order, and no graph replay (WFA_GPU_GRAPH is ignored); same
+                               results */
+  WFA_GPU_GRAPH = 16u,      /* with WFA_GPU_DEVICE_PTRS: for batches repeated with the same
                                arguments (same sizes and buffers, new contents), the first
                                call runs as usual and records the device work into a CUDA
                                graph; identical later calls replay it with a single host
                                synchronisation (one graph per context) */
+  WFA_GPU_ARENA_ONLY = 32u  /* every pair on one-warp (or, above 2,048 bases, one-CTA)
+                               arena teams from a work queue in pair order, without the
+                               short-read kernels, launched call by call (WFA_GPU_GRAPH is
+                               ignored); same results */
 };
 
 /* Device-side times of the last wfa_gpu_align_batch call on a context,
@@ -154,7 +160,7 @@ int wfa_gpu_set_ends_free(wfa_gpu_ctx *ctx, int32_t pattern_begin_free, int32_t 
  *   WFA_PAIR_SCORE_LIMIT (a score equal to max_score is reported); <= 0 means
  *   no bound.
  * flags: WFA_GPU_SCORE_ONLY | WFA_GPU_DEVICE_PTRS | WFA_GPU_TIMING |
- *   WFA_GPU_PLAIN | WFA_GPU_GRAPH.
+ *   WFA_GPU_PLAIN | WFA_GPU_GRAPH | WFA_GPU_ARENA_ONLY.
  *
  * Outputs (caller-owned):
  *   out_scores[n]   int32 optimal score, -1 if status != OK
@@ -215,17 +221,18 @@ int wfa_gpu_pack2bit(wfa_gpu_ctx *ctx, int64_t n_seqs, const char *seqs,
 /* Align short read pairs without allocating any memory.  (The paper has no
  * counterpart to this entry point; it exists for callers of this library.)
  *
- * Who needs it: callers that cannot call cudaMalloc -- code that runs while
- * a CUDA stream is being captured into a graph (an allocation would break
- * the capture), applications whose device memory is owned by a pool or
- * framework that forbids foreign allocations, and latency-critical paths
- * that must not risk a device-wide synchronisation inside cudaMalloc or
- * cudaFree.  wfa_gpu_create allocates a scratch arena and buffers; this
- * entry point instead keeps its scratch (control block, offset scans,
- * per-pair CIGAR slots, work lists) in one file-scope device array of
+ * Who needs it: callers that cannot call cudaMalloc -- applications whose
+ * device memory belongs to a pool or framework that forbids allocations
+ * made behind its back, and latency-critical paths that must not risk the
+ * device-wide synchronisation cudaMalloc and cudaFree can bring.
+ * wfa_gpu_create allocates a scratch arena and buffers; this entry point
+ * instead keeps its scratch (control block, offset scans, per-pair CIGAR
+ * slots, work lists) in one file-scope device array of
  * WFA_GPU_NOALLOC_SCRATCH_BYTES that every GPU which loads the library
  * holds until the process exits.  It calls no cudaMalloc, cudaFree or other
- * allocating routine.
+ * allocating routine.  It is not for use while `stream` is being captured
+ * into a CUDA graph: it synchronises `stream` (up to four times) to read its
+ * control block back and return its error codes.
  *
  * Same operation, inputs and outputs as wfa_gpu_align_batch with
  * WFA_GPU_DEVICE_PTRS (every pointer is device memory on the current device;
@@ -233,17 +240,18 @@ int wfa_gpu_pack2bit(wfa_gpu_ctx *ctx, int64_t n_seqs, const char *seqs,
  *   n_pairs <= WFA_GPU_NOALLOC_MAX_PAIRS, every sequence
  *   <= WFA_GPU_NOALLOC_MAX_LEN bases -- otherwise WFA_GPU_EINVAL;
  *   pairs whose wavefronts fit the short-read kernel's shared memory (for
- *   penalties 4/6/2, an optimal score up to 32) -- if one does not,
- *   WFA_GPU_ENOMEM (wfa_gpu_align_batch handles such pairs in its arena).
+ *   penalties 4/6/2: an optimal score up to 32), and whose CIGAR has at most
+ *   16 runs (a 127-base pair with 8 isolated mismatches scores 32 but needs
+ *   17 runs: 9 M and 8 X) -- if a pair breaks either, WFA_GPU_ENOMEM
+ *   (wfa_gpu_align_batch handles such pairs in its arena).
  * stream: the cudaStream_t to run on (NULL: the legacy default stream).
  *
  * The first call on a device sets that device up (looks up the scratch
- * array's device address, configures the kernel): make that first call
- * before any stream capture begins.  Every call shares the one scratch
- * array, which keeps the previous call's contents; calls whose work
- * overlaps on the GPU (other streams, other host threads) race on it and
- * must be serialised by the caller.  Returns after the outputs are written.
- * Returns OK, EINVAL, ENOMEM, ECUDA or ECIGAR_CAPACITY as
+ * array's device address, configures the kernel).  Every call shares the
+ * one scratch array, which keeps the previous call's contents; calls whose
+ * work overlaps on the GPU (other streams, other host threads) race on it
+ * and must be serialised by the caller.  Returns after the outputs are
+ * written.  Returns OK, EINVAL, ENOMEM, ECUDA or ECIGAR_CAPACITY as
  * wfa_gpu_align_batch does. */
 int wfa_gpu_align_short_noalloc(void *stream, int64_t n_pairs,
                                 const char *patterns, const int64_t *pattern_offsets,

@@ -27,6 +27,7 @@ WFA_GPU_ECIGAR_CAPACITY = -4
 WFA_GPU_ETIMEOUT = -5
 WFA_PAIR_OK, WFA_PAIR_SCORE_LIMIT, WFA_PAIR_INVALID_CHAR = 0, 1, 2
 WFA_GPU_SCORE_ONLY, WFA_GPU_DEVICE_PTRS, WFA_GPU_TIMING, WFA_GPU_PLAIN, WFA_GPU_GRAPH = 1, 2, 4, 8, 16
+WFA_GPU_ARENA_ONLY = 32
 WFA_GPU_MAX_SEQ_LEN = (1 << 28) - 1
 WFA_GPU_SERVER_MERGE_PAIRS = 65536
 
@@ -299,7 +300,7 @@ class Aligner:
 
     def align(self, batch, pen=(4, 6, 2), max_score: int = 0, score_only: bool = False,
               cigar_capacity: int | None = None, timing: bool = False, use_offsets: bool = True,
-              plain: bool = False):
+              plain: bool = False, arena_only: bool = False):
         """Host-memory call.  ``batch`` has patterns/pattern_offsets/
         pattern_lengths/texts/text_offsets/text_lengths as numpy arrays.
         Returns (scores, status, cigar words, cigar offsets)."""
@@ -313,7 +314,7 @@ class Aligner:
         scores = np.empty(n, dtype=np.int32)
         status = np.empty(n, dtype=np.int8)
         flags = (WFA_GPU_SCORE_ONLY if score_only else 0) | (WFA_GPU_TIMING if timing else 0) | \
-            (WFA_GPU_PLAIN if plain else 0)
+            (WFA_GPU_PLAIN if plain else 0) | (WFA_GPU_ARENA_ONLY if arena_only else 0)
         offs = np.zeros(n + 1, dtype=np.int64)
         cap = 0 if score_only else int(cigar_capacity if cigar_capacity is not None else max(16 * n, 1))
         words = np.empty(max(cap, 1), dtype=np.uint32)
@@ -335,13 +336,15 @@ class Aligner:
 
     def align_device(self, pat, poff, plen, txt, toff, tlen, out_scores, out_status, out_cigars,
                      out_cigar_offsets, pen=(4, 6, 2), max_score: int = 0, score_only: bool = False,
-                     timing: bool = False, plain: bool = False, graph: bool = False) -> int:
+                     timing: bool = False, plain: bool = False, graph: bool = False,
+                     arena_only: bool = False) -> int:
         """Device-memory call on torch CUDA tensors (offsets may be None).
         Returns the raw code (WFA_GPU_OK or WFA_GPU_ECIGAR_CAPACITY; other
         codes raise)."""
         n = int(plen.numel())
         flags = WFA_GPU_DEVICE_PTRS | (WFA_GPU_SCORE_ONLY if score_only else 0) | \
-            (WFA_GPU_TIMING if timing else 0) | (WFA_GPU_PLAIN if plain else 0) | (WFA_GPU_GRAPH if graph else 0)
+            (WFA_GPU_TIMING if timing else 0) | (WFA_GPU_PLAIN if plain else 0) | (WFA_GPU_GRAPH if graph else 0) | \
+            (WFA_GPU_ARENA_ONLY if arena_only else 0)
         cap = 0 if (score_only or out_cigars is None) else int(out_cigars.numel())
         rc = wfa_gpu_align_batch(self.ctx, n, _addr(pat), _addr(poff), _addr(plen), _addr(txt), _addr(toff),
                                  _addr(tlen), pen, max_score, flags, _addr(out_scores), _addr(out_status),
@@ -407,6 +410,7 @@ class Server:
         self._pending = {}
 
     def submit(self, batch, pen=(4, 6, 2), max_score: int = 0, score_only: bool = False, plain: bool = False,
+               arena_only: bool = False,
                cigar_capacity: int | None = None) -> int:
         n = int(len(batch.pattern_lengths))
         keep = dict(
@@ -422,7 +426,8 @@ class Server:
                         for p, t in zip(keep["plen"], keep["tlen"])) if not score_only else 0
             cigar_capacity = bound
         keep["w"] = np.empty(max(1, cigar_capacity), np.uint32)
-        flags = (WFA_GPU_SCORE_ONLY if score_only else 0) | (WFA_GPU_PLAIN if plain else 0)
+        flags = (WFA_GPU_SCORE_ONLY if score_only else 0) | (WFA_GPU_PLAIN if plain else 0) | \
+            (WFA_GPU_ARENA_ONLY if arena_only else 0)
         req = Request(n, _addr(keep["pat"]), _addr(keep["poff"]), _addr(keep["plen"]), _addr(keep["txt"]),
                       _addr(keep["toff"]), _addr(keep["tlen"]), pen if isinstance(pen, Penalties) else Penalties(*pen),
                       max_score, flags, _addr(keep["s"]), _addr(keep["st"]), None if score_only else _addr(keep["w"]),

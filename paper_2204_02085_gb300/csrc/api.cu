@@ -128,9 +128,11 @@ struct wfa_gpu_ctx {
   int variant_ef[2] = {11, 13};
   int variant_ef_mid[2] = {12, 14};
   // lane-per-pair variants (gap-affine, global), smallest store first: any
-  // penalties, and with the geometry of scaled penalties 2/4/1 compiled in
+  // penalties, and for scaled penalties 2/4/1 the small stores with their
+  // geometry compiled in (per-score code: for the large stores its size
+  // costs more in instruction fetch than the constants save)
   int lane_variants[4] = {15, 16, 17, 18};
-  int lane_ct_variants[4] = {19, 20, 21, 22};
+  int lane_ct_variants[4] = {19, 20, 17, 18};
   bool lane_on = true;      // WFA_GPU_LANE=0 turns them off (comparisons)
   int variant_forced = -1;  // tuning override (WFA_GPU_SHORT_VARIANT)
   int last_variant = -1;
@@ -499,6 +501,8 @@ int autotune_short(wfa_gpu_ctx* c, Call& k, const wfa::AlignArgs& a_in, int64_t 
   const bool lane = model == 0 && c->lane_on;
   const wfa::ShortVariant& ct = c->plan.v[c->lane_ct_variants[0]];
   const bool lane_ct = lane && ct.ct_x == a_in.xs && ct.ct_oe == a_in.oes && ct.ct_e == a_in.es;
+  // (the compiled-in variants serve only their penalties: any other entry of
+  // the list is a table-driven one)
   const int* cand = lane_ct ? c->lane_ct_variants : lane ? c->lane_variants : c->variants_small[model];
   const int ncand = lane ? 4 : 3;
   const int big = cand[ncand - 1];
@@ -544,6 +548,16 @@ int autotune_short(wfa_gpu_ctx* c, Call& k, const wfa::AlignArgs& a_in, int64_t 
   for (int j = 0; j < ncand; ++j)
     if (tot == 0 || fit[j] * 100 >= tot * 99) return cand[j];
   return big;
+}
+
+// The plain baseline's short-read variant: the largest store of the call's
+// length class and penalty model, chosen without sampling.
+int fixed_variant(const wfa_gpu_ctx* c, const wfa::AlignArgs& a, int max_len) {
+  const int model = a.oes == a.es ? 1 : 0;
+  const bool ef = (a.pb | a.pe | a.tb | a.te) != 0;
+  if (max_len > 127) return ef ? c->variant_ef_mid[model] : c->variant_mid[model];
+  if (ef) return c->variant_ef[model];
+  return model == 0 && c->lane_on ? c->lane_variants[3] : c->variant_big[model];
 }
 
 }  // namespace
@@ -598,7 +612,7 @@ int wfa_gpu_create(wfa_gpu_ctx** out, int device, size_t scratch_bytes) {
     if (cudaMalloc(reinterpret_cast<void**>(&c->arena), c->arena_bytes) != cudaSuccess) { rc = WFA_GPU_ENOMEM; break; }
     if (wfa::short_plan(device, &c->plan) != cudaSuccess) { rc = WFA_GPU_ECUDA; break; }
     if (c->plan.count < 23 || c->plan.v[c->lane_variants[0]].kind != 1 || c->plan.v[c->lane_variants[3]].kind != 1 ||
-        c->plan.v[c->lane_ct_variants[0]].ct_x == 0 || c->plan.v[c->lane_ct_variants[3]].ct_x == 0) {
+        c->plan.v[c->lane_ct_variants[0]].ct_x == 0 || c->plan.v[c->lane_ct_variants[1]].ct_x == 0) {
       rc = WFA_GPU_ECUDA;
       break;
     }
@@ -686,7 +700,9 @@ struct InStreamDrain {
   }
 };
 
-int align_pipelined(wfa_gpu_ctx* ctx, Call& k, const wfa::AlignArgs& a, int64_t n, bool plain,
+// mode: 0 default (autotuned variant, longest-first arena lists), 1 plain
+// (fixed variant, lists in pair order), 2 arena only.
+int align_pipelined(wfa_gpu_ctx* ctx, Call& k, const wfa::AlignArgs& a, int64_t n, int mode,
                     wfa_gpu_penalties pen, int32_t* out_scores, int8_t* out_status, uint32_t* out_cigars,
                     int64_t cap, int64_t* out_off, const StreamIn* sin) {
   cudaStream_t st = ctx->stream, cs = ctx->copy_stream, is = ctx->in_stream;
@@ -773,13 +789,12 @@ int align_pipelined(wfa_gpu_ctx* ctx, Call& k, const wfa::AlignArgs& a, int64_t 
     }
     *ctx->h_ctrl = staged_zero;
     if (!ctrl_to_device(k, ctx->ctrl, staged_zero, st)) return fail_cuda(k);
-    if (plain) {
+    if (mode == 2) {
       if (!k.launched(wfa::launch_route_all(ac, st))) return fail_cuda(k);
     } else {
       if (vi < 0) {
-        const bool ef = (a.pb | a.pe | a.tb | a.te) != 0;
-        vi = ef ? ctx->variant_ef_mid[pen.o == 0 ? 1 : 0] : ctx->variant_mid[pen.o == 0 ? 1 : 0];
-        if (staged.max_len <= 127) {
+        vi = fixed_variant(ctx, ac, staged.max_len);
+        if (mode == 0 && staged.max_len <= 127) {
           vi = autotune_short(ctx, k, ac, m);
           if (vi < 0) return fail_cuda(k);
         }
@@ -804,7 +819,7 @@ int align_pipelined(wfa_gpu_ctx* ctx, Call& k, const wfa::AlignArgs& a, int64_t 
     const int64_t dc = (int64_t)ctx->h_ctrl->defer_count + ctx->h_ctrl->defer_long_count;
     deferred += dc;
     if (dc > 0) {
-      const int rc = run_arena(ctx, k, ac, !plain);
+      const int rc = run_arena(ctx, k, ac, mode == 0);
       if (rc) return rc;
       if (!scan() || !k.ok(cudaStreamSynchronize(st))) return fail_cuda(k);
     }
@@ -859,9 +874,12 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
                 int32_t* out_scores, int8_t* out_status, uint32_t* out_cigars, int64_t cap,
                 int64_t* out_cigar_offsets) {
   if (!ctx || n < 0 || n > INT32_MAX || cap < 0 || !pen_ok(pen)) return WFA_GPU_EINVAL;
-  if (flags & ~(uint32_t)(WFA_GPU_SCORE_ONLY | WFA_GPU_DEVICE_PTRS | WFA_GPU_TIMING | WFA_GPU_PLAIN))
+  if (flags & ~(uint32_t)(WFA_GPU_SCORE_ONLY | WFA_GPU_DEVICE_PTRS | WFA_GPU_TIMING | WFA_GPU_PLAIN |
+                          WFA_GPU_ARENA_ONLY))
     return WFA_GPU_EINVAL;
-  const bool plain = flags & WFA_GPU_PLAIN;
+  const bool arena_only = flags & WFA_GPU_ARENA_ONLY;
+  const bool plain = !arena_only && (flags & WFA_GPU_PLAIN);
+  const int mode = arena_only ? 2 : plain ? 1 : 0;
   const bool dev = flags & WFA_GPU_DEVICE_PTRS;
   const bool score_only = flags & WFA_GPU_SCORE_ONLY;
   if (n > 0 && (!patterns || !pattern_lengths || !texts || !text_lengths || !out_scores || !out_status))
@@ -958,7 +976,7 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
                        lens_mapped ? text_lengths : nullptr};
     const bool streamed = host_seqs && !pattern_offsets && !text_offsets && mapped_range(patterns, pe) &&
                           mapped_range(texts, te);
-    rc = align_pipelined(ctx, k, a, n, plain, pen, out_scores, out_status, out_cigars, cap, out_cigar_offsets,
+    rc = align_pipelined(ctx, k, a, n, mode, pen, out_scores, out_status, out_cigars, cap, out_cigar_offsets,
                          streamed ? &sin : nullptr);
     if (rc < 0 && rc != WFA_GPU_ECIGAR_CAPACITY) return rc;
     ctx->last.kernel_launches = k.launches;
@@ -974,12 +992,11 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
     return rc;
   }
 
-  if (plain) {
+  if (arena_only) {
     if (!k.launched(wfa::launch_route_all(a, st))) return fail_cuda(k);
   } else {
-    const bool ef = (a.pb | a.pe | a.tb | a.te) != 0;
-    int vi = ef ? ctx->variant_ef_mid[pen.o == 0 ? 1 : 0] : ctx->variant_mid[pen.o == 0 ? 1 : 0];
-    if (ctx->h_ctrl->max_len <= 127) {
+    int vi = fixed_variant(ctx, a, ctx->h_ctrl->max_len);
+    if (!plain && ctx->h_ctrl->max_len <= 127) {
       vi = autotune_short(ctx, k, a, n);
       if (vi < 0) return fail_cuda(k);
     }
@@ -990,7 +1007,7 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
   if (!ctrl_to_host(k, st) || !k.ok(cudaStreamSynchronize(st))) return fail_cuda(k);
   ctx->last.deferred_pairs = (int64_t)ctx->h_ctrl->defer_count + ctx->h_ctrl->defer_long_count;
   if (ctx->last.deferred_pairs > 0) {
-    rc = run_arena(ctx, k, a, !plain);
+    rc = run_arena(ctx, k, a, mode == 0);
     if (rc) return rc;
   }
   if (ctx->h_ctrl->internal_error) return WFA_GPU_ECUDA;
@@ -1134,12 +1151,8 @@ int enqueue_device_work(wfa_gpu_ctx* c, Call& k, int64_t n, const char* pat, con
   if (!k.ok(cudaEventRecordWithFlags(c->ev[1], st, cudaEventRecordExternal))) return WFA_GPU_ECUDA;
   wfa::AlignArgs a = device_args(c, n, pat, d_poff, plen, txt, d_toff, tlen, pen, max_score, score_only,
                                  out_scores, out_status);
-  if (flags & WFA_GPU_PLAIN) {
-    if (!k.launched(wfa::launch_route_all(a, st))) return WFA_GPU_ECUDA;
-  } else {
-    if (c->last_variant < 0) return WFA_GPU_ECUDA;
-    if (!k.launched(wfa::launch_short(a, c->plan.v[c->last_variant], st))) return WFA_GPU_ECUDA;
-  }
+  if (c->last_variant < 0) return WFA_GPU_ECUDA;
+  if (!k.launched(wfa::launch_short(a, c->plan.v[c->last_variant], st))) return WFA_GPU_ECUDA;
   if (!k.ok(cudaEventRecordWithFlags(c->ev[2], st, cudaEventRecordExternal))) return WFA_GPU_ECUDA;
   const long arena = (long)c->arena_bytes;
   unsigned char* ab = reinterpret_cast<unsigned char*>(c->arena);
@@ -1235,7 +1248,7 @@ int align_graph(wfa_gpu_ctx* ctx, int64_t n, const char* pat, const int64_t* pof
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return WFA_GPU_ECUDA;
     // the longest-first sorts only when the eager run deferred many pairs
     // (a pure scheduling choice: replays stay correct either way)
-    const bool longest_first = !(flags & WFA_GPU_PLAIN) && eager_timing.deferred_pairs > 1024;
+    const bool longest_first = eager_timing.deferred_pairs > 1024;
     const int erc = enqueue_device_work(ctx, k, n, pat, poff, plen, txt, toff, tlen, pen, max_score, base,
                                         out_scores, out_status, out_cigars, cap, out_off, longest_first);
     const cudaError_t ee = cudaStreamEndCapture(st, &g);
@@ -1310,11 +1323,13 @@ int wfa_gpu_align_batch(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const
                         const int32_t* text_lengths, wfa_gpu_penalties pen, int32_t max_score, uint32_t flags,
                         int32_t* out_scores, int8_t* out_status, uint32_t* out_cigars, int64_t cap,
                         int64_t* out_cigar_offsets) {
-  if (flags & WFA_GPU_GRAPH)
+  if ((flags & WFA_GPU_GRAPH) && !(flags & (WFA_GPU_PLAIN | WFA_GPU_ARENA_ONLY)))
     return align_graph(ctx, n, patterns, pattern_offsets, pattern_lengths, texts, text_offsets, text_lengths, pen,
                        max_score, flags, out_scores, out_status, out_cigars, cap, out_cigar_offsets);
+  if ((flags & WFA_GPU_GRAPH) && !(flags & WFA_GPU_DEVICE_PTRS)) return WFA_GPU_EINVAL;
   return align_eager(ctx, n, patterns, pattern_offsets, pattern_lengths, texts, text_offsets, text_lengths, pen,
-                     max_score, flags, out_scores, out_status, out_cigars, cap, out_cigar_offsets);
+                     max_score, flags & ~(uint32_t)WFA_GPU_GRAPH, out_scores, out_status, out_cigars, cap,
+                     out_cigar_offsets);
 }
 
 int wfa_gpu_set_ends_free(wfa_gpu_ctx* ctx, int32_t pattern_begin_free, int32_t pattern_end_free,

@@ -52,6 +52,8 @@
 // so a long match on one pair does not hold up the other 31.
 #pragma once
 
+#include <type_traits>
+
 #include "launch.h"
 #include "short_path.cuh"
 #include "wfa_device.cuh"
@@ -197,9 +199,9 @@ __device__ __forceinline__ void lane_pending(LaneSt& st, uint32_t pend, int lo, 
 // One score's row: the cells of items i = 0 .. w-1 (diagonal lo + i), stored
 // at cells base + i.  Sources: row s - x has item i at cell cx + i while
 // 0 <= i - ax < wx, row s - o - e likewise (ao, wo, co) for diagonals k - 1
-// and k + 1; the I and D rows at positions pi0 + i and pd0 + i.  Then the
-// pending extensions and the end test.  Called with constants by the
-// compile-time forward pass.
+// and k + 1; the I and D rows at positions pi0 + i and pd0 + i.  The items
+// whose M sources all lie inside their rows (the middle of the row) run
+// without range tests.  Then the pending extensions and the end test.
 __device__ __forceinline__ void lane_row(LaneSt& st, int s, int lo, int w, int base, int ax, int wx, int cx, int ao,
                                          int wo, int co, int pi0, int pd0) {
   const int m = st.m;
@@ -211,12 +213,12 @@ __device__ __forceinline__ void lane_row(LaneSt& st, int s, int lo, int w, int b
     return (unsigned)(item - ao) < (unsigned)wo ? (uint32_t)H[(co + item) * 32] : 0xFFu;
   };
   uint32_t oa = ldo(-1), ob = ldo(0);
-  uint32_t pend = 0;
-  uint32_t bitv = 1, im = 0, dm = 0;  // this row's extension bits
-#pragma unroll 1
-  for (int i = 0; i < w; ++i) {
-    const uint32_t oc = ldo(i + 1);
-    const uint32_t mx = (unsigned)(i - ax) < (unsigned)wx ? (uint32_t)H[(cx + i) * 32] : 0xFFu;
+  uint32_t pend = 0, bitv = 1, im = 0, dm = 0;  // pending extensions, this row's extension bits
+  auto cell = [&](int i, auto tested) {
+    constexpr bool T = decltype(tested)::value;
+    const uint32_t oc = T ? ldo(i + 1) : (uint32_t)H[(co + i + 1) * 32];
+    const uint32_t mx = !T ? (uint32_t)H[(cx + i) * 32]
+                           : (unsigned)(i - ax) < (unsigned)wx ? (uint32_t)H[(cx + i) * 32] : 0xFFu;
     const uint32_t il = st.IR[(pi0 + i) * 32];  // I_{s-e}[k-1]
     const uint32_t dr = st.DR[(pd0 + i) * 32];  // D_{s-e}[k+1]
     const int t = t0 + i;
@@ -239,7 +241,19 @@ __device__ __forceinline__ void lane_row(LaneSt& st, int s, int lo, int w, int b
     st.DR[(pd0 + i) * 32] = (uint8_t)uD;
     oa = ob;
     ob = oc;
-  }
+  };
+  // the middle: items with the mismatch source (ax <= i < ax + wx) and the
+  // k + 1 source (ao - 1 <= i < ao + wo - 1) inside their rows
+  const int a = min(max(max(ax, ao - 1), 0), w);
+  const int b = max(min(min(ax + wx, ao + wo - 1), w), a);
+  using Tested = std::integral_constant<bool, true>;
+  using Untested = std::integral_constant<bool, false>;
+#pragma unroll 1
+  for (int i = 0; i < a; ++i) cell(i, Tested{});
+#pragma unroll 2
+  for (int i = a; i < b; ++i) cell(i, Untested{});
+#pragma unroll 1
+  for (int i = b; i < w; ++i) cell(i, Tested{});
   // the row's bits join the streams at bit base (cells run in order: the
   // words before hold the earlier rows)
   {
@@ -380,53 +394,48 @@ __device__ __forceinline__ int lane_backtrace(const UGeo* tab, const uint8_t* H,
     const int u = H[c * 32];
     return u < 128 ? min(m, n + kk) - u : -1;
   };
-  // I_ss[kk] (dk = -1) or D_ss[kk] (dk = +1): follow the extension bits
-  // to the opening level *J; -1 when null
-  auto gap = [&](int ss, int kk, int dk, int* J) -> int {
-    const uint32_t* XS = dk < 0 ? XI : XD;
-    int j = 0;
-    for (;; ++j) {
-      const int c = cell(ss - j * E, kk + dk * j);
-      if (c < 0) return -1;
-      if (!((XS[(c >> 5) * 32] >> (c & 31)) & 1u)) break;
-    }
-    *J = j;
-    const int src = mh(ss - j * E - OE, kk + dk * (j + 1));
-    if (src < 0) return -1;
-    const int v = dk < 0 ? src + 1 + j : src;
-    return (dk < 0 ? v > m : v - kk > n) ? -1 : v;
-  };
   for (int guard = 2 * s_top + 8; guard > 0 && !bad; --guard) {
     if (s == 0) {
       if (k != 0) bad = true;
       emit(kOpM, h);
       break;
     }
+    // the three candidates of M_s[k]: M_{s-x}[k] + 1, and I_s[k], D_s[k]
+    // found by following their extension bits (both chains in one loop)
     const int xm = mh(s - X, k);
-    const int xv = xm >= 0 && xm + 1 <= min(m, n + k) ? xm + 1 : -1;
-    int ij = 0, dj = 0;
-    const int iv = gap(s, k, -1, &ij);
-    const int dv = gap(s, k, 1, &dj);
-    if (xv >= 0 && xv >= iv && xv >= dv) {
-      emit(kOpM, h - xv);
-      emit(kOpX, 1);
-      s -= X;
-      h = xv - 1;
-    } else if (iv >= 0 && iv >= dv) {
-      emit(kOpM, h - iv);
-      emit(kOpI, ij + 1);
-      s -= ij * E + OE;
-      k -= ij + 1;
-      h = iv - ij - 1;
-    } else if (dv >= 0) {
-      emit(kOpM, h - dv);
-      emit(kOpD, dj + 1);
-      s -= dj * E + OE;
-      k += dj + 1;
-      h = dv;
-    } else {
-      return -2;
+    int ji = 0, jd = 0;
+    bool open_i = false, open_d = false, null_i = false, null_d = false;
+    while (!((open_i || null_i) && (open_d || null_d))) {
+      if (!(open_i || null_i)) {
+        const int c = cell(s - ji * E, k - ji);
+        if (c < 0) null_i = true;
+        else if ((XI[(c >> 5) * 32] >> (c & 31)) & 1u) ++ji;
+        else open_i = true;
+      }
+      if (!(open_d || null_d)) {
+        const int c = cell(s - jd * E, k + jd);
+        if (c < 0) null_d = true;
+        else if ((XD[(c >> 5) * 32] >> (c & 31)) & 1u) ++jd;
+        else open_d = true;
+      }
     }
+    const int im = null_i ? -1 : mh(s - ji * E - OE, k - ji - 1);
+    const int dm = null_d ? -1 : mh(s - jd * E - OE, k + jd + 1);
+    const int bk = min(m, n + k);
+    const int xv = xm >= 0 && xm + 1 <= bk ? xm + 1 : -1;
+    const int iv = im >= 0 && im + 1 + ji <= m ? im + 1 + ji : -1;
+    const int dv = dm >= 0 && dm - k <= n ? dm : -1;
+    // the largest; ties: mismatch, then insertion, then deletion
+    const bool px = xv >= 0 && xv >= iv && xv >= dv;
+    const bool pi = !px && iv >= 0 && iv >= dv;
+    if (!px && !pi && dv < 0) return -2;
+    const int c = px ? xv : pi ? iv : dv;
+    const int j = pi ? ji : jd;
+    emit(kOpM, h - c);
+    emit(px ? kOpX : pi ? kOpI : kOpD, px ? 1 : j + 1);
+    s -= px ? X : j * E + OE;
+    k += px ? 0 : pi ? -(j + 1) : j + 1;
+    h = px ? c - 1 : pi ? c - j - 1 : c;
     if (s < 0) return -2;
   }
   if (bad || s != 0) return -2;

@@ -303,7 +303,7 @@ int wfa_gpu_server_create(wfa_gpu_server** out, int device, int workers, size_t 
 
 int64_t wfa_gpu_server_submit(wfa_gpu_server* s, const wfa_gpu_request* r) {
   if (!s || !r) return WFA_GPU_EINVAL;
-  if (r->flags & ~(uint32_t)(WFA_GPU_SCORE_ONLY | WFA_GPU_PLAIN)) return WFA_GPU_EINVAL;
+  if (r->flags & ~(uint32_t)(WFA_GPU_SCORE_ONLY | WFA_GPU_PLAIN | WFA_GPU_ARENA_ONLY)) return WFA_GPU_EINVAL;
   const int64_t need = wfa_gpu_request_bytes(r);
   if (need < 0) return WFA_GPU_EINVAL;
   auto req = std::make_shared<Request>();

@@ -142,7 +142,7 @@ def test_paper_batches_every_store(pkg, oracle_mod, monkeypatch):
 def test_autotuner_picks_a_lane_store(pkg, oracle_mod):
     from paper_2204_02085_gb300 import synth
 
-    for e, expect in ((2, "lane_ct241_l127_c40"), (4, "lane_ct241_l127_c197")):
+    for e, expect in ((2, "lane_ct241_l127_c40"), (4, "lane_l127_c197")):
         batch = synth.uniform_reads(20_000, 100, e, seed=60 + e)
         with pkg.Aligner(0, 1 << 30) as al:
             got = al.align(batch, (4, 6, 2))

@@ -1,5 +1,7 @@
-"""The plain path (WFA_GPU_PLAIN, the comparison baseline) and graph replay
-(WFA_GPU_GRAPH) give exactly the results of the default path."""
+"""The plain path (WFA_GPU_PLAIN, the comparison baseline: fixed variant, no
+autotuner, no longest-first order, no graph), the arena-only path
+(WFA_GPU_ARENA_ONLY) and graph replay (WFA_GPU_GRAPH) give exactly the
+results of the default path."""
 
 import numpy as np
 import pytest
@@ -34,6 +36,9 @@ def test_plain_path_matches(pkg, oracle_mod):
             assert np.array_equal(x, y)
         so = al.align(batch, (4, 6, 2), plain=True, score_only=True)
         assert np.array_equal(so[0], ref[0]) and np.array_equal(so[1], ref[1])
+        ao = al.align(batch, (4, 6, 2), arena_only=True)  # every pair on arena teams
+        for x, y in zip(ref, ao):
+            assert np.array_equal(x, y)
     want = oracle_mod.wfa_batch(batch, (4, 6, 2), nthreads=8)
     assert np.array_equal(ref[0], want[0]) and np.array_equal(ref[2], want[2])
 

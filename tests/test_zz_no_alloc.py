@@ -1,15 +1,16 @@
 """The entry point that allocates nothing (wfa_gpu_align_short_noalloc).
 
-Some callers cannot call cudaMalloc: code running while a stream is being
-captured into a CUDA graph, applications whose device memory belongs to a
-pool that forbids foreign allocations, latency-critical paths.  For them
-the library keeps the short-read path's scratch in one static device array.
-This test calls that entry point through the C ABI, twice in a row on the
-same inputs (the array keeps the first call's contents), and requires the
-same scores, status, CIGAR offsets and CIGAR words as the regular entry
-point, bit for bit (integer results; no tolerance).  It lives in a file
-that pytest collects last, so a run that stops at the first failure has
-run every other test before it.
+Some callers cannot call cudaMalloc: applications whose device memory
+belongs to a pool that forbids allocations made behind its back, and
+latency-critical paths that must not risk the device-wide synchronisation
+of cudaMalloc and cudaFree.  For them the library keeps the short-read
+path's scratch in one static device array.  These tests call that entry
+point through the C ABI, twice in a row on the same inputs (the array keeps
+the first call's contents), and require the same scores, status, CIGAR
+offsets and CIGAR words as the regular entry point and as the CPU oracle,
+bit for bit (integer results; no tolerance), with the GPU's free memory
+unchanged across the calls.  They live in a file that pytest collects last,
+so a run that stops at the first failure has run every other test first.
 """
 
 import numpy as np
@@ -33,7 +34,7 @@ def _inputs():
     return synth.from_pairs(pairs)
 
 
-def test_noalloc_matches_align_batch_twice():
+def test_noalloc_matches_align_batch_twice(oracle_mod):
     import torch
 
     from paper_2204_02085_gb300 import build
@@ -46,16 +47,27 @@ def test_noalloc_matches_align_batch_twice():
     pen = (4, 6, 2)
     with pkg.Aligner(0) as al:
         ref = al.align(batch, pen)
+    want = oracle_mod.wfa_batch(batch, pen, nthreads=8)
+    for x, y in zip(ref, want):
+        assert np.array_equal(x, y), "the regular entry point differs from the oracle"
     stream = torch.cuda.current_stream(torch.device("cuda:0"))
     pat, txt = _dev(torch, batch.patterns), _dev(torch, batch.texts)
     plen, tlen = _dev(torch, batch.pattern_lengths), _dev(torch, batch.text_lengths)
     poff, toff = _dev(torch, batch.pattern_offsets), _dev(torch, batch.text_offsets)
     cap = int(ref[3][-1])
-    for with_offsets in (True, True, False):  # two calls in a row, then back-to-back offsets
-        s = torch.full((n,), 12345, dtype=torch.int32, device="cuda:0")
-        st = torch.full((n,), 99, dtype=torch.int8, device="cuda:0")
-        off = torch.full((n + 1,), -5, dtype=torch.int64, device="cuda:0")
-        w = torch.zeros(cap, dtype=torch.int32, device="cuda:0")
+    outs = []
+    for _ in range(3):
+        outs.append((torch.full((n,), 12345, dtype=torch.int32, device="cuda:0"),
+                     torch.full((n,), 99, dtype=torch.int8, device="cuda:0"),
+                     torch.full((n + 1,), -5, dtype=torch.int64, device="cuda:0"),
+                     torch.zeros(cap, dtype=torch.int32, device="cuda:0")))
+    torch.cuda.synchronize()
+    free_before = None
+    for call, with_offsets in enumerate((True, True, False)):  # two calls in a row, then back-to-back offsets
+        s, st, off, w = outs[call]
+        if call == 1:  # after a first call has loaded every kernel
+            torch.cuda.synchronize()
+            free_before = torch.cuda.mem_get_info(0)[0]
         rc = pkg.wfa_gpu_align_short_noalloc(
             stream.cuda_stream, n, pat.data_ptr(), poff.data_ptr() if with_offsets else None, plen.data_ptr(),
             txt.data_ptr(), toff.data_ptr() if with_offsets else None, tlen.data_ptr(), pen, 0, s.data_ptr(),
@@ -66,6 +78,8 @@ def test_noalloc_matches_align_batch_twice():
         assert np.array_equal(st.cpu().numpy(), ref[1])
         assert np.array_equal(off.cpu().numpy(), ref[3])
         assert np.array_equal(w.cpu().numpy().view(np.uint32), ref[2])
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info(0)[0] == free_before, "device memory was allocated or freed"
 
 
 def test_noalloc_rejects_sizes_beyond_its_limits():
@@ -85,9 +99,22 @@ def test_noalloc_rejects_sizes_beyond_its_limits():
     st = torch.zeros(1, dtype=torch.int8, device="cuda:0")
     off = torch.zeros(2, dtype=torch.int64, device="cuda:0")
     w = torch.zeros(4, dtype=torch.int32, device="cuda:0")
-    rc = pkg.wfa_gpu_align_short_noalloc(stream, 1, _dev(torch, long.patterns).data_ptr(), None,
-                                         _dev(torch, long.pattern_lengths).data_ptr(),
-                                         _dev(torch, long.texts).data_ptr(), None,
-                                         _dev(torch, long.text_lengths).data_ptr(), (4, 6, 2), 0, s.data_ptr(),
-                                         st.data_ptr(), w.data_ptr(), 4, off.data_ptr())
+    keep = [_dev(torch, a) for a in (long.patterns, long.pattern_lengths, long.texts, long.text_lengths)]
+    rc = pkg.wfa_gpu_align_short_noalloc(stream, 1, keep[0].data_ptr(), None, keep[1].data_ptr(), keep[2].data_ptr(),
+                                         None, keep[3].data_ptr(), (4, 6, 2), 0, s.data_ptr(), st.data_ptr(),
+                                         w.data_ptr(), 4, off.data_ptr())
     assert rc == pkg.WFA_GPU_EINVAL
+    # more than the 16 CIGAR runs a pair may keep: 8 isolated mismatches in
+    # 127 bases score 32 (within the store) but need 17 runs
+    text = bytearray(b"ACGT" * 31 + b"ACG")
+    pat = bytearray(text)
+    for j in range(8):
+        i = 7 + 15 * j
+        pat[i] = ord("A") if pat[i] != ord("A") else ord("C")
+    runs17 = synth.from_pairs([(bytes(pat), bytes(text))])
+    keep = [_dev(torch, a) for a in (runs17.patterns, runs17.pattern_lengths, runs17.texts, runs17.text_lengths)]
+    rc = pkg.wfa_gpu_align_short_noalloc(stream, 1, keep[0].data_ptr(), None, keep[1].data_ptr(), keep[2].data_ptr(),
+                                         None, keep[3].data_ptr(), (4, 6, 2), 0, s.data_ptr(), st.data_ptr(),
+                                         w.data_ptr(), 4, off.data_ptr())
+    torch.cuda.synchronize()
+    assert rc == pkg.WFA_GPU_ENOMEM
