@@ -147,3 +147,19 @@ def test_graph_replay_with_arena_retries(pkg, oracle_mod):
             got = d.out()
             for x, y in zip(got, want):
                 assert np.array_equal(x, y)
+
+
+def test_work_balanced_shards_reassemble(pkg, oracle_mod):
+    """One mixed-length batch split into work-balanced shares, each aligned by
+    its own context (two contexts on GPU 0 stand in for two devices: their
+    kernels never wait on each other), reassembled: the one-context result
+    and the oracle's."""
+    from paper_2204_02085_gb300 import sharding, synth
+
+    batch = synth.mixed_reads(2000, 100, 2000, 0.10, 0.05, seed=90)
+    got = sharding.align_multi_gpu(batch, (4, 6, 2), [0, 0], scratch_bytes=2 << 30)
+    with pkg.Aligner(0, 2 << 30) as al:
+        one = al.align(batch, (4, 6, 2))
+    want = oracle_mod.wfa_batch(batch, (4, 6, 2), nthreads=16)
+    for x, y, z in zip(got, one, want):
+        assert np.array_equal(x, y) and np.array_equal(x, z)

@@ -6,6 +6,7 @@ gloo ranks on the CPU."""
 import os
 import socket
 
+import numpy as np
 import pytest
 import torch.multiprocessing as mp
 
@@ -69,3 +70,68 @@ def test_shard_range_covers(n, world):
 def test_single_process_identity():
     assert sharding.max_over_ranks(3.5) == 3.5
     sharding.barrier()
+
+
+def _work_worker(rank, world, port, q):
+    """Rank `rank` aligns its work-balanced share of a mixed-length sample
+    with the oracle (CPU) and sends it to rank 0, which reassembles."""
+    import torch.distributed as dist
+
+    import oracle
+    from paper_2204_02085_gb300 import synth
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", init_method="env://", rank=rank, world_size=world)
+    try:
+        batch = synth.mixed_reads(300, 100, 2000, 0.10, 0.05, seed=3)
+        w = sharding.work_estimate(batch.pattern_lengths, batch.text_lengths)
+        b, e = sharding.shard_by_work(w, rank, world)
+        sc, st, words, off = oracle.wfa_batch(sharding.sub_batch(batch, b, e), (4, 6, 2), nthreads=2)
+        gathered = [None] * world if rank == 0 else None
+        dist.gather_object((b, sc, st, words, off), gathered, dst=0)
+        if rank == 0:
+            q.put(("parts", gathered, [sharding.shard_by_work(w, r, world) for r in range(world)]))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_work_balanced_reassembly(oracle_mod):
+    from paper_2204_02085_gb300 import synth
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_work_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    tag, parts, ranges = q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    batch = synth.mixed_reads(300, 100, 2000, 0.10, 0.05, seed=3)
+    w = sharding.work_estimate(batch.pattern_lengths, batch.text_lengths)
+    # the shares' estimated work differs by at most one pair's
+    loads = [float(w[b:e].sum()) for b, e in ranges]
+    assert abs(loads[0] - loads[1]) <= float(w.max())
+    assert ranges[0][0] == 0 and ranges[0][1] == ranges[1][0] and ranges[1][1] == batch.n
+    got = sharding.reassemble(parts, batch.n)
+    want = oracle_mod.wfa_batch(batch, (4, 6, 2), nthreads=4)
+    for x, y in zip(got, want):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 5])
+def test_shard_by_work_balances(world):
+    rng = np.random.default_rng(world)
+    w = rng.integers(1, 1000, size=997).astype(np.float64) ** 2
+    bounds = [sharding.shard_by_work(w, r, world) for r in range(world)]
+    assert bounds[0][0] == 0 and bounds[-1][1] == len(w)
+    for (b0, e0), (b1, e1) in zip(bounds, bounds[1:]):
+        assert e0 == b1
+    loads = [w[b:e].sum() for b, e in bounds]
+    assert max(loads) - min(loads) <= 2 * w.max()
+    # each share's end is the first pair reaching its fraction of the total
+    total = w.sum()
+    for r, (b, e) in enumerate(bounds[:-1]):
+        assert w[:e].sum() >= (r + 1) * total / world > w[:e - 1].sum()
