@@ -267,16 +267,23 @@ int wfa_gpu_align_short_noalloc(void *stream, int64_t n_pairs,
  * Serving: continuous batching of alignment requests.
  *
  * Requests (batches of pairs, of any size, arriving at any time) are queued
- * and admitted in arrival order onto `workers` slots, each a context with its
- * own stream, buffers and scratch arena, so the work of several slots
- * overlaps on the GPU.  A request is admitted when a slot is free and its
- * estimated device memory (wfa_gpu_request_bytes) fits what the admitted
- * ones leave of the memory budget (a request alone is always admitted).  A
- * slot that admits a request also takes the requests queued right behind it
- * that have the same penalties, max_score and flags, up to
- * WFA_GPU_SERVER_MERGE_PAIRS pairs in all and within the budget: it copies
- * their pairs into one page-locked batch, aligns that with one call and
- * copies each request's results back into its own buffers.
+ * and admitted onto `workers` slots, each a context with its own stream and
+ * buffers, so the work of several slots overlaps on the GPU.  The server
+ * owns one scratch arena (the memory budget); every call runs on a slice of
+ * it sized to the call's estimated wavefront need (see
+ * wfa_gpu_request_bytes; at least 64 MiB, at most half the arena: on a
+ * smaller slice than they would like, the arena kernels run fewer pairs at
+ * once).  A request is admitted when a
+ * slot is free and its slice fits the free arena: the oldest that fits goes
+ * first (a later request may pass one that does not fit yet, until that one
+ * has waited 50 ms; then the slots drain until it fits; a request alone
+ * always fits, on the whole arena at most).  A slot that admits a request
+ * also takes the requests queued right behind it that have the same
+ * penalties, max_score and flags, up to WFA_GPU_SERVER_MERGE_PAIRS pairs in
+ * all, when their slice fits too: it gathers their pairs into one batch,
+ * copies it to the device, aligns it with one device-pointer call and copies
+ * each request's results back into its own buffers.  A call in which a pair
+ * outgrew its slice runs once more on the whole arena.
  * Every request's outputs and result code are the ones wfa_gpu_align_batch
  * gives for it alone (pairs are independent: paper Sec. I; a request whose
  * CIGAR words exceed its capacity gets WFA_GPU_ECIGAR_CAPACITY as alone, and
@@ -284,6 +291,8 @@ int wfa_gpu_align_short_noalloc(void *stream, int64_t n_pairs,
  * depends on the mix.
  * --------------------------------------------------------------------------- */
 #define WFA_GPU_SERVER_MERGE_PAIRS 65536
+/* the edit rate (edits per base) the arena need of a request is estimated for */
+#define WFA_GPU_SERVER_EDIT_RATE 0.10
 typedef struct wfa_gpu_server wfa_gpu_server;
 
 /* One request: the arguments of wfa_gpu_align_batch, host memory only
@@ -316,9 +325,10 @@ typedef struct {
 } wfa_gpu_request_stats;
 
 /* Create a server on `device` with `workers` slots (1..64) and a device
- * memory budget (0: 8 GiB): half is split evenly into the slots' scratch
- * arenas, the other half is the admission budget.  Returns OK, EINVAL,
- * ECUDA or ENOMEM; *out is NULL on failure. */
+ * memory budget (0: 8 GiB; at least 64 MiB): the scratch arena the calls
+ * share (the slots' gather and result buffers come on top, grown to the
+ * largest batch they ran).  Returns OK, EINVAL, ECUDA or ENOMEM; *out is
+ * NULL on failure. */
 int wfa_gpu_server_create(wfa_gpu_server **out, int device, int workers, size_t memory_budget_bytes);
 
 /* Queue a request; returns its id (>= 0) or a negative WFA_GPU_* code
@@ -331,8 +341,14 @@ int64_t wfa_gpu_server_submit(wfa_gpu_server *server, const wfa_gpu_request *req
  * running; wait again later), EINVAL for an unknown id. */
 int wfa_gpu_server_wait(wfa_gpu_server *server, int64_t id, double timeout_s, wfa_gpu_request_stats *stats);
 
-/* Estimated device bytes a request holds while it runs (inputs, outputs,
- * per-pair work buffers): the admission rule's measure.  Host-only. */
+/* Estimated device bytes a request holds while it runs: inputs, outputs,
+ * per-pair work buffers, and the arena its wavefronts take -- for pairs
+ * longer than 127 bases (the short-read kernels keep theirs in shared
+ * memory), 3 offsets of 2 bytes (4 from 32,000 bases) on about
+ * (s'/e' + 1)^2 cells, s' = WFA_GPU_SERVER_EDIT_RATE x max(n, m) x
+ * max(x, o + e) / g and e' = e / g (g = gcd(x, o, e)), summed over the 4,096
+ * largest such pairs (no more run at once).  The arena part is what the
+ * server admits requests by.  Host-only. */
 int64_t wfa_gpu_request_bytes(const wfa_gpu_request *req);
 
 /* Finish the admitted requests, drop the queued ones (their waits return

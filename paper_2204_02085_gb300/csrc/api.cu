@@ -112,6 +112,10 @@ struct wfa_gpu_ctx {
   cudaStream_t stream = nullptr;
   int32_t* arena = nullptr;
   size_t arena_bytes = 0;
+  int32_t* own_arena = nullptr;  // the context's own allocation (arena may be borrowed)
+  size_t own_arena_bytes = 0;
+  int occ_medium = 16, occ_long = 2, occ_narrow = 4;  // arena teams per SM
+  int nsm = 1;
   int teams_medium = 1;  // one-warp arena teams
   int teams_long = 1;    // one-CTA arena teams of kLongTeamWide warps
   int teams_narrow = 1;  // one-CTA arena teams of kLongTeamNarrow warps
@@ -188,6 +192,34 @@ void wfa::set_cigar_sink(wfa_gpu_ctx* ctx, wfa::CigarSink sink, void* user) {
   if (!ctx) return;
   ctx->cig_sink = sink;
   ctx->cig_sink_user = user;
+}
+
+namespace {
+
+// Arena teams for the context's arena: as many as fit on the GPU at once,
+// each with a slice of at least 256 KiB (one-warp teams), 4 MiB (wide
+// one-CTA teams) or 8 MiB (narrow ones, which run many more pairs at once:
+// smaller slices sent pairs of a few kbp to the retries); pairs that
+// outgrow their slice are retried with larger ones.
+void size_teams(wfa_gpu_ctx* c) {
+  const long arena_b = (long)c->arena_bytes;
+  c->teams_medium = (int)std::max(1L, std::min((long)c->nsm * c->occ_medium, arena_b / (256L << 10)));
+  c->teams_long = (int)std::max(1L, std::min((long)c->nsm * c->occ_long, arena_b / (4L << 20)));
+  c->teams_narrow = (int)std::max(1L, std::min((long)c->nsm * c->occ_narrow, arena_b / (8L << 20)));
+}
+
+}  // namespace
+
+void wfa::set_arena(wfa_gpu_ctx* ctx, void* arena, size_t bytes) {
+  if (!ctx) return;
+  if (arena && bytes >= 4096) {
+    ctx->arena = static_cast<int32_t*>(arena);
+    ctx->arena_bytes = bytes & ~(size_t)255;
+  } else {
+    ctx->arena = ctx->own_arena;
+    ctx->arena_bytes = ctx->own_arena_bytes;
+  }
+  size_teams(ctx);
 }
 
 namespace {
@@ -610,6 +642,8 @@ int wfa_gpu_create(wfa_gpu_ctx** out, int device, size_t scratch_bytes) {
     c->arena_bytes &= ~(size_t)255;
     if (c->arena_bytes < 4096) { rc = WFA_GPU_EINVAL; break; }
     if (cudaMalloc(reinterpret_cast<void**>(&c->arena), c->arena_bytes) != cudaSuccess) { rc = WFA_GPU_ENOMEM; break; }
+    c->own_arena = c->arena;
+    c->own_arena_bytes = c->arena_bytes;
     if (wfa::short_plan(device, &c->plan) != cudaSuccess) { rc = WFA_GPU_ECUDA; break; }
     if (c->plan.count < 23 || c->plan.v[c->lane_variants[0]].kind != 1 || c->plan.v[c->lane_variants[3]].kind != 1 ||
         c->plan.v[c->lane_ct_variants[0]].ct_x == 0 || c->plan.v[c->lane_ct_variants[1]].ct_x == 0) {
@@ -622,23 +656,14 @@ int wfa_gpu_create(wfa_gpu_ctx** out, int device, size_t scratch_bytes) {
       const int v = std::atoi(ev);
       if (v >= 0 && v < c->plan.count && c->plan.v[v].max_len >= 127) c->variant_forced = v;
     }
-    int nsm = 1;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
-    // as many teams as fit on the GPU at once, each with an arena slice of
-    // at least 256 KiB (one-warp teams), 4 MiB (wide one-CTA teams) or 8 MiB
-    // (narrow ones, which run many more pairs at once: smaller slices sent
-    // pairs of a few kbp to the retries); pairs that outgrow their slice are
-    // retried with larger ones
-    int tm = 16, tl = 2, tn = 4;
-    if (wfa::arena_occupancy(1, &tm) != cudaSuccess || wfa::arena_occupancy(wfa::kLongTeamWide, &tl) != cudaSuccess ||
-        wfa::arena_occupancy(wfa::kLongTeamNarrow, &tn) != cudaSuccess) {
+    cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device);
+    if (wfa::arena_occupancy(1, &c->occ_medium) != cudaSuccess ||
+        wfa::arena_occupancy(wfa::kLongTeamWide, &c->occ_long) != cudaSuccess ||
+        wfa::arena_occupancy(wfa::kLongTeamNarrow, &c->occ_narrow) != cudaSuccess) {
       rc = WFA_GPU_ECUDA;
       break;
     }
-    const long arena_b = (long)c->arena_bytes;
-    c->teams_medium = (int)std::max(1L, std::min((long)nsm * tm, arena_b / (256L << 10)));
-    c->teams_long = (int)std::max(1L, std::min((long)nsm * tl, arena_b / (4L << 20)));
-    c->teams_narrow = (int)std::max(1L, std::min((long)nsm * tn, arena_b / (8L << 20)));
+    size_teams(c);
     if (const char* ev = std::getenv("WFA_GPU_TEAMS")) {  // tuning override: "<medium>,<wide>[,<narrow>]"
       int a = 0, b = 0, d = 0;
       const int got = std::sscanf(ev, "%d,%d,%d", &a, &b, &d);
@@ -1470,7 +1495,7 @@ void wfa_gpu_destroy(wfa_gpu_ctx* c) {
   if (c->in_stream) cudaStreamSynchronize(c->in_stream);
   c->h_score.release(); c->h_status.release(); c->h_off.release(); c->h_cig.release();
   c->ring.release(); c->h_bounds.release();
-  if (c->arena) cudaFree(c->arena);
+  if (c->own_arena) cudaFree(c->own_arena);
   if (c->ctrl) cudaFree(c->ctrl);
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
   if (c->h_total) cudaFreeHost(c->h_total);

@@ -17,4 +17,10 @@ using CigarSink = uint32_t* (*)(void* user, int64_t words);
 // thread-safe against calls on the same context.
 __attribute__((visibility("hidden"))) void set_cigar_sink(wfa_gpu_ctx* ctx, CigarSink sink, void* user);
 
+// Run the context's later calls with the scratch arena [arena, arena +
+// bytes) of device memory the caller owns (arena teams and slices sized
+// for it), or, with arena NULL, with the context's own arena again.  Not
+// thread-safe against calls on the same context.
+__attribute__((visibility("hidden"))) void set_arena(wfa_gpu_ctx* ctx, void* arena, size_t bytes);
+
 }  // namespace wfa

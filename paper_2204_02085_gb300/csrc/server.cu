@@ -1,10 +1,14 @@
 // server.cu -- continuous batching of alignment requests (the serving half
-// of the C ABI in include/wfa_gpu.h): a FIFO queue, admission by free device
-// memory, and worker slots that each own a context (stream, buffers, arena).
-// A slot that frees up takes the oldest request together with the requests
-// queued behind it that share its parameters, gathers their pairs into one
-// batch (pairs are independent, paper Sec. I), aligns it with one call and
-// scatters every request's results back into its own buffers.
+// of the C ABI in include/wfa_gpu.h): a queue, admission by free scratch
+// arena, and worker slots that each own a context (stream, buffers).  A
+// slot that frees up takes the oldest request that fits the free arena
+// (a later one may pass a request that does not fit yet, until that one has
+// waited kMaxWaitS), together with the requests queued behind it that share
+// its parameters; it gathers their pairs into one batch (pairs are
+// independent, paper Sec. I), copies it to the device, aligns it with one
+// device-pointer call on a slice of the server's arena sized to the batch's
+// estimated wavefront need, and scatters every request's results back into
+// its own buffers.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -13,6 +17,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -27,10 +32,19 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// A request passed over by later ones (it did not fit the free arena) is
+// not passed any more once it has waited this long: the slots then drain
+// until it fits.
+constexpr double kMaxWaitS = 0.05;
+// The smallest arena slice a call runs on (short pairs the short-read kernel
+// defers go to the arena kernels too).
+constexpr int64_t kMinSlice = 64ll << 20;
+
 struct Request {
   int64_t id = 0;
   wfa_gpu_request r{};
-  int64_t need = 0;        // wfa_gpu_request_bytes
+  int64_t need_arena = 0;  // wavefront_bytes: the arena it is admitted by
+  bool whole = false;      // rerun on the whole arena (a pair outgrew its slice)
   int64_t pat_bytes = 0;   // sum of pattern lengths
   int64_t txt_bytes = 0;   // sum of text lengths
   bool mergeable = false;  // well-formed: safe to gather
@@ -63,19 +77,83 @@ struct Pinned {
   }
 };
 
-// A worker slot: its context and the staging of merged batches.
+// Device buffer that grows geometrically (contents not kept).
+template <class T>
+struct Dev {
+  T* p = nullptr;
+  size_t cap = 0;
+  bool ensure(size_t n) {
+    if (n <= cap && p) return true;
+    const size_t want = std::max<size_t>(std::max(n + n / 2, 2 * cap), 4096);
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    if (cudaMalloc(reinterpret_cast<void**>(&p), want * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return false;
+    }
+    cap = want;
+    return true;
+  }
+  ~Dev() {
+    if (p) cudaFree(p);
+  }
+};
+
+// A worker slot: its context and stream, the page-locked gather of merged
+// batches and their device copies.
 struct Slot {
   wfa_gpu_ctx* ctx = nullptr;
+  cudaStream_t stream = nullptr;
   Pinned<char> pat, txt;
-  Pinned<int64_t> poff, toff, off;
+  Pinned<int64_t> off;
   Pinned<int32_t> plen, tlen, score;
   Pinned<int8_t> status;
   Pinned<uint32_t> cig;
+  Dev<char> dpat, dtxt;
+  Dev<int32_t> dplen, dtlen, dscore;
+  Dev<int8_t> dstatus;
+  Dev<int64_t> doff;
+  Dev<uint32_t> dcig;
 };
 
-uint32_t* cigar_sink(void* user, int64_t words) {
-  Slot* s = static_cast<Slot*>(user);
-  return s->cig.ensure((size_t)words) ? s->cig.p : nullptr;
+// Scratch-arena bytes a request's wavefronts hold at once.  Pairs longer than
+// the short-read kernels take (127 bases) go to the arena kernels, which
+// keep every score's M, I and D offsets (2 bytes each below 32,000 bases, 4
+// above) over about (s'/e' + 1)^2 cells, s' the scaled score of
+// WFA_GPU_SERVER_EDIT_RATE edits per base at the costliest edit
+// (max(x, o + e) / g each), e' = e / g; at most kConcurrentTeams pairs are in
+// flight at once, so the estimate sums the kConcurrentTeams largest.
+constexpr int kConcurrentTeams = 4096;
+int gcd2(int a, int b) {
+  while (b) {
+    const int t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+int64_t wavefront_bytes(const wfa_gpu_request& r) {
+  if (r.n_pairs <= 0 || !r.pattern_lengths || !r.text_lengths) return 0;
+  const int g = gcd2(gcd2(r.pen.x, r.pen.o), r.pen.e);
+  if (g <= 0 || r.pen.e <= 0) return 0;
+  const double cost = (double)std::max(r.pen.x, r.pen.o + r.pen.e) / g, es = (double)r.pen.e / g;
+  std::vector<int64_t> per;
+  for (int64_t i = 0; i < r.n_pairs; ++i) {
+    const int64_t L = std::max<int64_t>(std::max(0, r.pattern_lengths[i]), std::max(0, r.text_lengths[i]));
+    if (L <= 127) continue;
+    const double sp = WFA_GPU_SERVER_EDIT_RATE * (double)L * cost;
+    const double cells = (sp / es + 1.0) * (sp / es + 1.0);
+    per.push_back((int64_t)(3.0 * (L < 32000 ? 2 : 4) * cells + 16.0 * (sp + 1)));
+  }
+  if ((int64_t)per.size() > kConcurrentTeams) {
+    std::nth_element(per.begin(), per.begin() + kConcurrentTeams, per.end(), std::greater<int64_t>());
+    per.resize(kConcurrentTeams);
+  }
+  int64_t sum = 0;
+  for (int64_t v : per) sum += v;
+  return sum;
 }
 
 // Host-side checks that make gathering a request's pairs safe; a request
@@ -109,10 +187,12 @@ int run_alone(wfa_gpu_ctx* ctx, const wfa_gpu_request& r) {
                              r.out_cigars, r.cigar_capacity_words, r.out_cigar_offsets);
 }
 
-// Align several well-formed requests of the same parameters as one batch.
-// Returns false when the merged call could not give every request the
-// result it gets alone (staging out of memory, a failed call); the caller
-// then runs them one by one.
+// Align several well-formed requests of the same parameters as one batch on
+// the device: their pairs gathered back to back into page-locked staging,
+// copied to the slot's device buffers, aligned by one device-pointer call,
+// and the outputs copied back and scattered.  Returns false when the merged
+// call could not give every request the result it gets alone (out of
+// memory, a failed call); the caller then runs them one by one.
 bool run_merged(Slot& sl, std::vector<std::shared_ptr<Request>>& run) {
   const wfa_gpu_request& r0 = run[0]->r;
   const bool so = r0.flags & WFA_GPU_SCORE_ONLY;
@@ -125,8 +205,12 @@ bool run_merged(Slot& sl, std::vector<std::shared_ptr<Request>>& run) {
   }
   if (n > INT32_MAX) return false;
   if (!sl.pat.ensure(std::max<int64_t>(pb, 1)) || !sl.txt.ensure(std::max<int64_t>(tb, 1)) ||
-      !sl.poff.ensure(n + 1) || !sl.toff.ensure(n + 1) || !sl.plen.ensure(n + 1) || !sl.tlen.ensure(n + 1) ||
-      !sl.score.ensure(n + 1) || !sl.status.ensure(n + 1) || (!so && !sl.off.ensure(n + 1)))
+      !sl.plen.ensure(n + 1) || !sl.tlen.ensure(n + 1) || !sl.score.ensure(n + 1) || !sl.status.ensure(n + 1) ||
+      (!so && !sl.off.ensure(n + 1)))
+    return false;
+  if (!sl.dpat.ensure(std::max<int64_t>(pb, 1) + 16) || !sl.dtxt.ensure(std::max<int64_t>(tb, 1) + 16) ||
+      !sl.dplen.ensure(n + 1) || !sl.dtlen.ensure(n + 1) || !sl.dscore.ensure(n + 1) ||
+      !sl.dstatus.ensure(n + 1) || (!so && (!sl.doff.ensure(n + 1) || !sl.dcig.ensure(std::max<int64_t>(cap, 1)))))
     return false;
   // gather: sequences back to back in request order, then pair order
   int64_t k = 0, pc = 0, tc = 0;
@@ -141,20 +225,40 @@ bool run_merged(Slot& sl, std::vector<std::shared_ptr<Request>>& run) {
       tr += lt;
       std::memcpy(sl.pat.p + pc, r.patterns + op, (size_t)lp);
       std::memcpy(sl.txt.p + tc, r.texts + ot, (size_t)lt);
-      sl.poff.p[k] = pc;
-      sl.toff.p[k] = tc;
       sl.plen.p[k] = lp;
       sl.tlen.p[k] = lt;
       pc += lp;
       tc += lt;
     }
   }
-  if (!so) wfa::set_cigar_sink(sl.ctx, cigar_sink, &sl);
-  const int rc = wfa_gpu_align_batch(sl.ctx, n, sl.pat.p, sl.poff.p, sl.plen.p, sl.txt.p, sl.toff.p, sl.tlen.p,
-                                     r0.pen, r0.max_score, r0.flags, sl.score.p, sl.status.p,
-                                     so ? nullptr : sl.cig.p, so ? 0 : cap, so ? nullptr : sl.off.p);
-  wfa::set_cigar_sink(sl.ctx, nullptr, nullptr);
+  cudaStream_t st = sl.stream;
+  auto h2d = [&](void* d, const void* h, size_t b) {
+    return !b || cudaMemcpyAsync(d, h, b, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  };
+  auto d2h = [&](void* h, const void* d, size_t b) {
+    return !b || cudaMemcpyAsync(h, d, b, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+  };
+  if (!h2d(sl.dpat.p, sl.pat.p, (size_t)pb) || !h2d(sl.dtxt.p, sl.txt.p, (size_t)tb) ||
+      !h2d(sl.dplen.p, sl.plen.p, (size_t)n * sizeof(int32_t)) ||
+      !h2d(sl.dtlen.p, sl.tlen.p, (size_t)n * sizeof(int32_t)))
+    return false;
+  // the call runs on the same stream, after the copies
+  const int rc = wfa_gpu_align_batch(sl.ctx, n, sl.dpat.p, nullptr, sl.dplen.p, sl.dtxt.p, nullptr, sl.dtlen.p,
+                                     r0.pen, r0.max_score, r0.flags | WFA_GPU_DEVICE_PTRS, sl.dscore.p,
+                                     sl.dstatus.p, so ? nullptr : sl.dcig.p, so ? 0 : cap,
+                                     so ? nullptr : sl.doff.p);
   if (rc != WFA_GPU_OK) return false;
+  if (!d2h(sl.score.p, sl.dscore.p, (size_t)n * sizeof(int32_t)) ||
+      !d2h(sl.status.p, sl.dstatus.p, (size_t)n * sizeof(int8_t)) ||
+      (!so && !d2h(sl.off.p, sl.doff.p, (size_t)(n + 1) * sizeof(int64_t))) ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return false;
+  if (!so) {
+    const int64_t words = sl.off.p[n];
+    if (words > cap || !sl.cig.ensure((size_t)std::max<int64_t>(words, 1)) ||
+        !d2h(sl.cig.p, sl.dcig.p, (size_t)words * sizeof(uint32_t)) || cudaStreamSynchronize(st) != cudaSuccess)
+      return false;
+  }
   // scatter: each request gets its slice, CIGAR offsets rebased to 0
   k = 0;
   for (auto& q : run) {
@@ -179,6 +283,45 @@ bool run_merged(Slot& sl, std::vector<std::shared_ptr<Request>>& run) {
   return true;
 }
 
+// First-fit allocator of arena slices (256-byte aligned), free ranges
+// coalesced on release.
+struct ArenaAlloc {
+  std::map<int64_t, int64_t> free_;  // offset -> size
+  int64_t total = 0;
+  void init(int64_t bytes) {
+    total = bytes & ~255ll;
+    free_.clear();
+    free_[0] = total;
+  }
+  int64_t take(int64_t bytes) {  // offset, or -1
+    bytes = (bytes + 255) & ~255ll;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < bytes) continue;
+      const int64_t off = it->first, rest = it->second - bytes;
+      free_.erase(it);
+      if (rest) free_[off + bytes] = rest;
+      return off;
+    }
+    return -1;
+  }
+  void give(int64_t off, int64_t bytes) {
+    bytes = (bytes + 255) & ~255ll;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+};
+
 }  // namespace
 
 struct wfa_gpu_server {
@@ -191,44 +334,73 @@ struct wfa_gpu_server {
   std::deque<std::shared_ptr<Request>> queue;
   std::unordered_map<int64_t, std::shared_ptr<Request>> live;
   int64_t next_id = 0;
-  int64_t budget = 0;     // admission budget, bytes
-  int64_t in_flight = 0;  // estimated bytes of the admitted requests
+  unsigned char* arena = nullptr;  // the scratch arena the calls share
+  ArenaAlloc alloc;
   int running = 0;
   bool stop = false;
 
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+
+  // The arena slice a call of estimated need runs on: the need, at least
+  // kMinSlice and at most half the arena (the arena kernels fit a smaller
+  // slice than the estimate by running fewer pairs at once, with larger
+  // slices each), or the whole arena for a rerun.
+  int64_t slice_for(int64_t need, bool whole) const {
+    if (whole) return alloc.total;
+    const int64_t mb = (int64_t)1 << 20;
+    const int64_t cap = std::max<int64_t>(kMinSlice, (alloc.total / 2) & ~(mb - 1));
+    const int64_t s = (std::max<int64_t>(need, kMinSlice) + mb - 1) & ~(mb - 1);
+    return std::min<int64_t>(std::min<int64_t>(s, cap), alloc.total);
+  }
+
+  // Under the lock: the next call to run -- the oldest request whose slice
+  // fits the free arena (a later one only while the oldest has waited less
+  // than kMaxWaitS), with the same-parameter requests queued right behind
+  // it when their slice fits too -- taken off the queue; false if none.
+  bool pick(std::vector<std::shared_ptr<Request>>* run, int64_t* slice, int64_t* off) {
+    if (queue.empty()) return false;
+    const bool may_pass = now() - queue.front()->st.submit_s < kMaxWaitS;
+    const size_t limit = may_pass ? std::min<size_t>(queue.size(), 64) : 1;
+    for (size_t i = 0; i < limit; ++i) {
+      const Request& q = *queue[i];
+      // the group: q and the requests right behind it that share its call
+      size_t j = i + 1;
+      int64_t pairs = q.r.n_pairs;
+      while (q.mergeable && !q.whole && j < queue.size()) {
+        const Request& t = *queue[j];
+        if (!t.mergeable || t.whole || !same_call(t.r, q.r) || pairs + t.r.n_pairs > WFA_GPU_SERVER_MERGE_PAIRS)
+          break;
+        pairs += t.r.n_pairs;
+        ++j;
+      }
+      for (size_t end : {j, i + 1}) {  // the group, else q alone
+        int64_t nd = 0;
+        for (size_t t = i; t < end; ++t) nd += queue[t]->need_arena;
+        const int64_t sl = slice_for(nd, q.whole);
+        const int64_t o = alloc.take(sl);
+        if (o < 0) continue;
+        run->assign(queue.begin() + (long)i, queue.begin() + (long)end);
+        queue.erase(queue.begin() + (long)i, queue.begin() + (long)end);
+        *slice = sl;
+        *off = o;
+        return true;
+      }
+    }
+    return false;
+  }
 
   void worker(int w) {
     Slot& sl = *slots[w];
     cudaSetDevice(device);
     for (;;) {
       std::vector<std::shared_ptr<Request>> run;
-      int64_t need = 0;
+      int64_t slice = 0, off = -1;
       {
         std::unique_lock<std::mutex> lk(mu);
-        // FIFO: the oldest request goes first, when it fits the budget (or
-        // nothing else is running, so that any request can make progress)
-        cv_work.wait(lk, [&] {
-          return stop || (!queue.empty() && (running == 0 || in_flight + queue.front()->need <= budget));
-        });
+        // a request waiting for arena space is looked at again when a call
+        // ends or when its passing time runs out
+        while (!stop && !pick(&run, &slice, &off)) cv_work.wait_for(lk, std::chrono::milliseconds(5));
         if (stop) return;
-        run.push_back(queue.front());
-        queue.pop_front();
-        need = run[0]->need;
-        int64_t pairs = run[0]->r.n_pairs;
-        // the requests queued right behind it join when they share its
-        // parameters and fit the merge limit and the budget
-        while (run[0]->mergeable && !queue.empty()) {
-          const Request& q = *queue.front();
-          if (!q.mergeable || !same_call(q.r, run[0]->r) || pairs + q.r.n_pairs > WFA_GPU_SERVER_MERGE_PAIRS ||
-              in_flight + need + q.need > budget)
-            break;
-          pairs += q.r.n_pairs;
-          need += q.need;
-          run.push_back(queue.front());
-          queue.pop_front();
-        }
-        in_flight += need;
         ++running;
         const double t = now();
         for (auto& q : run) {
@@ -237,16 +409,25 @@ struct wfa_gpu_server {
         }
       }
       cv_work.notify_all();  // another slot may admit the next request
-      if (run.size() == 1 || !run_merged(sl, run))
+      wfa::set_arena(sl.ctx, arena + off, (size_t)slice);
+      if (!(run[0]->mergeable && run_merged(sl, run)))
         for (auto& q : run) q->st.result = run_alone(sl.ctx, q->r);
+      wfa::set_arena(sl.ctx, nullptr, 0);
       {
         std::lock_guard<std::mutex> lk(mu);
+        alloc.give(off, slice);
         const double t = now();
-        for (auto& q : run) {
+        for (auto it = run.rbegin(); it != run.rend(); ++it) {
+          auto& q = *it;
+          if (q->st.result == WFA_GPU_ENOMEM && slice < alloc.total && !q->whole) {
+            // a pair outgrew its slice: once more on the whole arena, first
+            q->whole = true;
+            queue.push_front(q);
+            continue;
+          }
           q->st.end_s = t;
           q->done = true;
         }
-        in_flight -= need;
         --running;
       }
       cv_done.notify_all();
@@ -263,8 +444,9 @@ int64_t wfa_gpu_request_bytes(const wfa_gpu_request* r) {
   for (int64_t i = 0; i < r->n_pairs; ++i) seq += (int64_t)std::max(0, r->pattern_lengths[i]) +
                                                  std::max(0, r->text_lengths[i]);
   // ASCII staging, lengths/offsets, outputs, per-pair work buffers and CIGAR
-  // slots (about 150 bytes a pair), the caller's CIGAR capacity
-  return seq + 150 * r->n_pairs + 4 * std::max<int64_t>(0, r->cigar_capacity_words);
+  // slots (about 150 bytes a pair), the caller's CIGAR capacity, and the
+  // wavefronts in the scratch arena
+  return seq + 150 * r->n_pairs + 4 * std::max<int64_t>(0, r->cigar_capacity_words) + wavefront_bytes(*r);
 }
 
 int wfa_gpu_server_create(wfa_gpu_server** out, int device, int workers, size_t budget) {
@@ -272,22 +454,39 @@ int wfa_gpu_server_create(wfa_gpu_server** out, int device, int workers, size_t 
   *out = nullptr;
   if (device < 0 || workers < 1 || workers > 64) return WFA_GPU_EINVAL;
   if (!budget) budget = (size_t)8 << 30;
+  if (budget < (size_t)kMinSlice) return WFA_GPU_EINVAL;
   wfa_gpu_server* s = new (std::nothrow) wfa_gpu_server();
   if (!s) return WFA_GPU_ENOMEM;
   s->device = device;
   s->t0 = Clock::now();
-  s->budget = (int64_t)(budget / 2);
-  const size_t arena = std::max<size_t>((budget / 2) / (size_t)workers, (size_t)64 << 20);
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete s;
+    return WFA_GPU_ECUDA;
+  }
+  if (cudaMalloc(reinterpret_cast<void**>(&s->arena), budget) != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    return WFA_GPU_ENOMEM;
+  }
+  s->alloc.init((int64_t)budget);
   for (int w = 0; w < workers; ++w) {
     std::unique_ptr<Slot> sl(new (std::nothrow) Slot());
     if (!sl) {
       wfa_gpu_server_destroy(s);
       return WFA_GPU_ENOMEM;
     }
-    const int rc = wfa_gpu_create(&sl->ctx, device, arena);
+    // each call borrows a slice of the shared arena; the context's own is
+    // a minimal one
+    const int rc = wfa_gpu_create(&sl->ctx, device, (size_t)4 << 20);
     if (rc != WFA_GPU_OK) {
       wfa_gpu_server_destroy(s);
       return rc;
+    }
+    if (cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        wfa_gpu_set_stream(sl->ctx, sl->stream) != WFA_GPU_OK) {
+      s->slots.push_back(std::move(sl));
+      wfa_gpu_server_destroy(s);
+      return WFA_GPU_ECUDA;
     }
     s->slots.push_back(std::move(sl));
   }
@@ -304,11 +503,10 @@ int wfa_gpu_server_create(wfa_gpu_server** out, int device, int workers, size_t 
 int64_t wfa_gpu_server_submit(wfa_gpu_server* s, const wfa_gpu_request* r) {
   if (!s || !r) return WFA_GPU_EINVAL;
   if (r->flags & ~(uint32_t)(WFA_GPU_SCORE_ONLY | WFA_GPU_PLAIN | WFA_GPU_ARENA_ONLY)) return WFA_GPU_EINVAL;
-  const int64_t need = wfa_gpu_request_bytes(r);
-  if (need < 0) return WFA_GPU_EINVAL;
+  if (wfa_gpu_request_bytes(r) < 0) return WFA_GPU_EINVAL;
   auto req = std::make_shared<Request>();
   req->r = *r;
-  req->need = need;
+  req->need_arena = wavefront_bytes(*r);
   req->mergeable = well_formed(*r, &req->pat_bytes, &req->txt_bytes);
   {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -357,8 +555,11 @@ void wfa_gpu_server_destroy(wfa_gpu_server* s) {
   for (auto& sl : s->slots) {
     if (sl->ctx) wfa_gpu_destroy(sl->ctx);
     sl->ctx = nullptr;
+    if (sl->stream) cudaStreamDestroy(sl->stream);
+    sl->stream = nullptr;
   }
-  s->slots.clear();  // page-locked staging freed here
+  s->slots.clear();  // page-locked staging and device buffers freed here
+  if (s->arena) cudaFree(s->arena);
   delete s;
 }
 

@@ -123,14 +123,19 @@ def test_product_never_imports_the_oracle():
 
 def test_request_bytes_is_host_only(pkg):
     """The admission measure of the serving API: sequence bytes plus a fixed
-    per-pair share and the caller's CIGAR capacity; no device needed."""
+    per-pair share, the caller's CIGAR capacity and the arena the wavefronts
+    of pairs longer than 127 bases take; no device needed."""
     import numpy as np
 
     plen = np.array([100, 0, 250], np.int32)
     tlen = np.array([90, 10, 300], np.int32)
     req = pkg.Request(3, None, None, plen.ctypes.data, None, None, tlen.ctypes.data, pkg.Penalties(4, 6, 2), 0, 0,
                       None, None, None, 1000, None)
-    assert pkg.wfa_gpu_request_bytes(req) == int(plen.sum() + tlen.sum()) + 150 * 3 + 4 * 1000
+    # the third pair (300 bases) only: g = 2, costliest edit max(4, 6 + 2) / 2
+    # = 4, e' = 1, s' = 0.10 x 300 x 4 = 120, (s'/e' + 1)^2 cells of 3
+    # two-byte offsets, 16 bytes of metadata per score
+    wavefront = int(3 * 2 * 121 ** 2 + 16 * 121)
+    assert pkg.wfa_gpu_request_bytes(req) == int(plen.sum() + tlen.sum()) + 150 * 3 + 4 * 1000 + wavefront
     bad = pkg.Request(-1, None, None, None, None, None, None, pkg.Penalties(4, 6, 2), 0, 0, None, None, None, 0, None)
     assert pkg.wfa_gpu_request_bytes(bad) == -1
     assert pkg.load().wfa_gpu_server_create(None, 0, 4, 0) == pkg.WFA_GPU_EINVAL

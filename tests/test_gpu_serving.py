@@ -72,16 +72,19 @@ def test_score_only_and_plain_requests(pkg):
 
 
 def test_tiny_budget_admits_one_at_a_time(pkg):
-    """With a budget smaller than any request, a request is admitted only
-    when nothing else runs: no two requests overlap, results unchanged."""
+    """With an arena no larger than one call's smallest slice (64 MiB), a
+    call starts only when nothing else runs: no two calls overlap, results
+    unchanged."""
     reqs = _requests(300, 8)
     with pkg.Aligner(0, 2 << 30) as al:
         alone = [al.align(b, (4, 6, 2)) for b in reqs]
-    with pkg.Server(0, workers=4, memory_budget_bytes=4096) as srv:
+    with pkg.Server(0, workers=4, memory_budget_bytes=64 << 20) as srv:
         ids = [srv.submit(b, (4, 6, 2), cigar_capacity=int(b.pattern_lengths.sum() + b.text_lengths.sum()) + 1)
                for b in reqs]
         outs = [srv.wait(i) for i in ids]
-    assert _overlaps([st for _, st in outs]) == 0
+    # requests merged into one call share its interval: compare the calls
+    calls = {(st.worker, st.start_s): st for _, st in outs}
+    assert _overlaps(list(calls.values())) == 0
     for (got, _), want in zip(outs, alone):
         for x, y in zip(got, want):
             assert np.array_equal(x, y)
@@ -171,3 +174,40 @@ def test_merge_boundaries_and_errors(pkg):
         assert np.array_equal(got[3], want[3])  # offsets, also when the capacity was short
         if code == pkg.WFA_GPU_OK:
             assert np.array_equal(got[2], want[2])
+
+
+def test_large_need_waits_while_small_ones_run(pkg, oracle_mod):
+    """A request whose estimated wavefront need does not fit the free arena
+    waits while requests queued after it, with small needs, pass it and
+    run.  Arena of 192 MiB: small calls take 64 MiB slices; the large request
+    (60 pairs of 5 kbp: above 1 GiB at the 10% edit-rate bound) a slice of
+    half the arena, 96 MiB, which the first two small calls leave no room
+    for.  Every result equals the request aligned alone."""
+    from paper_2204_02085_gb300 import synth
+
+    small = [synth.uniform_reads(3000, 100, 3, seed=600 + j) for j in range(5)]
+    big = synth.long_reads(60, 5000, 0.01, 0.02, seed=610)
+    # distinct max_score values keep the first two small requests and the
+    # large one in calls of their own (merging joins only equal parameters)
+    bounds = [0, 100000, 0, 0, 0]
+    with pkg.Aligner(0, 2 << 30) as al:
+        alone_small = [al.align(b, (4, 6, 2), max_score=ms) for b, ms in zip(small, bounds)]
+        alone_big = al.align(big, (4, 6, 2), max_score=1 << 20)
+    with pkg.Server(0, workers=4, memory_budget_bytes=192 << 20) as srv:
+        ids = [srv.submit(small[j], (4, 6, 2), max_score=bounds[j], cigar_capacity=_cap(small[j])) for j in (0, 1)]
+        big_id = srv.submit(big, (4, 6, 2), max_score=1 << 20, cigar_capacity=_cap(big))
+        ids += [srv.submit(small[j], (4, 6, 2), max_score=bounds[j], cigar_capacity=_cap(small[j]))
+                for j in (2, 3, 4)]
+        outs = [srv.wait(i) for i in ids]
+        big_out, big_st = srv.wait(big_id)
+    stats = [st for _, st in outs]
+    assert big_st.result == pkg.WFA_GPU_OK and all(st.result == pkg.WFA_GPU_OK for st in stats)
+    # requests submitted after the large one started before it
+    assert any(st.start_s < big_st.start_s for st in stats[2:])
+    for (got, _), want in zip(outs, alone_small):
+        for x, y in zip(got, want):
+            assert np.array_equal(x, y)
+    for x, y in zip(big_out, alone_big):
+        assert np.array_equal(x, y)
+    o = oracle_mod.wfa_batch(big, (4, 6, 2), nthreads=16)
+    assert np.array_equal(big_out[0], o[0]) and np.array_equal(big_out[2], o[2])
