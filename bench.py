@@ -95,6 +95,8 @@ def parse():
     ap.add_argument("--short-variant", type=int, default=None,
                     help="force one short-read kernel variant (tuning; default: the library's autotuner)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-pointer (end-to-end) measurement")
+    ap.add_argument("--no-numa-bind", action="store_true",
+                    help="do not restrict the process to the GPU's local CPUs before allocating page-locked buffers")
     ap.add_argument("--no-samples", action="store_true",
                     help="skip the bounded mixed-length and serving samples of the default run")
     ap.add_argument("--mixed-pairs", type=int, default=200_000, help="pairs of the mixed-length sample")
@@ -678,7 +680,7 @@ def main():
 
     import paper_2204_02085_gb300 as pkg
     from paper_2204_02085_gb300 import build as gpu_build
-    from paper_2204_02085_gb300 import sharding
+    from paper_2204_02085_gb300 import hostnuma, sharding
 
     rank, world, local = sharding.dist_env()
     if world > 1:
@@ -686,6 +688,9 @@ def main():
         dist.init_process_group("nccl", init_method="env://")
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
+    # page-locked buffers land on the node of the allocating thread's CPU:
+    # run on the GPU's own node before allocating any
+    numa = {"bound": False, "skipped": True} if args.no_numa_bind else hostnuma.bind_to_gpu(dev.index)
     if rank == 0 or not os.path.exists(pkg.LIB_PATH):
         gpu_build.build()
     sharding.barrier()
@@ -831,12 +836,21 @@ def main():
     for _ in range(max(1, args.warmup) if e2e_steps else 0):
         host_step()
     h2d = d2h = 0
+    # clocks during the end-to-end region too: a slow process shows whether
+    # the GPU's clock or the link was the cause
+    e2e_sampler = ClockSampler(dev.index) if (rank == 0 and e2e_steps) else None
+    if e2e_sampler:
+        e2e_sampler.start()
     sharding.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         h2d, d2h = host_step()
     e2e_s = sharding.max_over_ranks(time.perf_counter() - t0)
+    e2e_clocks = e2e_sampler.stop() if e2e_sampler else None
     e2e_value = pairs_per_step * world * e2e_steps / e2e_s if e2e_steps else None
+    if pinned:
+        numa["pinned_pages_per_node"] = {str(k): v for k, v in sorted(hostnuma.placement(
+            [a.ctypes.data for p in pinned for a in p.values()]).items())}
     if e2e_steps:
         for p, (s, st, off) in zip(pinned, outs):
             assert np.array_equal(p["s"], s) and np.array_equal(p["off"], off), "host and device calls disagree"
@@ -914,6 +928,8 @@ def main():
                 "steps": e2e_steps,
                 "inputs": "page-locked host buffers, sequences back to back (no offset arrays): streamed "
                           "chunk by chunk into a device ring on a copy stream; outputs copied back",
+                "host_numa": numa,
+                "clocks": e2e_clocks,
                 "phase_ms_per_call": {k: round(float(np.mean([t[k] for t in e2e_phases[-2 * e2e_steps:]])), 3)
                                       for k in ("h2d_ms", "align_ms", "general_ms", "cigar_ms", "d2h_ms",
                                                 "total_ms")} if e2e_phases else None},
