@@ -138,6 +138,11 @@ struct wfa_gpu_ctx {
   int lane_variants[4] = {15, 16, 17, 18};
   int lane_ct_variants[4] = {19, 20, 17, 18};
   bool lane_on = true;      // WFA_GPU_LANE=0 turns them off (comparisons)
+  // the lane kernel's pairs sorted by estimated score in groups (default
+  // path; WFA_GPU_LANE_ORDER=0: call order), and the ordering's buffers
+  bool lane_order = true;
+  DevBuf<uint32_t> lane_words;
+  DevBuf<int2> lane_slots;
   int variant_forced = -1;  // tuning override (WFA_GPU_SHORT_VARIANT)
   int last_variant = -1;
   wfa::Ctrl* ctrl = nullptr;    // device
@@ -515,6 +520,26 @@ int run_retries(wfa_gpu_ctx* c, Call& k, wfa::AlignArgs& a) {
 
 constexpr int64_t kTuneSample = 4096;
 
+// The lane ordering's buffers for calls of up to n pairs: allocated here
+// (eager calls), or only taken when already large enough (captured work,
+// which must not allocate); left null when the context keeps call order.
+cudaError_t lane_order_args(wfa_gpu_ctx* c, wfa::AlignArgs& a, int64_t n, bool may_alloc) {
+  a.lane_words = nullptr;
+  a.lane_slots = nullptr;
+  if (!c->lane_order || n <= 0) return cudaSuccess;
+  const int64_t slots = (n + wfa::kLaneGroup - 1) / wfa::kLaneGroup * wfa::kLaneGroup;
+  const size_t words = (size_t)slots * 2 * wfa::kLaneNW;
+  if (may_alloc) {
+    cudaError_t e;
+    if ((e = c->lane_words.ensure(words)) || (e = c->lane_slots.ensure((size_t)slots))) return e;
+  } else if (c->lane_words.cap < words || c->lane_slots.cap < (size_t)slots) {
+    return cudaSuccess;
+  }
+  a.lane_words = c->lane_words.p;
+  a.lane_slots = c->lane_slots.p;
+  return cudaSuccess;
+}
+
 // Pick the short-kernel variant for a batch of sequences <= 127 bases: the
 // large-store variant scores the first kTuneSample pairs (score only); the
 // smallest store that holds nearly all of them (more pairs resident per SM,
@@ -568,7 +593,7 @@ int autotune_short(wfa_gpu_ctx* c, Call& k, const wfa::AlignArgs& a_in, int64_t 
   if (!k.ok(cudaMemsetAsync(a.ctrl, 0, sizeof(wfa::Ctrl), st))) return -1;
   // pairs the sample run defers keep score -1
   if (!k.ok(cudaMemsetAsync(a.score, 0xff, m * sizeof(int32_t), st))) return -1;
-  if (!k.launched(wfa::launch_short(a, c->plan.v[big], st))) return -1;
+  if (!k.launched(wfa::launch_short(a, c->plan.v[big], st), wfa::short_launches(a, c->plan.v[big]))) return -1;
   if (!k.ok(d2h(c->h_tune, c->tune_score.p, m * sizeof(int32_t), st)) || !k.ok(cudaStreamSynchronize(st))) return -1;
   int64_t fit[4] = {0, 0, 0, 0}, tot = 0;
   for (int64_t i = 0; i < m; ++i) {
@@ -651,6 +676,7 @@ int wfa_gpu_create(wfa_gpu_ctx** out, int device, size_t scratch_bytes) {
       break;
     }
     if (const char* ev = std::getenv("WFA_GPU_LANE")) c->lane_on = std::atoi(ev) != 0;
+    if (const char* ev = std::getenv("WFA_GPU_LANE_ORDER")) c->lane_order = std::atoi(ev) != 0;
     // tuning override: WFA_GPU_SHORT_VARIANT=<index> for the <= 127-base case
     if (const char* ev = std::getenv("WFA_GPU_SHORT_VARIANT")) {
       const int v = std::atoi(ev);
@@ -825,7 +851,8 @@ int align_pipelined(wfa_gpu_ctx* ctx, Call& k, const wfa::AlignArgs& a, int64_t 
         }
         ctx->last_variant = vi;
       }
-      if (!k.launched(wfa::launch_short(ac, ctx->plan.v[vi], st))) return fail_cuda(k);
+      if (!k.launched(wfa::launch_short(ac, ctx->plan.v[vi], st), wfa::short_launches(ac, ctx->plan.v[vi])))
+        return fail_cuda(k);
     }
     // later chunks' bases move while this one computes
     if (sin && c + kRing - 1 < nchunks && !copy_in(c + kRing - 1)) return fail_cuda(k);
@@ -1001,6 +1028,7 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
                        lens_mapped ? text_lengths : nullptr};
     const bool streamed = host_seqs && !pattern_offsets && !text_offsets && mapped_range(patterns, pe) &&
                           mapped_range(texts, te);
+    if (mode == 0 && (e = lane_order_args(ctx, a, std::min(n, kPipeChunk), true))) return map_alloc(e);
     rc = align_pipelined(ctx, k, a, n, mode, pen, out_scores, out_status, out_cigars, cap, out_cigar_offsets,
                          streamed ? &sin : nullptr);
     if (rc < 0 && rc != WFA_GPU_ECIGAR_CAPACITY) return rc;
@@ -1020,13 +1048,15 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
   if (arena_only) {
     if (!k.launched(wfa::launch_route_all(a, st))) return fail_cuda(k);
   } else {
+    if (!plain && (e = lane_order_args(ctx, a, n, true))) return map_alloc(e);
     int vi = fixed_variant(ctx, a, ctx->h_ctrl->max_len);
     if (!plain && ctx->h_ctrl->max_len <= 127) {
       vi = autotune_short(ctx, k, a, n);
       if (vi < 0) return fail_cuda(k);
     }
     ctx->last_variant = vi;
-    if (!k.launched(wfa::launch_short(a, ctx->plan.v[vi], st))) return fail_cuda(k);
+    if (!k.launched(wfa::launch_short(a, ctx->plan.v[vi], st), wfa::short_launches(a, ctx->plan.v[vi])))
+      return fail_cuda(k);
   }
   k.rec(2);
   if (!ctrl_to_host(k, st) || !k.ok(cudaStreamSynchronize(st))) return fail_cuda(k);
@@ -1177,7 +1207,10 @@ int enqueue_device_work(wfa_gpu_ctx* c, Call& k, int64_t n, const char* pat, con
   wfa::AlignArgs a = device_args(c, n, pat, d_poff, plen, txt, d_toff, tlen, pen, max_score, score_only,
                                  out_scores, out_status);
   if (c->last_variant < 0) return WFA_GPU_ECUDA;
-  if (!k.launched(wfa::launch_short(a, c->plan.v[c->last_variant], st))) return WFA_GPU_ECUDA;
+  if (lane_order_args(c, a, n, false) != cudaSuccess) return WFA_GPU_ECUDA;
+  if (!k.launched(wfa::launch_short(a, c->plan.v[c->last_variant], st),
+                  wfa::short_launches(a, c->plan.v[c->last_variant])))
+    return WFA_GPU_ECUDA;
   if (!k.ok(cudaEventRecordWithFlags(c->ev[2], st, cudaEventRecordExternal))) return WFA_GPU_ECUDA;
   const long arena = (long)c->arena_bytes;
   unsigned char* ab = reinterpret_cast<unsigned char*>(c->arena);
@@ -1230,7 +1263,7 @@ int graph_key(wfa_gpu_ctx* c, uint64_t* key, int64_t n, const void* const* ptrs,
   key[l++] = (uint64_t)(uintptr_t)c->stream;
   const void* bufs[] = {c->ctrl, c->poff.p, c->toff.p, c->scan_tmp.p, c->nruns.p, c->run_src.p, c->runs.p,
                         c->pool.p, c->defer.p, c->defer_long.p, c->overflow.p, c->arena,
-                        c->sorted.p, c->sorted_long.p, c->sort_aux.p};
+                        c->sorted.p, c->sorted_long.p, c->sort_aux.p, c->lane_words.p, c->lane_slots.p};
   for (const void* b : bufs) key[l++] = (uint64_t)(uintptr_t)b;
   key[l++] = c->pool.cap;
   key[l++] = ((uint64_t)(uint32_t)c->teams_medium << 32) | (uint32_t)c->teams_long;
@@ -1250,7 +1283,7 @@ int align_graph(wfa_gpu_ctx* ctx, int64_t n, const char* pat, const int64_t* pof
   if (!ctx || !(flags & WFA_GPU_DEVICE_PTRS)) return WFA_GPU_EINVAL;
   const bool score_only = flags & WFA_GPU_SCORE_ONLY;
   const void* ptrs[] = {pat, poff, plen, txt, toff, tlen, out_scores, out_status, out_cigars, out_off};
-  uint64_t key[40];
+  uint64_t key[40];  // 37 entries
   int kl = graph_key(ctx, key, n, ptrs, 10, pen, max_score, flags, cap);
   wfa_gpu_ctx::Graph* hit = nullptr;
   for (auto& gr : ctx->graphs)
@@ -1495,6 +1528,7 @@ void wfa_gpu_destroy(wfa_gpu_ctx* c) {
   if (c->in_stream) cudaStreamSynchronize(c->in_stream);
   c->h_score.release(); c->h_status.release(); c->h_off.release(); c->h_cig.release();
   c->ring.release(); c->h_bounds.release();
+  c->lane_words.release(); c->lane_slots.release();
   if (c->own_arena) cudaFree(c->own_arena);
   if (c->ctrl) cudaFree(c->ctrl);
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);

@@ -43,6 +43,14 @@ __global__ void __launch_bounds__(32 * WPB) lane_kernel(const AlignArgs a, const
   lane_body<LMAX, CELLS, RW, SPAN, Fwd>(a, g, smem);
 }
 
+// The lane kernel's ordering pass: a block per group of kLaneGroup pairs
+// (lane_path.cuh).
+template <int LMAX>
+__global__ void __launch_bounds__(kLaneGroup) lane_order_kernel(const AlignArgs a, int est_cap) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  lane_order_body<LMAX>(a, est_cap, smem);
+}
+
 // ----------------------------------------------------------- arena kernels
 
 template <int WPP>
@@ -419,6 +427,20 @@ constexpr int kLaneSpan1 = 4096;
 
 // A lane-per-pair variant; CT_X, CT_OE, CT_E: the scaled penalties whose
 // geometry is compiled in (0: any penalties, geometry from the table).
+using OrderShm = LaneOrderShm<127>;
+
+cudaError_t plan_order(int device, int* grid) {
+  auto k = lane_order_kernel<127>;
+  const size_t smem = sizeof(OrderShm);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kLaneGroup, smem);
+  if (e != cudaSuccess) return e;
+  *grid = sm_count(device) * (per_sm < 1 ? 1 : per_sm);
+  return cudaSuccess;
+}
+
 template <int LMAX, int CELLS, int RW, int WPB, int CT_X = 0, int CT_OE = 0, int CT_E = 0, int SPAN = kLaneSpan>
 cudaError_t plan_lane(int device, ShortVariant* v, const char* name) {
   using C = LaneCfg<LMAX, CELLS, RW, SPAN>;
@@ -449,7 +471,7 @@ cudaError_t plan_lane(int device, ShortVariant* v, const char* name) {
   v->ct_x = CT_X;
   v->ct_oe = CT_OE;
   v->ct_e = CT_E;
-  return cudaSuccess;
+  return plan_order(device, &v->order_grid);
 }
 
 }  // namespace
@@ -515,15 +537,37 @@ cudaError_t short_plan(int device, ShortPlan* plan) {
                               (int)arena_smem);
 }
 
+// Ordered input only for sequences in device memory (the ordering pass
+// reads each pair's bytes with its own loads, which page-locked host memory
+// read in place over the link would turn into many small transfers).
+static bool lane_ordered(const AlignArgs& a, const ShortVariant& v) {
+  return a.n > 0 && v.kind == 1 && a.lane_slots && a.lane_words && !a.host_seqs;
+}
+
+int short_launches(const AlignArgs& a, const ShortVariant& v) { return lane_ordered(a, v) ? 2 : 1; }
+
 cudaError_t launch_short(const AlignArgs& a, const ShortVariant& v, cudaStream_t st) {
   if (a.n <= 0) return cudaSuccess;
   int grid = v.grid;
-  const int64_t need = (a.n + v.pairs_per_block - 1) / v.pairs_per_block;
-  if (need < grid) grid = (int)need;
   AlignArgs copy = a;
+  const bool ordered = lane_ordered(a, v);
+  if (!ordered) copy.lane_words = nullptr, copy.lane_slots = nullptr;
+  const int64_t groups = (a.n + kLaneGroup - 1) / kLaneGroup;
+  const int64_t units = ordered ? groups * kLaneGroup : a.n;  // pairs, or slots of whole groups
+  const int64_t need = (units + v.pairs_per_block - 1) / v.pairs_per_block;
+  if (need < grid) grid = (int)need;
   if (v.kind == 1) {
     LaneGeo g;
     lane_geometry(a, v.cells, v.rw, &g);
+    if (ordered) {
+      // estimates above the store's last score all mean "deferred": the
+      // greedy walk stops there
+      const int cap = g.s_store < 0 ? 1 : std::min(g.s_store + 1, kLaneEstMax);
+      const int og = groups < v.order_grid ? (int)groups : v.order_grid;
+      lane_order_kernel<127><<<og, kLaneGroup, sizeof(OrderShm), st>>>(copy, cap);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
     void* args[] = {&copy, &g};
     return cudaLaunchKernel(v.kernel, dim3(grid), dim3(v.block), args, v.smem, st);
   }

@@ -447,6 +447,201 @@ __device__ __forceinline__ int lane_backtrace(const UGeo* tab, const uint8_t* H,
   return over ? -1 : nr;
 }
 
+// ------------------------------------------------------------ ordering
+//
+// The warp's 32 pairs run in lockstep until the last of them ends, so a
+// warp's cost is set by its highest score.  The ordering pass puts pairs of
+// similar score into the same warp: every group of kLaneGroup consecutive
+// pairs is packed, each pair gets a cheap upper bound on its scaled score,
+// and the group is sorted by it (stable counting sort, in the block).  The
+// packed words go out in the sorted order, so the lane kernel reads them
+// with coalesced loads and packs nothing itself.
+
+// Largest estimate kept apart; empty slots take it too.
+constexpr int kLaneEstMax = 63;
+
+// Cost of a greedy alignment, an upper bound on the optimal scaled score,
+// followed only up to cap (a higher bound changes nothing: such a pair
+// passes the store): from the furthest point of diagonal 0, repeatedly take
+// one edit and extend.  A mismatch followed by at least four matches is
+// taken at once; otherwise the mismatch, one inserted and one deleted base
+// (each priced as a fresh event) are all tried, and the one whose extension
+// ends furthest along v + h, less its cost, is taken.  The rest of the
+// longer sequence at an end is one gap.  Packed words at pw[j * 32].
+__device__ __forceinline__ int lane_estimate(const uint32_t* pw, const uint32_t* tw, int n, int m, int X, int OE,
+                                             int E, int cap) {
+  int k = 0, h = extend_diag32(pw, tw, n, m, 0, 0, 32), cost = 0;
+#pragma unroll 1
+  while (cost < cap) {  // every edit costs at least 1
+    const int v = h - k;
+    if (v >= n || h >= m) {
+      const int rem = (n - v) + (m - h);
+      return min(cost + (rem > 0 ? OE + E * (rem - 1) : 0), cap);
+    }
+    const int hx = extend_diag32(pw, tw, n, m, k, h + 1, 32);  // mismatch: v + 1, h + 1
+    if (hx - h >= 5 || hx - k >= n || hx >= m) {
+      h = hx;
+      cost += X;
+      continue;
+    }
+    const int hi = extend_diag32(pw, tw, n, m, k + 1, h + 1, 32);  // insertion: h + 1
+    const int hd = extend_diag32(pw, tw, n, m, k - 1, h, 32);      // deletion: v + 1
+    // v + h after the extension, less the edit's cost (v = h - k)
+    const int gx = 2 * hx - k - X, gi = 2 * hi - (k + 1) - OE, gd = 2 * hd - (k - 1) - OE;
+    if (gx >= gi && gx >= gd) {
+      h = hx;
+      cost += X;
+    } else if (gi >= gd) {
+      ++k;
+      h = hi;
+      cost += OE;
+    } else {
+      --k;
+      h = hd;
+      cost += OE;
+    }
+  }
+  return cap;
+}
+
+// One lane packs one sequence of at most 16 * NCH - 15 bases from device
+// memory into words 0 .. NCH - 1 (16 bases each, first base in the top bits,
+// zero past the end) at out[j * 32]: every aligned 16-byte chunk holding a
+// base is loaded at once, then the words are cut from the chunks' 2-bit
+// codes.  Returns whether a byte of the sequence is not A/C/G/T.
+template <int NCH>
+__device__ __forceinline__ bool lane_pack_direct(const char* seq, int len, uint32_t* out) {
+  const unsigned long long a0 = reinterpret_cast<uintptr_t>(seq), b0 = a0 & ~15ull;
+  const int h = (int)(a0 - b0);
+  const int nch = (h + len + 15) >> 4;
+  uint4 raw[NCH];
+#pragma unroll
+  for (int c = 0; c < NCH; ++c)  // all loads first: their latencies overlap
+    raw[c] = c < nch ? __ldg(reinterpret_cast<const uint4*>(b0 + 16ull * c)) : make_uint4(0u, 0u, 0u, 0u);
+  uint32_t code[NCH + 1], bad[NCH + 1];
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) {
+    code[c] = 0u;
+    bad[c] = 0u;
+    if (c < nch) code[c] = code16_bad(raw[c], &bad[c]);
+  }
+  code[NCH] = 0u;
+  bad[NCH] = 0u;
+  const int nw = (len + 15) >> 4;
+  bool any_bad = false;
+#pragma unroll
+  for (int j = 0; j < NCH; ++j) {
+    uint32_t word = 0u;
+    if (j < nw) {
+      const int rem = min(16, len - 16 * j);
+      word = __funnelshift_l(code[j + 1], code[j], 2 * h);
+      if (rem < 16) word &= ~0u << (32 - 2 * rem);
+      const uint32_t in = (rem >= 16 ? 0xFFFFu : ((1u << rem) - 1u)) << h;  // the word's bytes in chunks j, j + 1
+      if ((bad[j] | (bad[j + 1] << 16)) & in) any_bad = true;
+    }
+    out[j * 32] = word;
+  }
+  return any_bad;
+}
+
+// Shared memory of the ordering pass: per warp the packed words of its 32
+// pairs; the per-warp counts of each estimate and each estimate's first slot.
+template <int LMAX>
+struct LaneOrderShm {
+  static constexpr int NW = LMAX / 16 + 2;
+  static constexpr int kWarps = kLaneGroup / 32;
+  struct Warp {
+    uint32_t pw[NW * 32];
+    uint32_t tw[NW * 32];
+  } w[kWarps];
+  int cnt[kWarps][kLaneEstMax + 1];
+  int start[kLaneEstMax + 1];
+};
+
+// The ordering pass (block of kLaneGroup threads, one per pair of a group;
+// sequences in device memory, each lane reading its own pair's aligned
+// 16-byte chunks).  Pairs longer than LMAX are deferred and pairs with a
+// byte other than A/C/G/T get their status here; both, and the slots past
+// the last pair, become empty slots (pair -1) at the end of their group.
+template <int LMAX>
+__device__ void lane_order_body(const AlignArgs& a, int est_cap, unsigned char* smem) {
+  using S_t = LaneOrderShm<LMAX>;
+  constexpr int NW = S_t::NW, WG = S_t::kWarps, NK = kLaneEstMax + 1;
+  static_assert(NW == kLaneNW, "packed words per sequence");
+  static_assert(NK <= 64, "two estimates per lane in the scan");
+  constexpr unsigned FULL = 0xffffffffu;
+  if (*(volatile int32_t*)&a.ctrl->bad_input) return;  // inputs rejected by the validation kernel
+  auto& S = *reinterpret_cast<S_t*>(smem);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto& W = S.w[warp];
+  const int64_t groups = (a.n + kLaneGroup - 1) / kLaneGroup;
+  for (int64_t gi = blockIdx.x; gi < groups; gi += gridDim.x) {
+    const int64_t pair = gi * kLaneGroup + threadIdx.x;
+    bool active = pair < a.n;
+    int n = 0, m = 0;
+    if (active) {
+      n = a.plen[pair];
+      m = a.tlen[pair];
+      if (n > LMAX || m > LMAX) {
+        defer_pair(a, pair);
+        active = false;
+      }
+    }
+    if (active) {
+      static_assert(16 * NW - 15 >= LMAX, "chunks of the longest sequence");
+      const bool bad = lane_pack_direct<NW>(a.pat + a.poff[pair], n, W.pw + lane) |
+                       lane_pack_direct<NW>(a.txt + a.toff[pair], m, W.tw + lane);
+      if (bad) {
+        write_result(a, pair, 2, -1, 0, 0);
+        active = false;
+      }
+    }
+    const int key = active ? lane_estimate(W.pw + lane, W.tw + lane, n, m, a.xs, a.oes, a.es, est_cap) : kLaneEstMax;
+    for (int i = threadIdx.x; i < WG * NK; i += kLaneGroup) (&S.cnt[0][0])[i] = 0;
+    __syncthreads();
+    // stable: a pair's slot follows every pair of a lower estimate and every
+    // earlier pair of its own
+    const unsigned same = __match_any_sync(FULL, key);
+    const int before = __popc(same & ((1u << lane) - 1u));
+    if (before == 0) S.cnt[warp][key] = __popc(same);
+    __syncthreads();
+    if (warp == 0) {
+      // lane l: estimates 2l and 2l + 1; each warp's count becomes the count
+      // of the warps before it, then each estimate's first slot
+      int tot[2] = {0, 0};
+      for (int q = 0; q < 2; ++q) {
+        const int e = 2 * lane + q;
+        if (e >= NK) continue;
+        int run = 0;
+        for (int w = 0; w < WG; ++w) {
+          const int c = S.cnt[w][e];
+          S.cnt[w][e] = run;
+          run += c;
+        }
+        tot[q] = run;
+      }
+      const int both = tot[0] + tot[1];
+      int incl = both;
+      for (int d = 1; d < 32; d <<= 1) {
+        const int o = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += o;
+      }
+      if (2 * lane < NK) S.start[2 * lane] = incl - both;
+      if (2 * lane + 1 < NK) S.start[2 * lane + 1] = incl - both + tot[0];
+    }
+    __syncthreads();
+    const int slot = S.start[key] + S.cnt[warp][key] + before;
+    uint32_t* out = a.lane_words + gi * (2 * NW * kLaneGroup) + slot;
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+      out[j * kLaneGroup] = active ? W.pw[j * 32 + lane] : 0u;
+      out[(NW + j) * kLaneGroup] = active ? W.tw[j * 32 + lane] : 0u;
+    }
+    a.lane_slots[gi * kLaneGroup + slot] = make_int2(active ? (int)pair : -1, active ? n | (m << 8) : 0);
+    __syncthreads();  // the counts are reused
+  }
+}
+
 // The lane-per-pair kernel body (global gap-affine alignment, both sequences
 // <= LMAX).  Pairs longer than LMAX, or whose score passes the last stored
 // wavefront (but not the caller's max_score), are deferred to the arena
@@ -473,19 +668,51 @@ __device__ __forceinline__ void lane_body(const AlignArgs& a, const LaneGeo& lg,
   st.s_hi = min(s_store, a.s_cap);
   const int64_t wpb = blockDim.x >> 5;
   const int64_t stride = (int64_t)gridDim.x * wpb * 32;
-  for (int64_t first = ((int64_t)blockIdx.x * wpb + warp) * 32; first < a.n; first += stride) {
-    const int64_t pair = first + lane;
-    bool active = pair < a.n;
+  // ordered input: slots of the ordering pass, whole groups, taken by the
+  // warps in batches of 32 from a queue (within a group the batches' costs
+  // rise with the estimates, so a fixed share would give some warps only
+  // the dearest batches); call order: a fixed stride
+  const bool ordered = a.lane_slots != nullptr;
+  static_assert(C::NW == kLaneNW, "packed words per sequence");
+  const int64_t total = ordered ? (a.n + kLaneGroup - 1) / kLaneGroup * kLaneGroup : a.n;
+  for (int64_t first = ((int64_t)blockIdx.x * wpb + warp) * 32;; first += stride) {
+    if (ordered) {
+      int b = 0;
+      if (lane == 0) b = atomicAdd(&a.ctrl->lane_next, 1);
+      first = (int64_t)__shfl_sync(0xffffffffu, b, 0) * 32;
+    }
+    if (first >= total) break;
+    int64_t pair;
+    bool active;
     int n = 0, m = 0;
-    if (active) {
-      n = a.plen[pair];
-      m = a.tlen[pair];
-      if (n > LMAX || m > LMAX || s_store < 0) {
+    if (ordered) {
+      const int2 sl = a.lane_slots[first + lane];
+      pair = sl.x;
+      active = pair >= 0;
+      n = sl.y & 255;
+      m = sl.y >> 8;
+      if (active && s_store < 0) {
         defer_pair(a, pair);
         active = false;
       }
-    }
-    {
+      const uint32_t* src = a.lane_words + (first / kLaneGroup) * (2 * kLaneNW * kLaneGroup) + first % kLaneGroup +
+                            lane;
+#pragma unroll
+      for (int j = 0; j < kLaneNW; ++j) {
+        W->pw[j * 32 + lane] = src[j * kLaneGroup];
+        W->tw[j * 32 + lane] = src[(kLaneNW + j) * kLaneGroup];
+      }
+    } else {
+      pair = first + lane;
+      active = pair < a.n;
+      if (active) {
+        n = a.plen[pair];
+        m = a.tlen[pair];
+        if (n > LMAX || m > LMAX || s_store < 0) {
+          defer_pair(a, pair);
+          active = false;
+        }
+      }
       // all lanes take part: the warp reads its pairs' sequences together
       uint32_t* scratch = reinterpret_cast<uint32_t*>(W->u);
       const char* ps = active ? a.pat + a.poff[pair] : nullptr;
@@ -504,6 +731,7 @@ __device__ __forceinline__ void lane_body(const AlignArgs& a, const LaneGeo& lg,
         active = false;
       }
     }
+    const bool real = ordered ? pair >= 0 : pair < a.n;
     __syncwarp();  // the packer's scratch becomes the store
     {
       // the I and D rows start null
@@ -523,7 +751,7 @@ __device__ __forceinline__ void lane_body(const AlignArgs& a, const LaneGeo& lg,
       st.XI[(st.cnext >> 5) * 32] = st.ai;
       st.XD[(st.cnext >> 5) * 32] = st.ad;
     }
-    if (pair < a.n) {
+    if (real) {
       if (st.active) {
         // every stored score was tried: beyond the caller's bound, or beyond
         // what this kernel stores (then the arena kernel takes the pair)

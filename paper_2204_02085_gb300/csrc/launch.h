@@ -25,7 +25,7 @@ struct Ctrl {
   long long pat_extent;     // max(offset + length) over patterns
   long long txt_extent;     // max(offset + length) over texts
   int32_t max_len;          // longest pattern or text
-  int32_t pad;
+  int32_t lane_next;        // work-queue head of the lane kernel on ordered input
 };
 
 struct AlignArgs {
@@ -56,7 +56,20 @@ struct AlignArgs {
   int32_t* defer_long_list;  // [n] pairs for the one-CTA arena kernel
   int32_t* overflow_list;    // [n]
   Ctrl* ctrl;
+  // lane-per-pair kernel input order (both null: pairs in call order).  Each
+  // group of kLaneGroup consecutive pairs is packed and sorted by an
+  // estimate of its score; slot q of group j holds its pair's packed words
+  // at lane_words[(j * 2 * kLaneNW + w) * kLaneGroup + q] (w < kLaneNW the
+  // pattern's word w, then the text's) and (pair or -1, n | m << 8) at
+  // lane_slots[j * kLaneGroup + q].
+  uint32_t* lane_words;
+  int2* lane_slots;
 };
+
+// Pairs the lane ordering sorts together, and packed 16-base words per
+// sequence of at most 127 bases the lane kernel reads.
+constexpr int kLaneGroup = 256;
+constexpr int kLaneNW = 127 / 16 + 2;
 
 // longest sequence handled by a one-warp arena team; longer pairs go to a
 // one-CTA team
@@ -86,6 +99,7 @@ struct ShortVariant {
   int kind;     // 0 shared-lane, 1 lane-per-pair
   int rw;       // kind 1: positions of each in-place I and D row
   int ct_x, ct_oe, ct_e;  // kind 1: scaled penalties compiled in (0: any)
+  int order_grid;         // kind 1: blocks of the ordering pass that fit the GPU at once
 };
 struct ShortPlan {
   ShortVariant v[24];
@@ -93,6 +107,9 @@ struct ShortPlan {
 };
 cudaError_t short_plan(int device, ShortPlan* plan);
 cudaError_t launch_short(const AlignArgs& a, const ShortVariant& v, cudaStream_t st);
+// Kernels launch_short enqueues: the ordering pass and the lane kernel for a
+// lane variant with lane_slots set (sequences in device memory), else one.
+int short_launches(const AlignArgs& a, const ShortVariant& v);
 
 // Geometry of the lane-per-pair kernel for one call (a kernel parameter):
 // the uniform table of scores 0..31, the last score the kernel stores (-1:

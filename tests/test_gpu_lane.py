@@ -159,3 +159,52 @@ def test_shared_lane_kernel_still_matches(pkg, oracle_mod, monkeypatch):
         got = al.align(batch, (4, 6, 2))
         assert not al.variant_name(al.timing()["short_variant"]).startswith("lane")
         _check(got, want)
+
+
+@pytest.mark.parametrize("order", ["0", "1"])
+@pytest.mark.parametrize("name", ("lane_l127_c40", "lane_l127_c197", "lane_ct241_l127_c104"))
+def test_input_order_does_not_change_results(pkg, oracle_mod, monkeypatch, order, name):
+    """The lane kernel's pairs sorted by estimated score in groups of 256
+    (default) or taken in call order: the same results, bit for bit, on a
+    batch whose size is no multiple of the group and that holds pairs
+    longer than the kernel takes, pairs with other bytes than A/C/G/T and
+    empty sequences."""
+    from paper_2204_02085_gb300 import synth
+
+    monkeypatch.setenv("WFA_GPU_LANE_ORDER", order)
+    monkeypatch.setenv("WFA_GPU_SHORT_VARIANT", str(_variant_index(pkg, name)))
+    base = _batch(4242)
+    pairs = [base.pair(i) for i in range(base.n)]
+    rng = np.random.default_rng(17)
+    extra = [(b"ACGT" * 40, b"ACGA" * 40), (b"ACGNT", b"ACGT"), (b"", b""), (b"ACGT", b"AC-T"),
+             (b"A" * 128, b"A" * 127), (b"C" * 127, b"C" * 128)]
+    for pr in extra:
+        pairs.insert(int(rng.integers(0, 1500)), pr)
+    pairs = pairs[:2 * 256 * 3 + 77]
+    batch = synth.from_pairs(pairs)
+    pen = (4, 6, 2)
+    want = oracle_mod.wfa_batch(batch, pen, nthreads=8)
+    with pkg.Aligner(0, 1 << 30) as al:
+        _check(al.align(batch, pen), want)
+        for bound in (8, 16):
+            _check(al.align(batch, pen, max_score=bound), oracle_mod.wfa_batch(batch, pen, max_score=bound, nthreads=8))
+        so = al.align(batch, pen, score_only=True)
+        assert np.array_equal(so[0], want[0]) and np.array_equal(so[1], want[1])
+
+
+@pytest.mark.parametrize("e", (2, 4))
+def test_ordered_paper_batch_launch_count(pkg, oracle_mod, monkeypatch, e):
+    """Default path on the paper's workload: the ordering pass runs (one more
+    launch than in call order, for the autotuner's sample run and for the
+    main run) and the results match the oracle."""
+    from paper_2204_02085_gb300 import synth
+
+    batch = synth.uniform_reads(100_003, 100, e, seed=80 + e)
+    want = oracle_mod.wfa_batch(batch, (4, 6, 2), nthreads=16)
+    launches = {}
+    for order in ("0", "1"):
+        monkeypatch.setenv("WFA_GPU_LANE_ORDER", order)
+        with pkg.Aligner(0, 1 << 30) as al:
+            _check(al.align(batch, (4, 6, 2)), want)
+            launches[order] = al.timing()["kernel_launches"]
+    assert launches["1"] == launches["0"] + 2
