@@ -43,8 +43,8 @@ SEED = 1
 CIGAR_WORDS_PER_PAIR = 16
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
 N_SM = 152
-# Integer work of the method, per unit and instruction class (the derivation
-# is in the design notes): a wavefront cell is the three recurrences (three
+# Integer work of the method, per unit and instruction class: a wavefront
+# cell is the three recurrences (three
 # maxima, two +1, three sequence-end tests with their selects) and one
 # 16-base extension window (two word indices, two funnel shifts, XOR,
 # count-leading-zeros, halving, the advance and its end clamp); its shared
@@ -61,13 +61,14 @@ WORK = {"cell": {"alu": 22, "xu": 1, "lsu": 12},
 PIPE_RATE = {"alu": 64, "xu": 16, "lsu": 32, "issue": 128}
 # the flat model of earlier measurements: every op at the issue rate
 FLAT_OPS = {"cell": 32, "window": 18, "bt_step": 12}
-# DRAM traffic of the short kernel (dram__bytes_read.sum + dram__bytes_write.sum
-# from ncu on 1M-pair launches of the same workload, per pair; the traffic of
-# a launch grows in proportion to its pairs), valid for the device sources
-# whose digest is "sha" (kernel_sources_digest); any change to them voids it
-NCU_TRAFFIC = {"sha": "833bd94eef7f6030", "bytes_per_pair": {2: 289.90, 4: 297.69}}
-# the short kernel of the timed region at the time of that capture
-NCU_KERNEL = "short_kernel"
+# DRAM traffic of the short-read path (dram__bytes_read.sum +
+# dram__bytes_write.sum from ncu on 1M-pair launches of the same workload, per
+# pair, the ordering pass and the lane kernel added; the traffic of a launch
+# grows in proportion to its pairs), valid for the device sources whose
+# digest is "sha" (kernel_sources_digest); any change to them voids it
+NCU_TRAFFIC = {"sha": "1bc4e8a3e7585f7a", "bytes_per_pair": {2: 274.62 + 147.76, 4: 274.38 + 145.71}}
+# the kernels of the timed region at the time of that capture
+NCU_KERNEL = "lane_order_kernel + lane_kernel"
 KERNEL_SOURCES = ("wfa_device.cuh", "short_path.cuh", "arena_path.cuh", "lane_path.cuh", "kernels.cu", "launch.h")
 
 
@@ -900,7 +901,8 @@ def main():
                 "frac": achieved_gbs / hbm_gbs, "peak_source": peak_src}
         if alu is not None:
             roof["alu"] = alu
-    roof["kernel"] = "the short-read wavefront kernel (fused pack + wavefront + backtrace)"
+    roof["kernel"] = ("the short-read path: ordering pass (pack, score bound, sort in groups of 256) and lane-per-pair "
+                      "kernel (wavefronts, backtrace), timed together by the call's events")
     roof["bytes_per_pair"] = bpp
     roof["avg_launch_ms"] = align_ms
     roof["traffic"] = None
