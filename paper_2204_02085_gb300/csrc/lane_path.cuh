@@ -504,6 +504,37 @@ __device__ __forceinline__ int lane_estimate(const uint32_t* pw, const uint32_t*
   return cap;
 }
 
+// 16 ASCII bytes -> 16 two-bit codes, first byte in the top bits (A C G T
+// = 0 1 2 3 in either case: bits 1 and 2 of the byte, XORed), and whether a
+// byte is not A/C/G/T: the upper-case letter of each byte's code is picked
+// from "ACGT" by a byte permute with the codes as selectors and compared
+// with the byte folded to upper case.  Only when some byte differs is the
+// per-byte mask (bit i: byte i) worked out.
+__device__ __forceinline__ uint32_t lane_code16(uint4 v, uint32_t* bad16) {
+  const uint32_t q[4] = {v.x, v.y, v.z, v.w};
+  uint32_t code = 0u, xs[4], any = 0u;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t w = q[i];
+    const uint32_t c = ((w >> 1) ^ (w >> 2)) & 0x03030303u;  // byte j's code in bits 8j, 8j + 1
+    const uint32_t sel = __byte_perm(c | (c >> 4), 0u, 0x4420u);  // nibble j = byte j's code
+    xs[i] = (w & 0xDFDFDFDFu) ^ __byte_perm(0x54474341u, 0u, sel);  // zero byte <=> valid
+    any |= xs[i];
+    code = (code << 8) | ((c * 0x40100401u) >> 24);
+  }
+  uint32_t bad = 0u;
+  if (any) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t x = xs[i];
+      const uint32_t hb = ((((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) >> 7) & 0x01010101u;  // 1 per nonzero byte
+      bad |= ((hb * 0x01020408u) >> 24 & 0xFu) << (4 * i);
+    }
+  }
+  *bad16 = bad;
+  return code;
+}
+
 // One lane packs one sequence of at most 16 * NCH - 15 bases from device
 // memory into words 0 .. NCH - 1 (16 bases each, first base in the top bits,
 // zero past the end) at out[j * 32]: every aligned 16-byte chunk holding a
@@ -523,7 +554,7 @@ __device__ __forceinline__ bool lane_pack_direct(const char* seq, int len, uint3
   for (int c = 0; c < NCH; ++c) {
     code[c] = 0u;
     bad[c] = 0u;
-    if (c < nch) code[c] = code16_bad(raw[c], &bad[c]);
+    if (c < nch) code[c] = lane_code16(raw[c], &bad[c]);
   }
   code[NCH] = 0u;
   bad[NCH] = 0u;
@@ -554,7 +585,7 @@ struct LaneOrderShm {
     uint32_t pw[NW * 32];
     uint32_t tw[NW * 32];
   } w[kWarps];
-  int cnt[kWarps][kLaneEstMax + 1];
+  int cnt[2][kWarps][kLaneEstMax + 1];  // alternate groups use alternate halves
   int start[kLaneEstMax + 1];
 };
 
@@ -575,7 +606,10 @@ __device__ void lane_order_body(const AlignArgs& a, int est_cap, unsigned char* 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   auto& W = S.w[warp];
   const int64_t groups = (a.n + kLaneGroup - 1) / kLaneGroup;
-  for (int64_t gi = blockIdx.x; gi < groups; gi += gridDim.x) {
+  for (int i = threadIdx.x; i < 2 * WG * NK; i += kLaneGroup) (&S.cnt[0][0][0])[i] = 0;
+  __syncthreads();
+  int half = 0;
+  for (int64_t gi = blockIdx.x; gi < groups; gi += gridDim.x, half ^= 1) {
     const int64_t pair = gi * kLaneGroup + threadIdx.x;
     bool active = pair < a.n;
     int n = 0, m = 0;
@@ -597,14 +631,16 @@ __device__ void lane_order_body(const AlignArgs& a, int est_cap, unsigned char* 
       }
     }
     const int key = active ? lane_estimate(W.pw + lane, W.tw + lane, n, m, a.xs, a.oes, a.es, est_cap) : kLaneEstMax;
-    for (int i = threadIdx.x; i < WG * NK; i += kLaneGroup) (&S.cnt[0][0])[i] = 0;
-    __syncthreads();
     // stable: a pair's slot follows every pair of a lower estimate and every
-    // earlier pair of its own
+    // earlier pair of its own.  This group's counts are in half `half` (zero:
+    // cleared while the group before used the other half)
+    auto& cnt = S.cnt[half];
     const unsigned same = __match_any_sync(FULL, key);
     const int before = __popc(same & ((1u << lane) - 1u));
-    if (before == 0) S.cnt[warp][key] = __popc(same);
+    if (before == 0) cnt[warp][key] = __popc(same);
     __syncthreads();
+    // every warp is past its reads of the other half (the group before)
+    for (int i = threadIdx.x; i < WG * NK; i += kLaneGroup) (&S.cnt[half ^ 1][0][0])[i] = 0;
     if (warp == 0) {
       // lane l: estimates 2l and 2l + 1; each warp's count becomes the count
       // of the warps before it, then each estimate's first slot
@@ -614,8 +650,8 @@ __device__ void lane_order_body(const AlignArgs& a, int est_cap, unsigned char* 
         if (e >= NK) continue;
         int run = 0;
         for (int w = 0; w < WG; ++w) {
-          const int c = S.cnt[w][e];
-          S.cnt[w][e] = run;
+          const int c = cnt[w][e];
+          cnt[w][e] = run;
           run += c;
         }
         tot[q] = run;
@@ -630,7 +666,7 @@ __device__ void lane_order_body(const AlignArgs& a, int est_cap, unsigned char* 
       if (2 * lane + 1 < NK) S.start[2 * lane + 1] = incl - both + tot[0];
     }
     __syncthreads();
-    const int slot = S.start[key] + S.cnt[warp][key] + before;
+    const int slot = S.start[key] + cnt[warp][key] + before;
     uint32_t* out = a.lane_words + gi * (2 * NW * kLaneGroup) + slot;
 #pragma unroll
     for (int j = 0; j < NW; ++j) {
@@ -638,7 +674,8 @@ __device__ void lane_order_body(const AlignArgs& a, int est_cap, unsigned char* 
       out[(NW + j) * kLaneGroup] = active ? W.tw[j * 32 + lane] : 0u;
     }
     a.lane_slots[gi * kLaneGroup + slot] = make_int2(active ? (int)pair : -1, active ? n | (m << 8) : 0);
-    __syncthreads();  // the counts are reused
+    // no barrier here: the next group's first barrier comes after every
+    // warp's reads of this group's counts and first slots
   }
 }
 
