@@ -137,6 +137,8 @@ template <int LMAX, int CELLS, int RW, int SPAN_BYTES>
 struct LaneCfg {
   static_assert(LMAX <= 127, "one-byte offsets");
   static constexpr int NW = LMAX / 16 + 2;  // packed 16-base words a window may touch
+  // words of room per sequence: a 32-base window of the pending pass reads
+  // one word past the last that holds a base (its value never counts)
   static constexpr int kHBytes = CELLS * 32;
   static constexpr int kXWords = (CELLS + 31) / 32;  // words of each bit stream
   static constexpr int kXBytes = 2 * kXWords * 4 * 32;
@@ -145,8 +147,8 @@ struct LaneCfg {
   static constexpr int kUnion = ((kStore > SPAN_BYTES ? kStore : SPAN_BYTES) + 15) / 16 * 16;
   static constexpr int kSpanFit = kUnion / 16;
   struct WarpShm {
-    uint32_t pw[NW * 32];
-    uint32_t tw[NW * 32];
+    uint32_t pw[(NW + 1) * 32];
+    uint32_t tw[(NW + 1) * 32];
     alignas(16) unsigned char u[kUnion];
   };
   static constexpr size_t kTabBytes = (sizeof(UGeo) * 32 + 15) / 16 * 16;
@@ -170,9 +172,21 @@ struct LaneSt {
   int s_fin;           // scaled score once finished
 };
 
+// 32 bases from base position pos of a packed sequence (words at W[j * 32]):
+// the XOR of the pattern's and the text's windows in two 32-bit halves
+// gives the matches before the first difference, up to 32.
+__device__ __forceinline__ int lane_match32(const uint32_t* pw, int v, const uint32_t* tw, int h) {
+  const int jp = v >> 4, sp = (v & 15) << 1, jt = h >> 4, st = (h & 15) << 1;
+  const uint32_t p1 = pw[(jp + 1) * 32];
+  const uint32_t t1 = tw[(jt + 1) * 32];
+  const uint32_t dh = __funnelshift_l(p1, pw[jp * 32], sp) ^ __funnelshift_l(t1, tw[jt * 32], st);
+  const uint32_t dl = __funnelshift_l(pw[(jp + 2) * 32], p1, sp) ^ __funnelshift_l(tw[(jt + 2) * 32], t1, st);
+  return dh ? (int)(__clz(dh) >> 1) : 16 + (int)(__clz(dl) >> 1);
+}
+
 // A lane's remaining extension rounds for the cells of one score whose first
-// 16 bases matched (bit i: item i); each pass of the loop runs one round on
-// every lane that has a cell left.
+// 16 bases matched (bit i: item i); each pass of the loop runs one round of
+// 32 bases on every lane that has a cell left.
 __device__ __forceinline__ void lane_pending(LaneSt& st, uint32_t pend, int lo, int base) {
   constexpr unsigned FULL = 0xffffffffu;
   int ci = -1, ck = 0, cb = 0, ch = 0;
@@ -185,10 +199,9 @@ __device__ __forceinline__ void lane_pending(LaneSt& st, uint32_t pend, int lo, 
       ch = cb - (int)st.H[(base + ci) * 32];
     }
     if (ci >= 0) {
-      const uint32_t d = window32s(st.pw, ch - ck, 32) ^ window32s(st.tw, ch, 32);
-      const int eq = __clz(d) >> 1;
+      const int eq = lane_match32(st.pw, ch - ck, st.tw, ch);
       ch += eq;
-      if (eq < 16 || ch >= cb) {
+      if (eq < 32 || ch >= cb) {
         st.H[(base + ci) * 32] = (uint8_t)(cb - min(ch, cb));
         ci = -1;
       }
@@ -712,18 +725,42 @@ __device__ __forceinline__ void lane_body(const AlignArgs& a, const LaneGeo& lg,
   const bool ordered = a.lane_slots != nullptr;
   static_assert(C::NW == kLaneNW, "packed words per sequence");
   const int64_t total = ordered ? (a.n + kLaneGroup - 1) / kLaneGroup * kLaneGroup : a.n;
+  // ordered input: the next batch's slot and packed words are loaded into
+  // registers while the current batch computes
+  int64_t next = total;
+  int2 nsl = make_int2(-1, 0);
+  uint32_t nwd[2 * kLaneNW];
+  auto grab = [&]() -> int64_t {
+    int b = 0;
+    if (lane == 0) b = atomicAdd(&a.ctrl->lane_next, 1);
+    return (int64_t)__shfl_sync(0xffffffffu, b, 0) * 32;
+  };
+  auto fetch = [&](int64_t f) {
+    if (f >= total) return;
+    nsl = a.lane_slots[f + lane];
+    const uint32_t* src = a.lane_words + (f / kLaneGroup) * (2 * kLaneNW * kLaneGroup) + f % kLaneGroup + lane;
+#pragma unroll
+    for (int j = 0; j < 2 * kLaneNW; ++j) nwd[j] = src[j * kLaneGroup];
+  };
+  if (ordered) {
+    next = grab();
+    fetch(next);
+  }
   for (int64_t first = ((int64_t)blockIdx.x * wpb + warp) * 32;; first += stride) {
-    if (ordered) {
-      int b = 0;
-      if (lane == 0) b = atomicAdd(&a.ctrl->lane_next, 1);
-      first = (int64_t)__shfl_sync(0xffffffffu, b, 0) * 32;
-    }
+    if (ordered) first = next;
     if (first >= total) break;
     int64_t pair;
     bool active;
     int n = 0, m = 0;
     if (ordered) {
-      const int2 sl = a.lane_slots[first + lane];
+      const int2 sl = nsl;
+#pragma unroll
+      for (int j = 0; j < kLaneNW; ++j) {
+        W->pw[j * 32 + lane] = nwd[j];
+        W->tw[j * 32 + lane] = nwd[kLaneNW + j];
+      }
+      next = grab();
+      fetch(next);
       pair = sl.x;
       active = pair >= 0;
       n = sl.y & 255;
@@ -731,13 +768,6 @@ __device__ __forceinline__ void lane_body(const AlignArgs& a, const LaneGeo& lg,
       if (active && s_store < 0) {
         defer_pair(a, pair);
         active = false;
-      }
-      const uint32_t* src = a.lane_words + (first / kLaneGroup) * (2 * kLaneNW * kLaneGroup) + first % kLaneGroup +
-                            lane;
-#pragma unroll
-      for (int j = 0; j < kLaneNW; ++j) {
-        W->pw[j * 32 + lane] = src[j * kLaneGroup];
-        W->tw[j * 32 + lane] = src[(kLaneNW + j) * kLaneGroup];
       }
     } else {
       pair = first + lane;
