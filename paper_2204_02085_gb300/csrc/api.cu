@@ -141,6 +141,7 @@ struct wfa_gpu_ctx {
   // the lane kernel's pairs sorted by estimated score in groups (default
   // path; WFA_GPU_LANE_ORDER=0: call order), and the ordering's buffers
   bool lane_order = true;
+  int lane_sort_min = 12;  // the ordering sorts for stores of scores 0-12 and up (WFA_GPU_LANE_SORT_MIN)
   DevBuf<uint32_t> lane_words;
   DevBuf<int2> lane_slots;
   int variant_forced = -1;  // tuning override (WFA_GPU_SHORT_VARIANT)
@@ -537,6 +538,7 @@ cudaError_t lane_order_args(wfa_gpu_ctx* c, wfa::AlignArgs& a, int64_t n, bool m
   }
   a.lane_words = c->lane_words.p;
   a.lane_slots = c->lane_slots.p;
+  a.lane_sort_min = c->lane_sort_min;
   return cudaSuccess;
 }
 
@@ -677,6 +679,7 @@ int wfa_gpu_create(wfa_gpu_ctx** out, int device, size_t scratch_bytes) {
     }
     if (const char* ev = std::getenv("WFA_GPU_LANE")) c->lane_on = std::atoi(ev) != 0;
     if (const char* ev = std::getenv("WFA_GPU_LANE_ORDER")) c->lane_order = std::atoi(ev) != 0;
+    if (const char* ev = std::getenv("WFA_GPU_LANE_SORT_MIN")) c->lane_sort_min = std::atoi(ev);
     // tuning override: WFA_GPU_SHORT_VARIANT=<index> for the <= 127-base case
     if (const char* ev = std::getenv("WFA_GPU_SHORT_VARIANT")) {
       const int v = std::atoi(ev);

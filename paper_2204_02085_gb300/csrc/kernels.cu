@@ -561,8 +561,8 @@ cudaError_t launch_short(const AlignArgs& a, const ShortVariant& v, cudaStream_t
     lane_geometry(a, v.cells, v.rw, &g);
     if (ordered) {
       // estimates above the store's last score all mean "deferred": the
-      // greedy walk stops there
-      const int cap = g.s_store < 0 ? 1 : std::min(g.s_store + 1, kLaneEstMax);
+      // greedy walk stops there; a small store is ordered by packing alone
+      const int cap = g.s_store < a.lane_sort_min ? 0 : std::min(g.s_store + 1, kLaneEstMax);
       const int og = groups < v.order_grid ? (int)groups : v.order_grid;
       lane_order_kernel<127><<<og, kLaneGroup, sizeof(OrderShm), st>>>(copy, cap);
       const cudaError_t e = cudaGetLastError();

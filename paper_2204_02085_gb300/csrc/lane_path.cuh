@@ -604,7 +604,9 @@ struct LaneOrderShm {
 
 // The ordering pass (block of kLaneGroup threads, one per pair of a group;
 // sequences in device memory, each lane reading its own pair's aligned
-// 16-byte chunks).  Pairs longer than LMAX are deferred and pairs with a
+// 16-byte chunks).  est_cap = 0: pack only, every slot keeps its pair's
+// place in the group (for stores so small that every warp ends within a few
+// scores anyway, where the estimate would cost more than it saves).  Pairs longer than LMAX are deferred and pairs with a
 // byte other than A/C/G/T get their status here; both, and the slots past
 // the last pair, become empty slots (pair -1) at the end of their group.
 template <int LMAX>
@@ -642,6 +644,16 @@ __device__ void lane_order_body(const AlignArgs& a, int est_cap, unsigned char* 
         write_result(a, pair, 2, -1, 0, 0);
         active = false;
       }
+    }
+    if (est_cap <= 0) {  // call order (uniform over the launch)
+      uint32_t* out = a.lane_words + gi * (2 * NW * kLaneGroup) + threadIdx.x;
+#pragma unroll
+      for (int j = 0; j < NW; ++j) {
+        out[j * kLaneGroup] = active ? W.pw[j * 32 + lane] : 0u;
+        out[(NW + j) * kLaneGroup] = active ? W.tw[j * 32 + lane] : 0u;
+      }
+      a.lane_slots[pair] = make_int2(active ? (int)pair : -1, active ? n | (m << 8) : 0);
+      continue;
     }
     const int key = active ? lane_estimate(W.pw + lane, W.tw + lane, n, m, a.xs, a.oes, a.es, est_cap) : kLaneEstMax;
     // stable: a pair's slot follows every pair of a lower estimate and every

@@ -64,6 +64,7 @@ struct AlignArgs {
   // lane_slots[j * kLaneGroup + q].
   uint32_t* lane_words;
   int2* lane_slots;
+  int lane_sort_min;  // smallest store (last stored score) whose ordering sorts
 };
 
 // Pairs the lane ordering sorts together, and packed 16-base words per

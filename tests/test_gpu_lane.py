@@ -208,3 +208,18 @@ def test_ordered_paper_batch_launch_count(pkg, oracle_mod, monkeypatch, e):
             _check(al.align(batch, (4, 6, 2)), want)
             launches[order] = al.timing()["kernel_launches"]
     assert launches["1"] == launches["0"] + 2
+
+
+@pytest.mark.parametrize("sort_min", ["0", "99"])
+@pytest.mark.parametrize("name", ("lane_ct241_l127_c40", "lane_l127_c197"))
+def test_sorted_and_pack_only_ordering_agree(pkg, oracle_mod, monkeypatch, sort_min, name):
+    """The ordering pass sorting every store's groups (WFA_GPU_LANE_SORT_MIN=0)
+    or packing them in call order (99): the oracle's results either way."""
+    from paper_2204_02085_gb300 import synth
+
+    monkeypatch.setenv("WFA_GPU_LANE_SORT_MIN", sort_min)
+    monkeypatch.setenv("WFA_GPU_SHORT_VARIANT", str(_variant_index(pkg, name)))
+    batch = synth.uniform_reads(30_001, 100, 4, seed=91)
+    want = oracle_mod.wfa_batch(batch, (4, 6, 2), nthreads=16)
+    with pkg.Aligner(0, 1 << 30) as al:
+        _check(al.align(batch, (4, 6, 2)), want)
