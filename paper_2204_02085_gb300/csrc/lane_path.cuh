@@ -481,9 +481,22 @@ constexpr int kLaneEstMax = 63;
 // (each priced as a fresh event) are all tried, and the one whose extension
 // ends furthest along v + h, less its cost, is taken.  The rest of the
 // longer sequence at an end is one gap.  Packed words at pw[j * 32].
+// The furthest offset of diagonal k from offset h (packed words at W[j * 32],
+// one word of room past the last base): 32 bases a round.
+__device__ __forceinline__ int lane_extend32(const uint32_t* pw, const uint32_t* tw, int n, int m, int k, int h) {
+  for (;;) {
+    const int rem = min(n - (h - k), m - h);
+    if (rem <= 0) return h;
+    const int eq = lane_match32(pw, h - k, tw, h);
+    if (eq >= rem) return h + rem;
+    h += eq;
+    if (eq < 32) return h;
+  }
+}
+
 __device__ __forceinline__ int lane_estimate(const uint32_t* pw, const uint32_t* tw, int n, int m, int X, int OE,
                                              int E, int cap) {
-  int k = 0, h = extend_diag32(pw, tw, n, m, 0, 0, 32), cost = 0;
+  int k = 0, h = lane_extend32(pw, tw, n, m, 0, 0), cost = 0;
 #pragma unroll 1
   while (cost < cap) {  // every edit costs at least 1
     const int v = h - k;
@@ -491,14 +504,14 @@ __device__ __forceinline__ int lane_estimate(const uint32_t* pw, const uint32_t*
       const int rem = (n - v) + (m - h);
       return min(cost + (rem > 0 ? OE + E * (rem - 1) : 0), cap);
     }
-    const int hx = extend_diag32(pw, tw, n, m, k, h + 1, 32);  // mismatch: v + 1, h + 1
+    const int hx = lane_extend32(pw, tw, n, m, k, h + 1);  // mismatch: v + 1, h + 1
     if (hx - h >= 5 || hx - k >= n || hx >= m) {
       h = hx;
       cost += X;
       continue;
     }
-    const int hi = extend_diag32(pw, tw, n, m, k + 1, h + 1, 32);  // insertion: h + 1
-    const int hd = extend_diag32(pw, tw, n, m, k - 1, h, 32);      // deletion: v + 1
+    const int hi = lane_extend32(pw, tw, n, m, k + 1, h + 1);  // insertion: h + 1
+    const int hd = lane_extend32(pw, tw, n, m, k - 1, h);      // deletion: v + 1
     // v + h after the extension, less the edit's cost (v = h - k)
     const int gx = 2 * hx - k - X, gi = 2 * hi - (k + 1) - OE, gd = 2 * hd - (k - 1) - OE;
     if (gx >= gi && gx >= gd) {
@@ -594,9 +607,9 @@ template <int LMAX>
 struct LaneOrderShm {
   static constexpr int NW = LMAX / 16 + 2;
   static constexpr int kWarps = kLaneGroup / 32;
-  struct Warp {
-    uint32_t pw[NW * 32];
-    uint32_t tw[NW * 32];
+  struct Warp {  // one word of room past the last for 32-base windows
+    uint32_t pw[(NW + 1) * 32];
+    uint32_t tw[(NW + 1) * 32];
   } w[kWarps];
   int cnt[2][kWarps][kLaneEstMax + 1];  // alternate groups use alternate halves
   int start[kLaneEstMax + 1];
