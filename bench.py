@@ -901,7 +901,7 @@ def main():
                 "frac": achieved_gbs / hbm_gbs, "peak_source": peak_src}
         if alu is not None:
             roof["alu"] = alu
-    roof["kernel"] = ("the short-read path: ordering pass (pack, score bound, sort in groups of 256) and lane-per-pair "
+    roof["kernel"] = ("the short-read path: ordering pass (pack, score bound, sort in groups of 1,024) and lane-per-pair "
                       "kernel (wavefronts, backtrace), timed together by the call's events")
     roof["bytes_per_pair"] = bpp
     roof["avg_launch_ms"] = align_ms

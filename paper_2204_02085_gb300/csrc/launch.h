@@ -69,7 +69,7 @@ struct AlignArgs {
 
 // Pairs the lane ordering sorts together, and packed 16-base words per
 // sequence of at most 127 bases the lane kernel reads.
-constexpr int kLaneGroup = 256;
+constexpr int kLaneGroup = 1024;
 constexpr int kLaneNW = 127 / 16 + 2;
 
 // longest sequence handled by a one-warp arena team; longer pairs go to a

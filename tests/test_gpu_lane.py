@@ -164,7 +164,7 @@ def test_shared_lane_kernel_still_matches(pkg, oracle_mod, monkeypatch):
 @pytest.mark.parametrize("order", ["0", "1"])
 @pytest.mark.parametrize("name", ("lane_l127_c40", "lane_l127_c197", "lane_ct241_l127_c104"))
 def test_input_order_does_not_change_results(pkg, oracle_mod, monkeypatch, order, name):
-    """The lane kernel's pairs sorted by estimated score in groups of 256
+    """The lane kernel's pairs sorted by estimated score in groups
     (default) or taken in call order: the same results, bit for bit, on a
     batch whose size is no multiple of the group and that holds pairs
     longer than the kernel takes, pairs with other bytes than A/C/G/T and
@@ -180,7 +180,7 @@ def test_input_order_does_not_change_results(pkg, oracle_mod, monkeypatch, order
              (b"A" * 128, b"A" * 127), (b"C" * 127, b"C" * 128)]
     for pr in extra:
         pairs.insert(int(rng.integers(0, 1500)), pr)
-    pairs = pairs[:2 * 256 * 3 + 77]
+    pairs = pairs[:2 * 1024 + 77]  # two groups of 1,024 and a ragged third
     batch = synth.from_pairs(pairs)
     pen = (4, 6, 2)
     want = oracle_mod.wfa_batch(batch, pen, nthreads=8)
