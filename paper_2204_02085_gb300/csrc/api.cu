@@ -141,7 +141,8 @@ struct wfa_gpu_ctx {
   // the lane kernel's pairs sorted by estimated score in groups (default
   // path; WFA_GPU_LANE_ORDER=0: call order), and the ordering's buffers
   bool lane_order = true;
-  int lane_sort_min = 12;  // the ordering sorts for stores of scores 0-12 and up (WFA_GPU_LANE_SORT_MIN)
+  int lane_sort_min = 12;
+  int64_t pipe_chunk = 1 << 19;  // pairs per chunk of a pipelined host call (WFA_GPU_PIPE_CHUNK)  // the ordering sorts for stores of scores 0-12 and up (WFA_GPU_LANE_SORT_MIN)
   DevBuf<uint32_t> lane_words;
   DevBuf<int2> lane_slots;
   int variant_forced = -1;  // tuning override (WFA_GPU_SHORT_VARIANT)
@@ -324,22 +325,14 @@ int stage_inputs(wfa_gpu_ctx* c, Call& k, int64_t n, bool dev, const char* pat, 
     *d_plen = plen;
     *d_tlen = tlen;
   } else {
-    const void* mp = mapped_range(plen, n * sizeof(int32_t));
-    const void* mt = mapped_range(tlen, n * sizeof(int32_t));
-    if (mp) {
-      *d_plen = static_cast<const int32_t*>(mp);
-    } else {
-      if ((e = c->plen.ensure(n))) return map_alloc(e);
-      if (!k.ok(h2d(c->plen.p, plen, n * sizeof(int32_t), st))) return WFA_GPU_ECUDA;
-      *d_plen = c->plen.p;
-    }
-    if (mt) {
-      *d_tlen = static_cast<const int32_t*>(mt);
-    } else {
-      if ((e = c->tlen.ensure(n))) return map_alloc(e);
-      if (!k.ok(h2d(c->tlen.p, tlen, n * sizeof(int32_t), st))) return WFA_GPU_ECUDA;
-      *d_tlen = c->tlen.p;
-    }
+    // host lengths: one bulk copy each, also from page-locked memory (the
+    // offset scans read them twice, and the kernels again: in place over
+    // the link that costs several times the copy)
+    if ((e = c->plen.ensure(n)) || (e = c->tlen.ensure(n))) return map_alloc(e);
+    if (!k.ok(h2d(c->plen.p, plen, n * sizeof(int32_t), st)) || !k.ok(h2d(c->tlen.p, tlen, n * sizeof(int32_t), st)))
+      return WFA_GPU_ECUDA;
+    *d_plen = c->plen.p;
+    *d_tlen = c->tlen.p;
   }
   if ((e = c->scan_tmp.ensure(wfa::scan_tmp_elems(n)))) return map_alloc(e);
   bool validated = false;
@@ -680,6 +673,10 @@ int wfa_gpu_create(wfa_gpu_ctx** out, int device, size_t scratch_bytes) {
     if (const char* ev = std::getenv("WFA_GPU_LANE")) c->lane_on = std::atoi(ev) != 0;
     if (const char* ev = std::getenv("WFA_GPU_LANE_ORDER")) c->lane_order = std::atoi(ev) != 0;
     if (const char* ev = std::getenv("WFA_GPU_LANE_SORT_MIN")) c->lane_sort_min = std::atoi(ev);
+    if (const char* ev = std::getenv("WFA_GPU_PIPE_CHUNK")) {
+      const long long v = std::atoll(ev);
+      if (v >= (1 << 14) && v <= (1 << 24)) c->pipe_chunk = v;
+    }
     // tuning override: WFA_GPU_SHORT_VARIANT=<index> for the <= 127-base case
     if (const char* ev = std::getenv("WFA_GPU_SHORT_VARIANT")) {
       const int v = std::atoi(ev);
@@ -722,7 +719,10 @@ int wfa_gpu_set_stream(wfa_gpu_ctx* ctx, void* stream) {
 namespace {
 
 // Host-pointer calls of at least kPipeMinPairs pairs whose outputs are
-// page-locked run in chunks of kPipeChunk pairs: each chunk goes through
+// page-locked run in chunks of pipe_chunk pairs (512K unless the
+// WFA_GPU_PIPE_CHUNK tuning variable says otherwise; smaller chunks measured
+// slower, the host's round trip per chunk outweighing a shorter fill and
+// drain of the pipeline): each chunk goes through
 // the whole device sequence (short kernel, arena kernels for its deferred
 // pairs, CIGAR offset scan and compaction, its CIGAR offsets moved to the
 // call's running word count), and its outputs are copied back on the
@@ -733,7 +733,6 @@ namespace {
 // kernel that reads host memory in place waits on every load it sends over
 // the link, where the copy engine's transfers hold up no computation).
 constexpr int64_t kPipeMinPairs = 1 << 21;
-constexpr int64_t kPipeChunk = 1 << 19;
 
 // Host inputs a chunked call streams chunk by chunk (null: none): the
 // sequences, and the lengths when they are page-locked too (else they are
@@ -761,7 +760,8 @@ int align_pipelined(wfa_gpu_ctx* ctx, Call& k, const wfa::AlignArgs& a, int64_t 
                     int64_t cap, int64_t* out_off, const StreamIn* sin) {
   cudaStream_t st = ctx->stream, cs = ctx->copy_stream, is = ctx->in_stream;
   const bool score_only = a.score_only != 0;
-  const int64_t nchunks = (n + kPipeChunk - 1) / kPipeChunk;
+  const int64_t kChunk = ctx->pipe_chunk;
+  const int64_t nchunks = (n + kChunk - 1) / kChunk;
   cudaError_t e;
   if (!score_only && (e = ctx->cig_off.ensure(n + nchunks + 1))) return map_alloc(e);
   const wfa::Ctrl staged = *ctx->h_ctrl;  // the whole batch's validation: extents, longest sequence
@@ -778,12 +778,12 @@ int align_pipelined(wfa_gpu_ctx* ctx, Call& k, const wfa::AlignArgs& a, int64_t 
   // pattern lengths, text lengths (lens bytes each)
   const int64_t *hp = nullptr, *ht = nullptr;
   int64_t slot = 0;
-  const int64_t lens = (kPipeChunk * (int64_t)sizeof(int32_t) + 255) & ~(int64_t)255;
+  const int64_t lens = (kChunk * (int64_t)sizeof(int32_t) + 255) & ~(int64_t)255;
   auto slot_at = [&](int64_t c) { return ctx->ring.p + (size_t)(c % kRing) * (size_t)(2 * slot + 2 * lens); };
   auto copy_in = [&](int64_t c) -> bool {
     const int s2 = (int)(c % kRing);
     char* rp = slot_at(c);
-    const int64_t b = c * kPipeChunk, m = std::min(kPipeChunk, n - b);
+    const int64_t b = c * kChunk, m = std::min(kChunk, n - b);
     return k.ok(cudaStreamWaitEvent(is, ctx->ev_free[s2], 0)) &&
            k.ok(h2d(rp, sin->pat + hp[c], (size_t)(hp[c + 1] - hp[c]), is)) &&
            k.ok(h2d(rp + slot, sin->txt + ht[c], (size_t)(ht[c + 1] - ht[c]), is)) &&
@@ -794,7 +794,7 @@ int align_pipelined(wfa_gpu_ctx* ctx, Call& k, const wfa::AlignArgs& a, int64_t 
   if (sin) {
     if ((e = ctx->h_bounds.ensure((size_t)(2 * (nchunks + 1))))) return map_alloc(e);
     int64_t* hb = ctx->h_bounds.p;
-    const size_t pitch = (size_t)kPipeChunk * sizeof(int64_t);
+    const size_t pitch = (size_t)kChunk * sizeof(int64_t);
     if (!k.ok(cudaMemcpy2DAsync(hb, sizeof(int64_t), a.poff, pitch, sizeof(int64_t), (size_t)nchunks,
                                 cudaMemcpyDeviceToHost, st)) ||
         !k.ok(cudaMemcpy2DAsync(hb + nchunks + 1, sizeof(int64_t), a.toff, pitch, sizeof(int64_t),
@@ -817,7 +817,7 @@ int align_pipelined(wfa_gpu_ctx* ctx, Call& k, const wfa::AlignArgs& a, int64_t 
   int64_t base = 0, deferred = 0;
   bool over = false;
   for (int64_t c = 0; c < nchunks; ++c) {
-    const int64_t b = c * kPipeChunk, m = std::min(kPipeChunk, n - b);
+    const int64_t b = c * kChunk, m = std::min(kChunk, n - b);
     wfa::AlignArgs ac = a;
     ac.n = m;
     ac.poff = a.poff + b; ac.plen = a.plen + b;
@@ -1025,13 +1025,11 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
       (score_only || (mapped_range(out_cigar_offsets, (size_t)(n + 1) * sizeof(int64_t)) &&
                       (cap == 0 || mapped_range(out_cigars, (size_t)cap * sizeof(uint32_t)))))) {
     const size_t pe = (size_t)ctx->h_ctrl->pat_extent, te = (size_t)ctx->h_ctrl->txt_extent;
-    const bool lens_mapped = mapped_range(pattern_lengths, (size_t)n * sizeof(int32_t)) &&
-                             mapped_range(text_lengths, (size_t)n * sizeof(int32_t));
-    const StreamIn sin{patterns, texts, lens_mapped ? pattern_lengths : nullptr,
-                       lens_mapped ? text_lengths : nullptr};
+    // the lengths are on the device already (stage_inputs)
+    const StreamIn sin{patterns, texts, nullptr, nullptr};
     const bool streamed = host_seqs && !pattern_offsets && !text_offsets && mapped_range(patterns, pe) &&
                           mapped_range(texts, te);
-    if (mode == 0 && (e = lane_order_args(ctx, a, std::min(n, kPipeChunk), true))) return map_alloc(e);
+    if (mode == 0 && (e = lane_order_args(ctx, a, std::min(n, ctx->pipe_chunk), true))) return map_alloc(e);
     rc = align_pipelined(ctx, k, a, n, mode, pen, out_scores, out_status, out_cigars, cap, out_cigar_offsets,
                          streamed ? &sin : nullptr);
     if (rc < 0 && rc != WFA_GPU_ECIGAR_CAPACITY) return rc;
