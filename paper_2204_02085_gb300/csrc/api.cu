@@ -734,14 +734,11 @@ namespace {
 // the link, where the copy engine's transfers hold up no computation).
 constexpr int64_t kPipeMinPairs = 1 << 21;
 
-// Host inputs a chunked call streams chunk by chunk (null: none): the
-// sequences, and the lengths when they are page-locked too (else they are
-// on the device already).
+// Host sequences a chunked call streams chunk by chunk (the lengths are on
+// the device already).
 struct StreamIn {
   const char* pat;
   const char* txt;
-  const int32_t* plen;
-  const int32_t* tlen;
 };
 
 // Waits for the input stream when a chunked call returns: no copy of the
@@ -774,21 +771,16 @@ int align_pipelined(wfa_gpu_ctx* ctx, Call& k, const wfa::AlignArgs& a, int64_t 
   InStreamDrain drain{sin ? is : nullptr};
   // streamed inputs: each chunk's first pattern and text offsets (the
   // device scans'), the ring slot size, and the first chunk's copy
-  // ring slot layout: pattern bases (slot bytes), text bases (slot bytes),
-  // pattern lengths, text lengths (lens bytes each)
+  // ring slot layout: pattern bases, then text bases (slot bytes each)
   const int64_t *hp = nullptr, *ht = nullptr;
   int64_t slot = 0;
-  const int64_t lens = (kChunk * (int64_t)sizeof(int32_t) + 255) & ~(int64_t)255;
-  auto slot_at = [&](int64_t c) { return ctx->ring.p + (size_t)(c % kRing) * (size_t)(2 * slot + 2 * lens); };
+  auto slot_at = [&](int64_t c) { return ctx->ring.p + (size_t)(c % kRing) * (size_t)(2 * slot); };
   auto copy_in = [&](int64_t c) -> bool {
     const int s2 = (int)(c % kRing);
     char* rp = slot_at(c);
-    const int64_t b = c * kChunk, m = std::min(kChunk, n - b);
     return k.ok(cudaStreamWaitEvent(is, ctx->ev_free[s2], 0)) &&
            k.ok(h2d(rp, sin->pat + hp[c], (size_t)(hp[c + 1] - hp[c]), is)) &&
            k.ok(h2d(rp + slot, sin->txt + ht[c], (size_t)(ht[c + 1] - ht[c]), is)) &&
-           (!sin->plen || (k.ok(h2d(rp + 2 * slot, sin->plen + b, (size_t)m * sizeof(int32_t), is)) &&
-                           k.ok(h2d(rp + 2 * slot + lens, sin->tlen + b, (size_t)m * sizeof(int32_t), is)))) &&
            k.ok(cudaEventRecord(ctx->ev_in[s2], is));
   };
   if (sin) {
@@ -809,7 +801,7 @@ int align_pipelined(wfa_gpu_ctx* ctx, Call& k, const wfa::AlignArgs& a, int64_t 
     for (int64_t c = 0; c < nchunks; ++c) slot = std::max(slot, std::max(hp[c + 1] - hp[c], ht[c + 1] - ht[c]));
     // 16 bytes of slack: the packer reads whole aligned 16-byte chunks
     slot = (slot + 16 + 255) & ~(int64_t)255;
-    if ((e = ctx->ring.ensure((size_t)(kRing * (2 * slot + 2 * lens))))) return map_alloc(e);
+    if ((e = ctx->ring.ensure((size_t)(kRing * 2 * slot)))) return map_alloc(e);
     for (int64_t c = 0; c < std::min<int64_t>(kRing - 1, nchunks); ++c)
       if (!copy_in(c)) return fail_cuda(k);
   }
@@ -835,10 +827,6 @@ int align_pipelined(wfa_gpu_ctx* ctx, Call& k, const wfa::AlignArgs& a, int64_t 
       ac.pat = reinterpret_cast<const char*>(rp - (uintptr_t)hp[c]);
       ac.txt = reinterpret_cast<const char*>(rp + (uintptr_t)slot - (uintptr_t)ht[c]);
       ac.host_seqs = 0;
-      if (sin->plen) {
-        ac.plen = reinterpret_cast<const int32_t*>(sp + 2 * slot);
-        ac.tlen = reinterpret_cast<const int32_t*>(sp + 2 * slot + lens);
-      }
       if (!k.ok(cudaStreamWaitEvent(st, ctx->ev_in[s2], 0))) return fail_cuda(k);
     }
     *ctx->h_ctrl = staged_zero;
@@ -1026,7 +1014,7 @@ int align_eager(wfa_gpu_ctx* ctx, int64_t n, const char* patterns, const int64_t
                       (cap == 0 || mapped_range(out_cigars, (size_t)cap * sizeof(uint32_t)))))) {
     const size_t pe = (size_t)ctx->h_ctrl->pat_extent, te = (size_t)ctx->h_ctrl->txt_extent;
     // the lengths are on the device already (stage_inputs)
-    const StreamIn sin{patterns, texts, nullptr, nullptr};
+    const StreamIn sin{patterns, texts};
     const bool streamed = host_seqs && !pattern_offsets && !text_offsets && mapped_range(patterns, pe) &&
                           mapped_range(texts, te);
     if (mode == 0 && (e = lane_order_args(ctx, a, std::min(n, ctx->pipe_chunk), true))) return map_alloc(e);
