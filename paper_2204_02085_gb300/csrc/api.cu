@@ -141,8 +141,8 @@ struct wfa_gpu_ctx {
   // the lane kernel's pairs sorted by estimated score in groups (default
   // path; WFA_GPU_LANE_ORDER=0: call order), and the ordering's buffers
   bool lane_order = true;
-  int lane_sort_min = 12;
-  int64_t pipe_chunk = 1 << 19;  // pairs per chunk of a pipelined host call (WFA_GPU_PIPE_CHUNK)  // the ordering sorts for stores of scores 0-12 and up (WFA_GPU_LANE_SORT_MIN)
+  int lane_sort_min = 12;        // the ordering sorts for stores of scores 0-12 and up (WFA_GPU_LANE_SORT_MIN)
+  int64_t pipe_chunk = 1 << 19;  // pairs per chunk of a pipelined host call (WFA_GPU_PIPE_CHUNK)
   DevBuf<uint32_t> lane_words;
   DevBuf<int2> lane_slots;
   int variant_forced = -1;  // tuning override (WFA_GPU_SHORT_VARIANT)

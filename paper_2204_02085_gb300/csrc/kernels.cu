@@ -425,8 +425,8 @@ cudaError_t plan_one(int device, ShortVariant* v, const char* name) {
 constexpr int kLaneSpan = 8192;
 constexpr int kLaneSpan1 = 4096;
 
-// A lane-per-pair variant; CT_X, CT_OE, CT_E: the scaled penalties whose
-// geometry is compiled in (0: any penalties, geometry from the table).
+// The ordering pass's shared memory and its resident grid (the same for
+// every lane variant).
 using OrderShm = LaneOrderShm<127>;
 
 cudaError_t plan_order(int device, int* grid) {
@@ -441,6 +441,8 @@ cudaError_t plan_order(int device, int* grid) {
   return cudaSuccess;
 }
 
+// A lane-per-pair variant; CT_X, CT_OE, CT_E: the scaled penalties whose
+// geometry is compiled in (0: any penalties, geometry from the table).
 template <int LMAX, int CELLS, int RW, int WPB, int CT_X = 0, int CT_OE = 0, int CT_E = 0, int SPAN = kLaneSpan>
 cudaError_t plan_lane(int device, ShortVariant* v, const char* name) {
   using C = LaneCfg<LMAX, CELLS, RW, SPAN>;

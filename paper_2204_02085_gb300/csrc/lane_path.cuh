@@ -137,8 +137,6 @@ template <int LMAX, int CELLS, int RW, int SPAN_BYTES>
 struct LaneCfg {
   static_assert(LMAX <= 127, "one-byte offsets");
   static constexpr int NW = LMAX / 16 + 2;  // packed 16-base words a window may touch
-  // words of room per sequence: a 32-base window of the pending pass reads
-  // one word past the last that holds a base (its value never counts)
   static constexpr int kHBytes = CELLS * 32;
   static constexpr int kXWords = (CELLS + 31) / 32;  // words of each bit stream
   static constexpr int kXBytes = 2 * kXWords * 4 * 32;
@@ -146,6 +144,9 @@ struct LaneCfg {
   static constexpr int kStore = kHBytes + kXBytes + kRowBytes;
   static constexpr int kUnion = ((kStore > SPAN_BYTES ? kStore : SPAN_BYTES) + 15) / 16 * 16;
   static constexpr int kSpanFit = kUnion / 16;
+  // packed words: NW, and one word of room, since a 32-base window of the
+  // pending pass reads a word past the last that may hold a base (its value
+  // never counts)
   struct WarpShm {
     uint32_t pw[(NW + 1) * 32];
     uint32_t tw[(NW + 1) * 32];
@@ -172,9 +173,9 @@ struct LaneSt {
   int s_fin;           // scaled score once finished
 };
 
-// 32 bases from base position pos of a packed sequence (words at W[j * 32]):
-// the XOR of the pattern's and the text's windows in two 32-bit halves
-// gives the matches before the first difference, up to 32.
+// Matches from pattern position v and text position h, up to 32 (packed
+// words at pw[j * 32], tw[j * 32]): the XOR of the two 32-base windows in
+// two 32-bit halves, leading zeros halved.
 __device__ __forceinline__ int lane_match32(const uint32_t* pw, int v, const uint32_t* tw, int h) {
   const int jp = v >> 4, sp = (v & 15) << 1, jt = h >> 4, st = (h & 15) << 1;
   const uint32_t p1 = pw[(jp + 1) * 32];
