@@ -264,7 +264,7 @@ __device__ __forceinline__ void lane_row(LaneSt& st, int s, int lo, int w, int b
   using Untested = std::integral_constant<bool, false>;
 #pragma unroll 1
   for (int i = 0; i < a; ++i) cell(i, Tested{});
-#pragma unroll 2
+#pragma unroll 4
   for (int i = a; i < b; ++i) cell(i, Untested{});
 #pragma unroll 1
   for (int i = b; i < w; ++i) cell(i, Tested{});
