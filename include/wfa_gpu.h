@@ -359,10 +359,14 @@ int64_t wfa_gpu_request_bytes(const wfa_gpu_request *req);
 void wfa_gpu_server_destroy(wfa_gpu_server *server);
 
 /* Name of short-kernel variant `index` of the context (the index that
- * wfa_gpu_timing.short_variant reports), e.g. "g2_l127_c208_i8" (2 lanes
- * per pair, sequences up to 127 bases, 208 stored cells per pair, int8
- * offsets) or "..._lin" (gap-linear model, M only); NULL if there is no
- * such variant.  The string is static.  Host-only. */
+ * wfa_gpu_timing.short_variant reports): "lane_l127_c197" (one lane per
+ * pair, sequences up to 127 bases, 197 stored cells per pair, one byte per
+ * offset), "lane_ct241_l127_c40" (the same with the geometry of scaled
+ * penalties x = 2, o + e = 4, e = 1 compiled in), "g2_l127_c197_i8" (the
+ * cells of the running pairs spread over the warp's lanes, 2 lanes a pair,
+ * int8 offsets), "..._lin" (gap-linear model, M only) or "..._ef"
+ * (ends-free calls); NULL if there is no such variant.  The string is
+ * static.  Host-only. */
 const char *wfa_gpu_short_variant_name(const wfa_gpu_ctx *ctx, int index);
 
 /* Upper bound on the CIGAR words of one pair of lengths plen, tlen under pen
