@@ -83,9 +83,9 @@ enum {
   WFA_GPU_PLAIN = 8u,       /* the plain baseline for comparisons: the same kernels launched
                                call by call with one fixed short-read variant (the largest
                                store of the call's length class and penalty model), no
-                               sampling autotuner, the arena kernels' work lists in pair
-                               order, and no graph replay (WFA_GPU_GRAPH is ignored); same
-                               results */
+                               sampling autotuner, pairs in call order (no ordering pass),
+                               the arena kernels' work lists in pair order, and no graph
+                               replay (WFA_GPU_GRAPH is ignored); same results */
   WFA_GPU_GRAPH = 16u,      /* with WFA_GPU_DEVICE_PTRS: for batches repeated with the same
                                arguments (same sizes and buffers, new contents), the first
                                call runs as usual and records the device work into a CUDA
@@ -102,7 +102,7 @@ enum {
  * WFA_GPU_TIMING; otherwise zero). */
 typedef struct {
   float h2d_ms;      /* host -> device copies of inputs (host-pointer mode) */
-  float align_ms;    /* the fused short-read wavefront kernel */
+  float align_ms;    /* the short-read phase: ordering pass and short-read kernel */
   float general_ms;  /* the scratch-arena wavefront kernel (pairs it took over) */
   float cigar_ms;    /* CIGAR offset scan and compaction */
   float d2h_ms;      /* device -> host copies of outputs (host-pointer mode) */
