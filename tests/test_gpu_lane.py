@@ -225,12 +225,12 @@ def test_sorted_and_pack_only_ordering_agree(pkg, oracle_mod, monkeypatch, sort_
         _check(al.align(batch, (4, 6, 2)), want)
 
 
-@pytest.mark.parametrize("n", [1, 31, 33, 1023, 1025])
+@pytest.mark.parametrize("n", [1, 31, 33, 1023, 1024, 1025, 2048])
 @pytest.mark.parametrize("name", ("lane_ct241_l127_c40", "lane_l127_c197"))
 def test_ordering_partial_groups(pkg, oracle_mod, monkeypatch, n, name):
-    """Batches of one pair, part of a warp, part of a group and just past a
-    group, through the packing-only (40-cell store) and the sorting
-    (197-cell store) ordering: the oracle's results."""
+    """Batches of one pair, part of a warp, part of a group, whole groups and
+    just past a group, through the packing-only (40-cell store) and the
+    sorting (197-cell store) ordering: the oracle's results."""
     from paper_2204_02085_gb300 import synth
 
     monkeypatch.setenv("WFA_GPU_SHORT_VARIANT", str(_variant_index(pkg, name)))
