@@ -42,6 +42,15 @@ __global__ void __launch_bounds__(32 * WPB) lane_kernel(const AlignArgs a, const
   extern __shared__ __align__(16) unsigned char smem[];
   lane_body<LMAX, CELLS, RW, SPAN, Fwd>(a, g, smem);
 }
+// One large block per SM: its warps fill the shared memory that blocks of a
+// few warps leave unused (the 197-cell store: 17 warps in one block where
+// 2-warp blocks fit 16), and the explicit minimum of one block keeps the
+// compiler from capping its registers for more blocks.
+template <int LMAX, int CELLS, int RW, int SPAN, int WPB, class Fwd>
+__global__ void __launch_bounds__(32 * WPB, 1) lane_kernel_wide(const AlignArgs a, const LaneGeo g) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  lane_body<LMAX, CELLS, RW, SPAN, Fwd>(a, g, smem);
+}
 
 // The lane kernel's ordering pass: a block per group of kLaneGroup pairs
 // (lane_path.cuh).
@@ -424,6 +433,9 @@ cudaError_t plan_one(int device, ShortVariant* v, const char* name) {
 // small stores, where the scratch would otherwise set the shared memory).
 constexpr int kLaneSpan = 8192;
 constexpr int kLaneSpan1 = 4096;
+// warps of the 197-cell store's one block per SM (17 x 12.7 KB of shared
+// memory)
+constexpr int kWide197 = 17;
 
 // The ordering pass's shared memory and its resident grid (the same for
 // every lane variant).
@@ -449,7 +461,9 @@ cudaError_t plan_lane(int device, ShortVariant* v, const char* name) {
   using Fwd = typename std::conditional<CT_X == 0, LaneRunForward,
                                         LaneCtForward<(CT_X ? CT_X : 1), (CT_OE ? CT_OE : 1), (CT_E ? CT_E : 1), CELLS,
                                                       RW>>::type;
-  auto k = lane_kernel<LMAX, CELLS, RW, SPAN, WPB, Fwd>;
+  const void* k;
+  if constexpr (WPB >= 8) k = reinterpret_cast<const void*>(lane_kernel_wide<LMAX, CELLS, RW, SPAN, WPB, Fwd>);
+  else k = reinterpret_cast<const void*>(lane_kernel<LMAX, CELLS, RW, SPAN, WPB, Fwd>);
   const size_t smem = C::smem_bytes(WPB);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -523,7 +537,7 @@ cudaError_t short_plan(int device, ShortPlan* plan) {
   if ((e = plan_lane<127, 40, 16, 4, 0, 0, 0, kLaneSpan1>(device, &plan->v[i++], "lane_l127_c40"))) return e;
   if ((e = plan_lane<127, 64, 16, 4, 0, 0, 0, kLaneSpan1>(device, &plan->v[i++], "lane_l127_c64"))) return e;
   if ((e = plan_lane<127, 104, 32, 2>(device, &plan->v[i++], "lane_l127_c104"))) return e;
-  if ((e = plan_lane<127, 197, 32, 2>(device, &plan->v[i++], "lane_l127_c197"))) return e;
+  if ((e = plan_lane<127, 197, 32, kWide197>(device, &plan->v[i++], "lane_l127_c197"))) return e;
   if ((e = plan_lane<127, 40, 16, 4, 2, 4, 1, kLaneSpan1>(device, &plan->v[i++], "lane_ct241_l127_c40"))) return e;
   if ((e = plan_lane<127, 64, 16, 4, 2, 4, 1, kLaneSpan1>(device, &plan->v[i++], "lane_ct241_l127_c64"))) return e;
   if ((e = plan_lane<127, 104, 32, 2, 2, 4, 1>(device, &plan->v[i++], "lane_ct241_l127_c104"))) return e;
