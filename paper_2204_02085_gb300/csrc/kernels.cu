@@ -433,9 +433,10 @@ cudaError_t plan_one(int device, ShortVariant* v, const char* name) {
 // small stores, where the scratch would otherwise set the shared memory).
 constexpr int kLaneSpan = 8192;
 constexpr int kLaneSpan1 = 4096;
-// warps of the 197-cell store's one block per SM (17 x 12.7 KB of shared
-// memory)
-constexpr int kWide197 = 17;
+// warps of the 197-cell store's one block per SM (18 x 12.3 KB of shared
+// memory, with 30 row positions: the 4/6/2 geometry's rows need 30, penalty
+// sets whose rows are wider keep a shorter store)
+constexpr int kWide197 = 18;
 
 // The ordering pass's shared memory and its resident grid (the same for
 // every lane variant).
@@ -537,7 +538,7 @@ cudaError_t short_plan(int device, ShortPlan* plan) {
   if ((e = plan_lane<127, 40, 16, 4, 0, 0, 0, kLaneSpan1>(device, &plan->v[i++], "lane_l127_c40"))) return e;
   if ((e = plan_lane<127, 64, 16, 4, 0, 0, 0, kLaneSpan1>(device, &plan->v[i++], "lane_l127_c64"))) return e;
   if ((e = plan_lane<127, 104, 32, 2>(device, &plan->v[i++], "lane_l127_c104"))) return e;
-  if ((e = plan_lane<127, 197, 32, kWide197>(device, &plan->v[i++], "lane_l127_c197"))) return e;
+  if ((e = plan_lane<127, 197, 30, kWide197>(device, &plan->v[i++], "lane_l127_c197"))) return e;
   if ((e = plan_lane<127, 40, 16, 4, 2, 4, 1, kLaneSpan1>(device, &plan->v[i++], "lane_ct241_l127_c40"))) return e;
   if ((e = plan_lane<127, 64, 16, 4, 2, 4, 1, kLaneSpan1>(device, &plan->v[i++], "lane_ct241_l127_c64"))) return e;
   if ((e = plan_lane<127, 104, 32, 2, 2, 4, 1>(device, &plan->v[i++], "lane_ct241_l127_c104"))) return e;

@@ -144,12 +144,9 @@ struct LaneCfg {
   static constexpr int kStore = kHBytes + kXBytes + kRowBytes;
   static constexpr int kUnion = ((kStore > SPAN_BYTES ? kStore : SPAN_BYTES) + 15) / 16 * 16;
   static constexpr int kSpanFit = kUnion / 16;
-  // packed words: NW, and one word of room, since a 32-base window of the
-  // pending pass reads a word past the last that may hold a base (its value
-  // never counts)
   struct WarpShm {
-    uint32_t pw[(NW + 1) * 32];
-    uint32_t tw[(NW + 1) * 32];
+    uint32_t pw[NW * 32];
+    uint32_t tw[NW * 32];
     alignas(16) unsigned char u[kUnion];
   };
   static constexpr size_t kTabBytes = (sizeof(UGeo) * 32 + 15) / 16 * 16;
@@ -173,15 +170,19 @@ struct LaneSt {
   int s_fin;           // scaled score once finished
 };
 
-// Matches from pattern position v and text position h, up to 32 (packed
-// words at pw[j * 32], tw[j * 32]): the XOR of the two 32-base windows in
-// two 32-bit halves, leading zeros halved.
+// Matches from pattern position v and text position h, up to 32 (kLaneNW
+// packed words at pw[j * 32], tw[j * 32]): the XOR of the two 32-base
+// windows in two 32-bit halves, leading zeros halved.  A window's third word
+// past the last one (j + 2 = kLaneNW) would hold only positions beyond any
+// sequence's end, which no caller counts: the last word stands in for it.
 __device__ __forceinline__ int lane_match32(const uint32_t* pw, int v, const uint32_t* tw, int h) {
   const int jp = v >> 4, sp = (v & 15) << 1, jt = h >> 4, st = (h & 15) << 1;
   const uint32_t p1 = pw[(jp + 1) * 32];
   const uint32_t t1 = tw[(jt + 1) * 32];
+  const uint32_t p2 = pw[min(jp + 2, kLaneNW - 1) * 32];
+  const uint32_t t2 = tw[min(jt + 2, kLaneNW - 1) * 32];
   const uint32_t dh = __funnelshift_l(p1, pw[jp * 32], sp) ^ __funnelshift_l(t1, tw[jt * 32], st);
-  const uint32_t dl = __funnelshift_l(pw[(jp + 2) * 32], p1, sp) ^ __funnelshift_l(tw[(jt + 2) * 32], t1, st);
+  const uint32_t dl = __funnelshift_l(p2, p1, sp) ^ __funnelshift_l(t2, t1, st);
   return dh ? (int)(__clz(dh) >> 1) : 16 + (int)(__clz(dl) >> 1);
 }
 
@@ -474,16 +475,8 @@ __device__ __forceinline__ int lane_backtrace(const UGeo* tab, const uint8_t* H,
 // Largest estimate kept apart; empty slots take it too.
 constexpr int kLaneEstMax = 63;
 
-// Cost of a greedy alignment, an upper bound on the optimal scaled score,
-// followed only up to cap (a higher bound changes nothing: such a pair
-// passes the store): from the furthest point of diagonal 0, repeatedly take
-// one edit and extend.  A mismatch followed by at least four matches is
-// taken at once; otherwise the mismatch, one inserted and one deleted base
-// (each priced as a fresh event) are all tried, and the one whose extension
-// ends furthest along v + h, less its cost, is taken.  The rest of the
-// longer sequence at an end is one gap.  Packed words at pw[j * 32].
-// The furthest offset of diagonal k from offset h (packed words at W[j * 32],
-// one word of room past the last base): 32 bases a round.
+// The furthest offset of diagonal k from offset h (packed words at W[j * 32]):
+// 32 bases a round.
 __device__ __forceinline__ int lane_extend32(const uint32_t* pw, const uint32_t* tw, int n, int m, int k, int h) {
   for (;;) {
     const int rem = min(n - (h - k), m - h);
@@ -495,6 +488,14 @@ __device__ __forceinline__ int lane_extend32(const uint32_t* pw, const uint32_t*
   }
 }
 
+// Cost of a greedy alignment, an upper bound on the optimal scaled score,
+// followed only up to cap (a higher bound changes nothing: such a pair
+// passes the store): from the furthest point of diagonal 0, repeatedly take
+// one edit and extend.  A mismatch followed by at least four matches is
+// taken at once; otherwise the mismatch, one inserted and one deleted base
+// (each priced as a fresh event) are all tried, and the one whose extension
+// ends furthest along v + h, less its cost, is taken.  The rest of the
+// longer sequence at an end is one gap.  Packed words at pw[j * 32].
 __device__ __forceinline__ int lane_estimate(const uint32_t* pw, const uint32_t* tw, int n, int m, int X, int OE,
                                              int E, int cap) {
   int k = 0, h = lane_extend32(pw, tw, n, m, 0, 0), cost = 0;
@@ -608,9 +609,9 @@ template <int LMAX>
 struct LaneOrderShm {
   static constexpr int NW = LMAX / 16 + 2;
   static constexpr int kWarps = kLaneGroup / 32;
-  struct Warp {  // one word of room past the last for 32-base windows
-    uint32_t pw[(NW + 1) * 32];
-    uint32_t tw[(NW + 1) * 32];
+  struct Warp {
+    uint32_t pw[NW * 32];
+    uint32_t tw[NW * 32];
   } w[kWarps];
   int cnt[2][kWarps][kLaneEstMax + 1];  // alternate groups use alternate halves
   int start[kLaneEstMax + 1];
