@@ -63,3 +63,32 @@ def test_clock_records_that_void_a_number():
     assert not bench.clocks_rejected(dict(ok, sm_mhz=1200.0, reasons=["sw_power_cap"]))
     assert not bench.clocks_rejected({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]})
     assert not bench.clocks_rejected(None)
+
+
+def test_integer_roofline_arithmetic():
+    """The per-pipe bound of the bench's roofline on a hand-computed case:
+    one batch of 1,000 pairs, each 100 wavefront cells, 116 character
+    compares (one further 16-base window) and 5 backtrace steps, timed at
+    1 ms at 2,000 MHz.  Per pair: ALU 100*22 + 1*9 + 5*8 = 2,249, XU 100 + 1
+    = 101, shared memory 100*12 + 1*4 + 5*3 = 1,219 (issue: their sum,
+    3,569); per-pipe peak = 152 SMs x rate x 2e9 clocks/s.  The binding pipe
+    is the one with the longest time: shared memory (1,219 / 32 > 2,249 /
+    64 > 101 / 16)."""
+    import bench
+
+    class C:
+        cells, char_compares, bt_steps = 100_000, 116_000, 5_000
+
+    r = bench.integer_roofline([(1000, C())], [1000], [1.0], 2000.0)
+    clk = 152 * 2000e6
+    p = r["pipes"]
+    assert p["alu"]["ops_per_pair"] == 2249 and p["xu"]["ops_per_pair"] == 101
+    assert p["lsu"]["ops_per_pair"] == 1219 and p["issue"]["ops_per_pair"] == 3569
+    assert r["pipe"] == "lsu"
+    t_lsu = 1219 * 1000 / (32 * clk) * 1e3  # ms at the peak
+    assert abs(r["time_ms"] - t_lsu) < 1e-12 and abs(r["frac"] - t_lsu / 1.0) < 1e-12
+    assert abs(r["peak"] - 32 * clk / 1e12) < 1e-9
+    assert abs(r["achieved"] - 1219 * 1000 / 1e-3 / 1e12) < 1e-9
+    # the flat model: 100*32 + 1*18 + 5*12 = 3,278 ops a pair at the issue rate
+    assert r["flat"]["ops_per_pair"] == 3278
+    assert abs(r["flat"]["frac"] - 3278 * 1000 / (128 * clk) * 1e3 / 1.0) < 1e-12  # ms over the measured 1 ms
