@@ -278,17 +278,37 @@ __global__ void __launch_bounds__(kAuxBlock) compact_kernel(int64_t n, const int
   __shared__ int64_t s_off[kAuxBlock / 32][32];
   __shared__ int64_t s_src[kAuxBlock / 32][32];
   __shared__ int32_t s_cnt[kAuxBlock / 32][32];
+  __shared__ uint32_t s_words[kAuxBlock / 32][32 * kSlot];  // a batch's runs in output order
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5 << 5; i0 < n; i0 += nwarps * 32) {
     const int cnt = n - i0 < 32 ? (int)(n - i0) : 32;
     const int64_t i = i0 + lane;
+    int64_t my_off = 0, my_src = 0;
+    int my_cnt = 0;
     if (lane < cnt) {
-      s_off[wib][lane] = off[i];
-      s_src[wib][lane] = run_src[i];
-      s_cnt[wib][lane] = nruns[i];
+      my_off = off[i];
+      my_src = run_src[i];
+      my_cnt = nruns[i];
+      s_off[wib][lane] = my_off;
+      s_src[wib][lane] = my_src;
+      s_cnt[wib][lane] = my_cnt;
     }
     const int64_t begin = off[i0], end = off[i0 + cnt];
+    // every pair of the batch with its runs in its own slot (the short-read
+    // kernels'): each lane puts its pair's runs in output order in shared
+    // memory, then the warp writes the batch's words with coalesced stores
+    if (__all_sync(0xffffffffu, lane >= cnt || (my_src >= 0 && my_cnt <= kSlot))) {
+      if (lane < cnt) {
+        const uint32_t* r = runs + my_src;
+        uint32_t* d = s_words[wib] + (my_off - begin);
+        for (int j = 0; j < my_cnt; ++j) d[j] = r[my_cnt - 1 - j];  // runs are stored last first
+      }
+      __syncwarp();
+      for (int t = lane; t < (int)(end - begin); t += 32) out[begin + t] = s_words[wib][t];
+      __syncwarp();
+      continue;
+    }
     __syncwarp();
     for (int64_t w = begin + lane; w < end; w += 32) {
       int l = 0;
