@@ -268,10 +268,12 @@ int wfa_gpu_align_short_noalloc(void *stream, int64_t n_pairs,
  *
  * Requests (batches of pairs, of any size, arriving at any time) are queued
  * and admitted onto `workers` slots, each a context with its own stream and
- * buffers; at most three slots run a call at once (a call's device work
+ * buffers; at most two slots run a call at once (a call's device work
  * overlaps another's gathering and scattering on the host; more calls at
- * once only queued behind one another on the GPU and split the queue into
- * smaller batches), further slots wait for a turn.  The server
+ * once only queue behind one another on the GPU and split the queue into
+ * smaller batches), three when the third passes an older request whose
+ * slice does not fit the free arena yet; further slots wait for a turn.
+ * The server
  * owns one scratch arena (the memory budget); every call runs on a slice of
  * it sized to the call's estimated wavefront need (see
  * wfa_gpu_request_bytes; at least 64 MiB, at most half the arena: on a
