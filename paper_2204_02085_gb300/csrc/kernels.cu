@@ -124,143 +124,280 @@ __global__ void validate_kernel(int64_t n, const int64_t* poff, const int32_t* p
 }
 
 // -------------------------------------------------------------------- scan
+//
+// Prefix sums in three kernels: the tile sums (scan_reduce*), the tiles'
+// offsets (scan_tiles, one block), and each tile scanned again with its
+// offset (scan_apply*).  A tile of kScanTile elements is kScanItems items per
+// thread, an item being four consecutive elements moved with one 16-byte
+// load (and two 16-byte stores of the int64 results) when the array is
+// 16-byte aligned; item r of thread t holds elements
+// r * 4 * kScanBlock + 4 t .. + 3, so each warp access covers 512 consecutive
+// bytes of input.
 
 constexpr int kScanBlock = 256;
-constexpr int kScanRows = 8;
-constexpr int kScanTile = kScanBlock * kScanRows;
+constexpr int kScanWarps = kScanBlock / 32;
+constexpr int kScanItems = kScanTile / (4 * kScanBlock);
+static_assert(kScanItems * 4 * kScanBlock == kScanTile, "whole items per tile");
 
-__device__ __forceinline__ int64_t scan_value(const int32_t* in, int64_t i, int64_t n, int kind) {
-  if (i >= n) return 0;
-  const int64_t v = in[i];
-  return kind == 0 ? v : (v + 31) / 32 + 1;
+__device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Elements i .. i + 3 (zero from n on); kind 1: packed words per sequence,
+// ceil(len / 32) + 1, for the elements below n.
+__device__ __forceinline__ int4 scan_load4(const int32_t* in, int64_t i, int64_t n, int kind, bool vec) {
+  int4 v;
+  if (vec && i + 3 < n) {
+    v = __ldg(reinterpret_cast<const int4*>(in + i));
+  } else {
+    v.x = i < n ? in[i] : 0;
+    v.y = i + 1 < n ? in[i + 1] : 0;
+    v.z = i + 2 < n ? in[i + 2] : 0;
+    v.w = i + 3 < n ? in[i + 3] : 0;
+  }
+  if (kind == 1) {
+    v.x = i < n ? (v.x + 31) / 32 + 1 : 0;
+    v.y = i + 1 < n ? (v.y + 31) / 32 + 1 : 0;
+    v.z = i + 2 < n ? (v.z + 31) / 32 + 1 : 0;
+    v.w = i + 3 < n ? (v.w + 31) / 32 + 1 : 0;
+  }
+  return v;
 }
 
-// exclusive scan across the block of v; *total = block sum
-__device__ __forceinline__ int64_t block_exclusive(int64_t v, int64_t* total) {
-  __shared__ int64_t wsum[kScanBlock / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int64_t x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
+// out[i .. i + 3] = c, c + v.x, c + v.x + v.y, c + v.x + v.y + v.z (the
+// exclusive sums of the item from c), only the positions up to n.
+__device__ __forceinline__ void scan_store4(int64_t* out, int64_t i, int64_t n, bool vec, int64_t c, int4 v) {
+  const int64_t a = c, b = a + v.x, d = b + v.y, e = d + v.z;
+  if (vec && i + 3 <= n) {
+    longlong2* o = reinterpret_cast<longlong2*>(out + i);
+    o[0] = make_longlong2(a, b);
+    o[1] = make_longlong2(d, e);
+  } else {
+    if (i <= n) out[i] = a;
+    if (i + 1 <= n) out[i + 1] = b;
+    if (i + 2 <= n) out[i + 2] = d;
+    if (i + 3 <= n) out[i + 3] = e;
   }
-  if (lane == 31) wsum[warp] = x;
+}
+
+__device__ __forceinline__ int64_t item_sum(int4 v) { return (int64_t)v.x + v.y + v.z + v.w; }
+
+// Exclusive scan of R values per thread in element order (value r of thread
+// t comes after every value of rows < r and of threads < t in row r): each
+// warp scans its 32 values of every row with shuffles, the warps' row sums
+// go to shared memory (sh: R * kScanWarps + 1 entries) and warp 0 scans them
+// in order.  Two block barriers; ex[r] = the sum before value r; *total =
+// the sum of all.  A caller that scans again with the same sh synchronises
+// the block first.
+template <int R>
+__device__ __forceinline__ void tile_exclusive(const int64_t (&v)[R], int64_t (&ex)[R], int64_t* total, int64_t* sh) {
+  constexpr int NE = R * kScanWarps, P = (NE + 31) / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    int64_t x = v[r];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    ex[r] = x;  // inclusive within the warp's row for now
+    if (lane == 31) sh[r * kScanWarps + warp] = x;
+  }
   __syncthreads();
   if (warp == 0) {
-    int64_t w = lane < kScanBlock / 32 ? wsum[lane] : 0;
+    int64_t q[P], run = 0;
 #pragma unroll
-    for (int o = 1; o < kScanBlock / 32; o <<= 1) {
-      const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
+    for (int j = 0; j < P; ++j) {
+      q[j] = lane * P + j < NE ? sh[lane * P + j] : 0;
+      run += q[j];
     }
-    if (lane < kScanBlock / 32) wsum[lane] = w;
+    int64_t inc = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    int64_t pre = inc - run;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      if (lane * P + j < NE) sh[lane * P + j] = pre;
+      pre += q[j];
+    }
+    if (lane == 31) sh[NE] = inc;
   }
   __syncthreads();
-  const int64_t before = warp ? wsum[warp - 1] : 0;
-  *total = wsum[kScanBlock / 32 - 1];
+#pragma unroll
+  for (int r = 0; r < R; ++r) ex[r] += sh[r * kScanWarps + warp] - v[r];
+  *total = sh[NE];
+}
+
+// The block's sums of a and b, valid in thread 0.
+__device__ __forceinline__ void block_sum2(int64_t& a, int64_t& b) {
+  __shared__ int64_t sa[kScanWarps], sb[kScanWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if (lane == 0) {
+    sa[warp] = a;
+    sb[warp] = b;
+  }
   __syncthreads();
-  return before + x - v;
+  if (threadIdx.x == 0) {
+    a = b = 0;
+#pragma unroll
+    for (int w = 0; w < kScanWarps; ++w) {
+      a += sa[w];
+      b += sb[w];
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kScanBlock) scan_reduce(const int32_t* in, int64_t n, int kind, int64_t* tile_sums) {
-  const int64_t base = (int64_t)blockIdx.x * kScanTile;
-  int64_t acc = 0;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + 4 * threadIdx.x;
+  const bool vec = aligned16(in);
+  int64_t acc = 0, none = 0;
 #pragma unroll
-  for (int r = 0; r < kScanRows; ++r) acc += scan_value(in, base + r * kScanBlock + threadIdx.x, n, kind);
-  int64_t total;
-  block_exclusive(acc, &total);
-  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+  for (int r = 0; r < kScanItems; ++r) acc += item_sum(scan_load4(in, base + r * 4 * kScanBlock, n, kind, vec));
+  block_sum2(acc, none);
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = acc;
 }
 
 // pattern and text lengths in one pass: the two tile-sum arrays side by side
 __global__ void __launch_bounds__(kScanBlock) scan_reduce2(const int32_t* in1, const int32_t* in2, int64_t n,
                                                            int64_t* tile_sums) {
-  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + 4 * threadIdx.x;
+  const bool vec1 = aligned16(in1), vec2 = aligned16(in2);
   int64_t a1 = 0, a2 = 0;
 #pragma unroll
-  for (int r = 0; r < kScanRows; ++r) {
-    a1 += scan_value(in1, base + r * kScanBlock + threadIdx.x, n, 0);
-    a2 += scan_value(in2, base + r * kScanBlock + threadIdx.x, n, 0);
+  for (int r = 0; r < kScanItems; ++r) {
+    a1 += item_sum(scan_load4(in1, base + r * 4 * kScanBlock, n, 0, vec1));
+    a2 += item_sum(scan_load4(in2, base + r * 4 * kScanBlock, n, 0, vec2));
   }
-  int64_t t1, t2;
-  block_exclusive(a1, &t1);
-  block_exclusive(a2, &t2);
+  block_sum2(a1, a2);
   if (threadIdx.x == 0) {
-    tile_sums[blockIdx.x] = t1;
-    tile_sums[gridDim.x + blockIdx.x] = t2;
+    tile_sums[blockIdx.x] = a1;
+    tile_sums[gridDim.x + blockIdx.x] = a2;
   }
 }
 
-// tile offsets of array blockIdx.x (tile_sums + blockIdx.x * ntiles)
+// tile offsets of array blockIdx.x (tile_sums + blockIdx.x * ntiles):
+// 8 * kScanBlock tile sums a pass
 __global__ void __launch_bounds__(kScanBlock) scan_tiles(int64_t* tile_sums, int64_t ntiles) {
+  constexpr int R = 8;
+  __shared__ int64_t sh[R * kScanWarps + 1];
   tile_sums += (int64_t)blockIdx.x * ntiles;
   int64_t carry = 0;
-  for (int64_t b = 0; b < ntiles; b += kScanBlock) {
-    const int64_t i = b + threadIdx.x;
-    const int64_t v = i < ntiles ? tile_sums[i] : 0;
+  for (int64_t b = 0; b < ntiles; b += R * kScanBlock) {
+    int64_t v[R], ex[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t i = b + r * kScanBlock + threadIdx.x;
+      v[r] = i < ntiles ? tile_sums[i] : 0;
+    }
     int64_t total;
-    const int64_t ex = block_exclusive(v, &total);
-    if (i < ntiles) tile_sums[i] = carry + ex;
+    tile_exclusive(v, ex, &total, sh);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t i = b + r * kScanBlock + threadIdx.x;
+      if (i < ntiles) tile_sums[i] = carry + ex[r];
+    }
     carry += total;
+    __syncthreads();  // sh is scanned again
   }
 }
 
 // offsets of both sequences (out[n] = the totals) and the input checks of
-// validate_kernel on the way (lengths in range; offsets come from the scan)
-__global__ void __launch_bounds__(kScanBlock) scan_apply2_validate(const int32_t* in1, const int32_t* in2, int64_t n,
+// validate_kernel on the way (lengths in range; offsets come from the scan).
+// Both arrays' items are loaded at once, then scanned in registers.
+__global__ void __launch_bounds__(kScanBlock, 4) scan_apply2_validate(const int32_t* in1, const int32_t* in2, int64_t n,
                                                                    const int64_t* tile_off, int64_t* out1,
                                                                    int64_t* out2, Ctrl* ctrl) {
-  const int64_t base = (int64_t)blockIdx.x * kScanTile;
-  int64_t c1 = tile_off[blockIdx.x], c2 = tile_off[gridDim.x + blockIdx.x];
+  __shared__ int64_t sh[2][kScanItems * kScanWarps + 1];
+  __shared__ long long s_pe[kScanWarps], s_te[kScanWarps];
+  __shared__ int s_ml[kScanWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + 4 * threadIdx.x;
+  const bool vin1 = aligned16(in1), vin2 = aligned16(in2), vout = aligned16(out1) && aligned16(out2);
+  int4 v1[kScanItems], v2[kScanItems];
+  int64_t s1[kScanItems], s2[kScanItems], e1[kScanItems], e2[kScanItems];
+#pragma unroll
+  for (int r = 0; r < kScanItems; ++r) {
+    v1[r] = scan_load4(in1, base + r * 4 * kScanBlock, n, 0, vin1);
+    v2[r] = scan_load4(in2, base + r * 4 * kScanBlock, n, 0, vin2);
+    s1[r] = item_sum(v1[r]);
+    s2[r] = item_sum(v2[r]);
+  }
+  int64_t t1, t2;
+  tile_exclusive(s1, e1, &t1, sh[0]);
+  tile_exclusive(s2, e2, &t2, sh[1]);
+  const int64_t c1 = tile_off[blockIdx.x], c2 = tile_off[gridDim.x + blockIdx.x];
   long long pe = 0, te = 0;
   int ml = 0;
   bool bad = false;
-  for (int r = 0; r < kScanRows; ++r) {
-    const int64_t i = base + r * kScanBlock + threadIdx.x;
-    const int64_t v1 = scan_value(in1, i, n, 0), v2 = scan_value(in2, i, n, 0);
-    int64_t t1, t2;
-    const int64_t e1 = block_exclusive(v1, &t1);
-    const int64_t e2 = block_exclusive(v2, &t2);
-    if (i <= n) {
-      out1[i] = c1 + e1;
-      out2[i] = c2 + e2;
-    }
-    if (i < n) {
-      if (v1 < 0 || v2 < 0 || v1 > ((1 << 28) - 1) || v2 > ((1 << 28) - 1)) {
-        bad = true;
-      } else {
-        pe = max(pe, (long long)(c1 + e1 + v1));
-        te = max(te, (long long)(c2 + e2 + v2));
-        ml = max(ml, (int)max(v1, v2));
+#pragma unroll
+  for (int r = 0; r < kScanItems; ++r) {
+    const int64_t i = base + r * 4 * kScanBlock;
+    scan_store4(out1, i, n, vout, c1 + e1[r], v1[r]);
+    scan_store4(out2, i, n, vout, c2 + e2[r], v2[r]);
+    const int x1[4] = {v1[r].x, v1[r].y, v1[r].z, v1[r].w}, x2[4] = {v2[r].x, v2[r].y, v2[r].z, v2[r].w};
+    int64_t o1 = c1 + e1[r], o2 = c2 + e2[r];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      o1 += x1[j];  // the end of element i + j
+      o2 += x2[j];
+      if (i + j < n) {
+        if (x1[j] < 0 || x2[j] < 0 || x1[j] > ((1 << 28) - 1) || x2[j] > ((1 << 28) - 1)) {
+          bad = true;
+        } else {
+          pe = max(pe, (long long)o1);
+          te = max(te, (long long)o2);
+          ml = max(ml, max(x1[j], x2[j]));
+        }
       }
     }
-    c1 += t1;
-    c2 += t2;
   }
+  // the block's extents in one atomic each
   pe = warp_max64(pe);
   te = warp_max64(te);
   ml = __reduce_max_sync(0xffffffffu, ml);
-  if ((threadIdx.x & 31) == 0) {
-    if (pe) atomicMax(&ctrl->pat_extent, pe);
-    if (te) atomicMax(&ctrl->txt_extent, te);
-    if (ml) atomicMax(&ctrl->max_len, ml);
+  if (lane == 0) {
+    s_pe[warp] = pe;
+    s_te[warp] = te;
+    s_ml[warp] = ml;
   }
-  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(&ctrl->bad_input, 1);
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicExch(&ctrl->bad_input, 1);
+  __syncthreads();
+  if (warp == 0) {
+    pe = warp_max64(lane < kScanWarps ? s_pe[lane] : 0);
+    te = warp_max64(lane < kScanWarps ? s_te[lane] : 0);
+    ml = __reduce_max_sync(0xffffffffu, lane < kScanWarps ? s_ml[lane] : 0);
+    if (lane == 0) {
+      if (pe) atomicMax(&ctrl->pat_extent, pe);
+      if (te) atomicMax(&ctrl->txt_extent, te);
+      if (ml) atomicMax(&ctrl->max_len, ml);
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kScanBlock) scan_apply(const int32_t* in, int64_t n, int kind,
                                                          const int64_t* tile_off, int64_t* out) {
-  const int64_t base = (int64_t)blockIdx.x * kScanTile;
-  int64_t carry = tile_off[blockIdx.x];
-  for (int r = 0; r < kScanRows; ++r) {
-    const int64_t i = base + r * kScanBlock + threadIdx.x;
-    const int64_t v = scan_value(in, i, n, kind);
-    int64_t total;
-    const int64_t ex = block_exclusive(v, &total);
-    if (i <= n) out[i] = carry + ex;  // out[n] = grand total
-    carry += total;
+  __shared__ int64_t sh[kScanItems * kScanWarps + 1];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + 4 * threadIdx.x;
+  const bool vin = aligned16(in), vout = aligned16(out);
+  int4 v[kScanItems];
+  int64_t sum[kScanItems], ex[kScanItems];
+#pragma unroll
+  for (int r = 0; r < kScanItems; ++r) {
+    v[r] = scan_load4(in, base + r * 4 * kScanBlock, n, kind, vin);
+    sum[r] = item_sum(v[r]);
   }
+  int64_t total;
+  tile_exclusive(sum, ex, &total, sh);
+  const int64_t carry = tile_off[blockIdx.x];
+#pragma unroll
+  for (int r = 0; r < kScanItems; ++r) scan_store4(out, base + r * 4 * kScanBlock, n, vout, carry + ex[r], v[r]);  // out[n] = total
 }
 
 // ---------------------------------------------------------------- compact

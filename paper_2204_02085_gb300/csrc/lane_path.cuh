@@ -308,7 +308,12 @@ struct LaneRunForward {
                                              int E) {
     constexpr unsigned FULL = 0xffffffffu;
     lane_score0(st);
+    int q = 0, r = 0;  // s / E and s mod E, carried along (no division per score)
     for (int s = 1; s <= st.s_hi && __any_sync(FULL, st.active); ++s) {
+      if (++r == E) {
+        r = 0;
+        ++q;
+      }
       const UGeo g = tab[s];
       if (!(g.ex & 1)) continue;
       int ax = 0, wx = 0, cx = 0, ao = 0, wo = 0, co = 0;
@@ -324,7 +329,6 @@ struct LaneRunForward {
         wo = t.w;
         co = t.base - ao;
       }
-      const int q = s / E, r = s - q * E;
       lane_row(st, s, g.lo, g.w, g.base, ax, wx, cx, ao, wo, co, r * lg.span_i + g.lo - q + lg.off_i,
                r * lg.span_d + g.lo + q + lg.off_d);
     }

@@ -166,6 +166,9 @@ cudaError_t launch_offsets_validate(const int32_t* plen, const int32_t* tlen, in
 cudaError_t launch_validate(int64_t n, const int64_t* poff, const int32_t* plen, const int64_t* toff,
                             const int32_t* tlen, Ctrl* ctrl, cudaStream_t st);
 
+// Elements per tile of the prefix-sum kernels (one tile sum each in tmp).
+constexpr int kScanTile = 2048;
+
 // Exclusive prefix sums into out[0..n] (out[n] = total).  `kind`:
 //   0: values in[i];  1: ceil(in[i]/32) + 1 (packed words per sequence).
 // tmp must hold scan_tmp_elems(n) int64.

@@ -29,7 +29,7 @@ DeviceState g_state[kMaxDevices];
 constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 constexpr size_t kOffCtrl = 0;
 constexpr size_t kOffScanTmp = align256(kOffCtrl + 2 * sizeof(wfa::Ctrl));
-constexpr size_t kScanTmpBytes = ((kN + 1 + 2047) / 2048 + 2) * sizeof(int64_t);
+constexpr size_t kScanTmpBytes = ((kN + 1 + wfa::kScanTile - 1) / wfa::kScanTile + 2) * sizeof(int64_t);
 constexpr size_t kOffPoff = align256(kOffScanTmp + kScanTmpBytes);
 constexpr size_t kOffToff = align256(kOffPoff + (kN + 1) * sizeof(int64_t));
 constexpr size_t kOffNruns = align256(kOffToff + (kN + 1) * sizeof(int64_t));
