@@ -220,6 +220,49 @@ def test_device_pointers_match_host_path(pkg, al, oracle_mod):
         al.set_stream(None)
 
 
+@pytest.mark.parametrize("n", [2049, 4099])
+def test_device_pointers_unaligned_arrays(pkg, al, oracle_mod, n):
+    """Device arrays at addresses that are not 16-byte aligned (sequences one
+    byte in, lengths one int32 in, CIGAR offsets one int64 in) and batch sizes
+    just past prefix-sum tiles of 2,048 and not multiples of four: the
+    offset scans and the input checks take their element-wise loads and
+    stores there.  Scores, statuses, offsets and CIGARs equal the oracle's
+    (exact: integer results)."""
+    import torch
+
+    from paper_2204_02085_gb300 import synth
+
+    b = synth.random_pairs(n, 0, 200, seed=48 + n, edit_rate=0.03)
+    want = oracle_run(oracle_mod, b, (4, 6, 2))
+    dev = torch.device("cuda:0")
+
+    def shifted(a, dtype):  # a copy one element into a larger device buffer
+        buf = torch.zeros(len(a) + 1, dtype=dtype, device=dev)
+        buf[1:] = torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        return buf[1:]
+
+    al.set_stream(torch.cuda.current_stream(dev))
+    try:
+        out_s = torch.empty(n, dtype=torch.int32, device=dev)
+        out_st = torch.empty(n, dtype=torch.int8, device=dev)
+        out_off = torch.empty(n + 2, dtype=torch.int64, device=dev)[1:]
+        out_w = torch.empty(int(want[3][-1]), dtype=torch.int32, device=dev)
+        assert out_off.data_ptr() % 16 == 8
+        plen, tlen = shifted(b.pattern_lengths, torch.int32), shifted(b.text_lengths, torch.int32)
+        assert plen.data_ptr() % 16 == 4 and tlen.data_ptr() % 16 == 4
+        for offsets in (False, True):
+            rc = al.align_device(shifted(b.patterns, torch.uint8),
+                                 shifted(b.pattern_offsets, torch.int64) if offsets else None, plen,
+                                 shifted(b.texts, torch.uint8), shifted(b.text_offsets, torch.int64) if offsets else None,
+                                 tlen, out_s, out_st, out_w, out_off, pen=(4, 6, 2))
+            torch.cuda.synchronize(dev)
+            assert rc == pkg.WFA_GPU_OK
+            got = (out_s.cpu().numpy(), out_st.cpu().numpy(), out_w.cpu().numpy().view(np.uint32), out_off.cpu().numpy())
+            assert_same(got, want)
+    finally:
+        al.set_stream(None)
+
+
 def test_page_locked_host_inputs(pkg, al, oracle_mod):
     """Host-pointer calls whose buffers are page-locked (read by the kernels
     in place over the host link) give the oracle's results, as pageable
