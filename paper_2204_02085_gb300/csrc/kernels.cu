@@ -622,7 +622,7 @@ cudaError_t plan_lane(int device, ShortVariant* v, const char* name) {
   const void* k;
   if constexpr (WPB >= 8) k = reinterpret_cast<const void*>(lane_kernel_wide<LMAX, CELLS, RW, SPAN, WPB, Fwd>);
   else k = reinterpret_cast<const void*>(lane_kernel<LMAX, CELLS, RW, SPAN, WPB, Fwd>);
-  const size_t smem = C::smem_bytes(WPB);
+  const size_t smem = C::smem_bytes(WPB, Fwd::kRows);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -659,6 +659,35 @@ void lane_geometry(const AlignArgs& a, int cells, int rw, LaneGeo* g) {
   g->off_d = L.off_d;
   g->span_i = L.span_i;
   g->span_d = L.span_d;
+  // each score's row record (LaneRunForward): sources, I/D positions and
+  // the untested middle of the row
+  const int X = a.xs, OE = a.oes, E = a.es;
+  for (int s = 1; s < 32; ++s) {
+    const UGeo& t = g->tab[s];
+    LaneRow& r = g->rows[s];
+    if (!(t.ex & 1)) continue;  // ex = 0: the score has no M wavefront
+    r.ex = 1;
+    r.lo = t.lo;
+    r.w = t.w;
+    r.base = t.base;
+    if (s - X >= 0 && (g->tab[s - X].ex & 1)) {
+      const UGeo& x = g->tab[s - X];
+      r.ax = x.lo - t.lo;  // item of the source's first diagonal
+      r.wx = x.w;
+      r.cx = x.base - r.ax;
+    }
+    if (s - OE >= 0 && (g->tab[s - OE].ex & 1)) {
+      const UGeo& o = g->tab[s - OE];
+      r.ao = o.lo - t.lo;
+      r.wo = o.w;
+      r.co = o.base - r.ao;
+    }
+    const int q = s / E, rm = s % E;
+    r.pi0 = rm * L.span_i + t.lo - q + L.off_i;
+    r.pd0 = rm * L.span_d + t.lo + q + L.off_d;
+    r.a = lane_mid_a(r.ax, r.ao, r.w);
+    r.b = lane_mid_b(r.ax, r.wx, r.ao, r.wo, r.w, r.a);
+  }
 }
 
 // The short-kernel variants: (lanes per pair, longest sequence, cells per

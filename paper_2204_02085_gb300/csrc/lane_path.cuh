@@ -150,7 +150,10 @@ struct LaneCfg {
     alignas(16) unsigned char u[kUnion];
   };
   static constexpr size_t kTabBytes = (sizeof(UGeo) * 32 + 15) / 16 * 16;
-  static constexpr size_t smem_bytes(int warps) { return kTabBytes + (size_t)warps * sizeof(WarpShm); }
+  static constexpr size_t kRowsBytes = sizeof(LaneRow) * 32;  // forward passes that read row records
+  static constexpr size_t smem_bytes(int warps, bool rows) {
+    return kTabBytes + (rows ? kRowsBytes : 0) + (size_t)warps * sizeof(WarpShm);
+  }
 };
 
 // One lane's view of its pair and store during the forward pass.
@@ -211,14 +214,27 @@ __device__ __forceinline__ void lane_pending(LaneSt& st, uint32_t pend, int lo, 
   }
 }
 
+// The items of a row whose M sources all lie inside their rows: a .. b - 1
+// (the mismatch source ax <= i < ax + wx, the k + 1 source
+// ao - 1 <= i < ao + wo - 1).
+__host__ __device__ constexpr int lane_mid_a(int ax, int ao, int w) {
+  const int a = ax > ao - 1 ? ax : ao - 1;
+  return a < 0 ? 0 : a > w ? w : a;
+}
+__host__ __device__ constexpr int lane_mid_b(int ax, int wx, int ao, int wo, int w, int a) {
+  const int b = ax + wx < ao + wo - 1 ? ax + wx : ao + wo - 1;
+  return (b < w ? b : w) > a ? (b < w ? b : w) : a;
+}
+
 // One score's row: the cells of items i = 0 .. w-1 (diagonal lo + i), stored
 // at cells base + i.  Sources: row s - x has item i at cell cx + i while
 // 0 <= i - ax < wx, row s - o - e likewise (ao, wo, co) for diagonals k - 1
 // and k + 1; the I and D rows at positions pi0 + i and pd0 + i.  The items
-// whose M sources all lie inside their rows (the middle of the row) run
-// without range tests.  Then the pending extensions and the end test.
+// a .. b - 1, whose M sources all lie inside their rows (the middle of the
+// row), run without range tests.  Then the pending extensions and the end
+// test.
 __device__ __forceinline__ void lane_row(LaneSt& st, int s, int lo, int w, int base, int ax, int wx, int cx, int ao,
-                                         int wo, int co, int pi0, int pd0) {
+                                         int wo, int co, int pi0, int pd0, int a, int b) {
   const int m = st.m;
   const int t0 = lo - st.kf;  // k - (m - n) at item 0
   const int nk0 = st.n + lo;  // n + k at item 0
@@ -257,10 +273,6 @@ __device__ __forceinline__ void lane_row(LaneSt& st, int s, int lo, int w, int b
     oa = ob;
     ob = oc;
   };
-  // the middle: items with the mismatch source (ax <= i < ax + wx) and the
-  // k + 1 source (ao - 1 <= i < ao + wo - 1) inside their rows
-  const int a = min(max(max(ax, ao - 1), 0), w);
-  const int b = max(min(min(ax + wx, ao + wo - 1), w), a);
   using Tested = std::integral_constant<bool, true>;
   using Untested = std::integral_constant<bool, false>;
 #pragma unroll 1
@@ -302,35 +314,18 @@ __device__ __forceinline__ void lane_score0(LaneSt& st) {
   }
 }
 
-// Forward pass over a geometry table (any penalties).
+// Forward pass over the call's row records (any penalties): four 16-byte
+// loads a score.
 struct LaneRunForward {
-  static __device__ __forceinline__ void run(LaneSt& st, const UGeo* tab, const LaneGeo& lg, int X, int OE,
-                                             int E) {
+  static constexpr bool kRows = true;
+  static __device__ __forceinline__ void run(LaneSt& st, const LaneRow* rows) {
     constexpr unsigned FULL = 0xffffffffu;
     lane_score0(st);
-    int q = 0, r = 0;  // s / E and s mod E, carried along (no division per score)
     for (int s = 1; s <= st.s_hi && __any_sync(FULL, st.active); ++s) {
-      if (++r == E) {
-        r = 0;
-        ++q;
-      }
-      const UGeo g = tab[s];
-      if (!(g.ex & 1)) continue;
-      int ax = 0, wx = 0, cx = 0, ao = 0, wo = 0, co = 0;
-      if (s - X >= 0 && (tab[s - X].ex & 1)) {
-        const UGeo t = tab[s - X];
-        ax = t.lo - g.lo;  // item of the source's first diagonal
-        wx = t.w;
-        cx = t.base - ax;
-      }
-      if (s - OE >= 0 && (tab[s - OE].ex & 1)) {
-        const UGeo t = tab[s - OE];
-        ao = t.lo - g.lo;
-        wo = t.w;
-        co = t.base - ao;
-      }
-      lane_row(st, s, g.lo, g.w, g.base, ax, wx, cx, ao, wo, co, r * lg.span_i + g.lo - q + lg.off_i,
-               r * lg.span_d + g.lo + q + lg.off_d);
+      const int4* r = reinterpret_cast<const int4*>(rows + s);
+      const int4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3];
+      if (!r3.y) continue;  // no M wavefront at this score
+      lane_row(st, s, r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w, r3.x);
     }
   }
 };
@@ -354,7 +349,8 @@ struct LaneCtForward {
     constexpr int Q = S / E, R = S % E;
     constexpr int PI0 = R * G.L.span_i + g.lo - Q + G.L.off_i;
     constexpr int PD0 = R * G.L.span_d + g.lo + Q + G.L.off_d;
-    lane_row(st, S, g.lo, g.w, g.base, AX, WX, CX, AO, WO, CO, PI0, PD0);
+    constexpr int A = lane_mid_a(AX, AO, g.w), B = lane_mid_b(AX, WX, AO, WO, g.w, A);
+    lane_row(st, S, g.lo, g.w, g.base, AX, WX, CX, AO, WO, CO, PI0, PD0, A, B);
   }
 
   template <int S>
@@ -366,7 +362,8 @@ struct LaneCtForward {
     }
   }
 
-  static __device__ __forceinline__ void run(LaneSt& st, const UGeo*, const LaneGeo&, int, int, int) {
+  static constexpr bool kRows = false;
+  static __device__ __forceinline__ void run(LaneSt& st, const LaneRow*) {
     lane_score0(st);
     scores<1>(st);
   }
@@ -732,10 +729,14 @@ __device__ __forceinline__ void lane_body(const AlignArgs& a, const LaneGeo& lg,
   using C = LaneCfg<LMAX, CELLS, RW, SPAN_BYTES>;
   if (*(volatile int32_t*)&a.ctrl->bad_input) return;  // inputs rejected by the validation kernel
   UGeo* tab = reinterpret_cast<UGeo*>(smem);
+  LaneRow* rows = reinterpret_cast<LaneRow*>(smem + C::kTabBytes);  // when Fwd reads them
   for (int i = threadIdx.x; i < 32; i += blockDim.x) tab[i] = lg.tab[i];
+  if constexpr (Fwd::kRows)
+    for (int i = threadIdx.x; i < 32; i += blockDim.x) rows[i] = lg.rows[i];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  auto* W = reinterpret_cast<typename C::WarpShm*>(smem + C::kTabBytes + warp * sizeof(typename C::WarpShm));
+  constexpr size_t kHead = C::kTabBytes + (Fwd::kRows ? C::kRowsBytes : 0);
+  auto* W = reinterpret_cast<typename C::WarpShm*>(smem + kHead + warp * sizeof(typename C::WarpShm));
   const int s_store = lg.s_store;
   const int X = a.xs, OE = a.oes, E = a.es;
   LaneSt st;
@@ -844,7 +845,7 @@ __device__ __forceinline__ void lane_body(const AlignArgs& a, const LaneGeo& lg,
     st.kf = m - n;
     st.active = active;
     st.s_fin = -1;
-    Fwd::run(st, tab, lg, X, OE, E);
+    Fwd::run(st, rows);
     if (st.cnext & 31) {  // the last, partly filled words
       st.XI[(st.cnext >> 5) * 32] = st.ai;
       st.XD[(st.cnext >> 5) * 32] = st.ad;

@@ -117,8 +117,22 @@ int short_launches(const AlignArgs& a, const ShortVariant& v);
 // it takes no pair, e.g. ends-free calls), and where the in-place I and D
 // rows keep each score: I_s[k] at position (s mod e) * span_i + k - s/e +
 // off_i, D_s[k] at (s mod e) * span_d + k + s/e + off_d.
+// rows[s]: score s's row as the forward pass with the table read at run
+// time takes it (every lane of every warp the same, so it is worked out
+// once on the host): its diagonals and store cells, where its sources lie,
+// and the items whose sources all lie inside their rows.
+struct alignas(16) LaneRow {
+  int32_t lo, w, base;  // first diagonal, width, store cell of item 0
+  int32_t ax, wx, cx;   // row s - x: its first item, its width, the cell of item 0
+  int32_t ao, wo, co;   // row s - o - e, likewise
+  int32_t pi0, pd0;     // I and D row positions of item 0
+  int32_t a, b;         // items a .. b - 1 need no range test
+  int32_t ex;           // 1: the score has an M wavefront
+  int32_t pad[2];
+};
 struct LaneGeo {
   UGeo tab[32];
+  LaneRow rows[32];
   int32_t s_store, off_i, off_d, span_i, span_d, pad[3];
 };
 // Fills g for the call's penalties and a variant of `cells` cells and
