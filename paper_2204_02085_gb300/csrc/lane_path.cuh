@@ -644,9 +644,12 @@ __device__ void lane_order_body(const AlignArgs& a, int est_cap, unsigned char* 
     const int64_t pair = gi * kLaneGroup + threadIdx.x;
     bool active = pair < a.n;
     int n = 0, m = 0;
+    int64_t po = 0, to = 0;
     if (active) {
       n = a.plen[pair];
       m = a.tlen[pair];
+      po = a.poff[pair];  // with the lengths: one round trip for all four
+      to = a.toff[pair];
       if (n > LMAX || m > LMAX) {
         defer_pair(a, pair);
         active = false;
@@ -654,8 +657,8 @@ __device__ void lane_order_body(const AlignArgs& a, int est_cap, unsigned char* 
     }
     if (active) {
       static_assert(16 * NW - 15 >= LMAX, "chunks of the longest sequence");
-      const bool bad = lane_pack_direct<NW>(a.pat + a.poff[pair], n, W.pw + lane) |
-                       lane_pack_direct<NW>(a.txt + a.toff[pair], m, W.tw + lane);
+      const bool bad = lane_pack_direct<NW>(a.pat + po, n, W.pw + lane) |
+                       lane_pack_direct<NW>(a.txt + to, m, W.tw + lane);
       if (bad) {
         write_result(a, pair, 2, -1, 0, 0);
         active = false;
