@@ -346,14 +346,17 @@ int64_t wfa_gpu_server_submit(wfa_gpu_server *server, const wfa_gpu_request *req
  * running; wait again later), EINVAL for an unknown id. */
 int wfa_gpu_server_wait(wfa_gpu_server *server, int64_t id, double timeout_s, wfa_gpu_request_stats *stats);
 
-/* Estimated device bytes a request holds while it runs: inputs, outputs,
- * per-pair work buffers, and the arena its wavefronts take -- for pairs
- * longer than 127 bases (the short-read kernels keep theirs in shared
- * memory), 3 offsets of 2 bytes (4 from 32,000 bases) on about
- * (s'/e' + 1)^2 cells, s' = WFA_GPU_SERVER_EDIT_RATE x max(n, m) x
- * max(x, o + e) / g and e' = e / g (g = gcd(x, o, e)), summed over the 4,096
- * largest such pairs (no more run at once).  The arena part is what the
- * server admits requests by.  Host-only. */
+/* Estimated device bytes a request holds while it runs: its sequence
+ * bytes, 150 bytes a pair (lengths, offsets, outputs, work buffers, CIGAR
+ * slots), 4 bytes a word of CIGAR capacity, and the arena its wavefronts
+ * take -- for pairs longer than 127 bases (the short-read kernels keep
+ * theirs in shared memory), 3 offsets of 2 bytes (4 from 32,000 bases) on
+ * about (s'/e' + 1)^2 cells plus 16 (s' + 1) bytes of per-score records,
+ * s' = WFA_GPU_SERVER_EDIT_RATE x max(n, m) x max(x, o + e) / g and
+ * e' = e / g (g = gcd(x, o, e)), summed over the 4,096 largest such pairs
+ * (no more run at once).  The arena part is what the server admits
+ * requests by.  Returns -1 for a NULL or malformed request (n_pairs < 0,
+ * or missing length arrays).  Host-only. */
 int64_t wfa_gpu_request_bytes(const wfa_gpu_request *req);
 
 /* Finish the admitted requests, drop the queued ones (their waits return

@@ -175,3 +175,68 @@ def test_missing_library_fails_loudly():
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == "raised True"
+
+
+def _request(pkg, plens, tlens, pen=(4, 6, 2), cap=0):
+    """A request carrying only what the byte estimate reads (host-only)."""
+    import numpy as np
+
+    p = np.ascontiguousarray(plens, dtype=np.int32)
+    t = np.ascontiguousarray(tlens, dtype=np.int32)
+    r = pkg.Request()
+    r.n_pairs = len(p)
+    r.pattern_lengths = p.ctypes.data if len(p) else None
+    r.text_lengths = t.ctypes.data if len(t) else None
+    r.pen = pkg.Penalties(*pen)
+    r.cigar_capacity_words = cap
+    return r, (p, t)  # the arrays must outlive the call
+
+
+def test_request_bytes_closed_form(pkg):
+    """wfa_gpu_request_bytes on hand-worked cases.  A request holds its
+    sequence bytes, 150 bytes a pair, 4 per CIGAR word of capacity, and for
+    each pair longer than 127 bases 3 offsets of 2 bytes (4 from 32,000
+    bases) on (s'/e' + 1)^2 cells plus 16 (s' + 1) bytes, with
+    s' = 0.10 * max(n, m) * max(x, o + e) / g, e' = e / g, g = gcd(x, o, e);
+    over the 4,096 largest such pairs only."""
+    rb = pkg.wfa_gpu_request_bytes
+    # no pairs: the CIGAR capacity alone
+    r, keep = _request(pkg, [], [], cap=7)
+    assert rb(r) == 28
+    # short pairs keep their wavefronts in shared memory: no arena term
+    r, keep = _request(pkg, [100, 127], [100, 120], cap=10)
+    assert rb(r) == (100 + 100 + 127 + 120) + 2 * 150 + 4 * 10
+    # 1,000 bases under 4/6/2: g = 2, max(x, o + e) / g = 4, e' = 1,
+    # s' = 0.10 * 1000 * 4 = 400: 3 * 2 * 401^2 + 16 * 401 = 971,222
+    r, keep = _request(pkg, [1000], [990])
+    assert rb(r) == 1990 + 150 + 971222
+    # the longer sequence sets L; a negative length counts as 0 bytes
+    r, keep = _request(pkg, [-5], [1000])
+    assert rb(r) == 1000 + 150 + 971222
+    # 40,000 bases: 4-byte offsets, s' = 16,000:
+    # 3 * 4 * 16001^2 + 16 * 16001 = 3,072,640,028
+    r, keep = _request(pkg, [40000], [40000])
+    assert rb(r) == 80000 + 150 + 3072640028
+    # other penalties: 2/3/1 has g = 1, max(x, o + e) = 4, e' = 1: the same
+    # s' as 4/6/2 and the same bytes; 6/4/2 has g = 2, max = 6 / 2 = 3, e' = 1,
+    # s' = 300: 3 * 2 * 301^2 + 16 * 301 = 548,422
+    r, keep = _request(pkg, [1000], [1000], pen=(2, 3, 1))
+    assert rb(r) == 2000 + 150 + 971222
+    r, keep = _request(pkg, [1000], [1000], pen=(6, 4, 2))
+    assert rb(r) == 2000 + 150 + 548422
+    # 4,097 pairs of 200 bases and one of 300: only the 4,096 largest count
+    # (the 300-base pair and 4,095 of the others).  200 bases: s' = 80,
+    # 3 * 2 * 81^2 + 16 * 81 = 40,662; 300 bases: s' = 120,
+    # 3 * 2 * 121^2 + 16 * 121 = 89,782
+    r, keep = _request(pkg, [200] * 4097 + [300], [200] * 4097 + [300])
+    assert rb(r) == (400 * 4097 + 600) + 150 * 4098 + 4095 * 40662 + 89782
+
+
+def test_request_bytes_rejects_malformed(pkg):
+    rb = pkg.wfa_gpu_request_bytes
+    r, keep = _request(pkg, [10], [10])
+    r.n_pairs = -1
+    assert rb(r) == -1
+    r, keep = _request(pkg, [10], [10])
+    r.pattern_lengths = None
+    assert rb(r) == -1
