@@ -92,3 +92,20 @@ def test_integer_roofline_arithmetic():
     # the flat model: 100*32 + 1*18 + 5*12 = 3,278 ops a pair at the issue rate
     assert r["flat"]["ops_per_pair"] == 3278
     assert abs(r["flat"]["frac"] - 3278 * 1000 / (128 * clk) * 1e3 / 1.0) < 1e-12  # ms over the measured 1 ms
+
+
+def test_traffic_record_matches_the_sources():
+    """The DRAM traffic the bench reports comes from an ncu capture of the
+    device sources as they stand: the record's digest is the sources', the
+    launch-list and counter summaries name the same digest, and the bytes
+    per pair lie between the algorithmic input and output (about 248 B) and
+    twice that."""
+    import bench
+
+    sha = bench.kernel_sources_digest()
+    assert bench.NCU_TRAFFIC["sha"] == sha
+    for e in (2, 4):
+        assert 248 <= bench.NCU_TRAFFIC["bytes_per_pair"][e] <= 2 * 248
+    prof = os.path.join(ROOT, "profiles")
+    for name in ("launch_list_5Mx100bp_E2_E4.md", "lane_kernel_and_ordering_1Mx100bp_E2_E4_ncu.md"):
+        assert sha in open(os.path.join(prof, name)).read(), name
